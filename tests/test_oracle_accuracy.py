@@ -1,0 +1,78 @@
+"""Statistical pins: the oracle's centralities against exact breadth-first
+values on the Zipf(2.1) workload (Sec. 4.1 error bound; Sec. 8's
+observation that centrality errors stay near the single-counter RSD and
+shrink when runs are averaged)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1308_2144_gb300 import graphs
+
+
+@pytest.fixture(scope="module")
+def plain(orc):
+    g = graphs.plain_graph(n=10_000, seed=1)
+    off, tgt = g.numpy()
+    exact = orc.exact_centralities(off, tgt)
+    return off, tgt, exact
+
+
+def _rel(a, b):
+    return np.abs(a - b) / np.abs(b)
+
+
+def test_plain_workload_shape(plain):
+    off, tgt, exact = plain
+    n, m = off.size - 1, tgt.size
+    assert n == 10_000
+    # mean of Zipf(2.1) truncated at 1000 is about 3.57 arcs per node
+    assert 3.0 * n < m < 4.2 * n
+    assert exact["reach"].min() >= 1
+
+
+def test_error_across_runs_near_counter_rsd(orc, plain):
+    """Over independent hash seeds, each node's RMS relative error stays
+    within the single-counter bound 1.06/sqrt(p) (Sec. 4.1, Sec. 8), and
+    the estimates are unbiased.  (Most nodes share one coreachable set, so
+    within a single run their errors are one shared draw: the statistic is
+    taken across runs.)"""
+    off, tgt, exact = plain
+    b, K = 8, 24
+    bound = 1.06 / math.sqrt(1 << b)
+    big = exact["reach"] >= 200
+    assert big.sum() > 1000
+    err = {"reach": [], "harm": [], "sumd": []}
+    for k in range(K):
+        res = orc.run(off, tgt, b, 500 + k)
+        fin = orc.finalize(b, res.regs, res.sumd, res.harm)
+        err["reach"].append(fin["reachable"][big] / exact["reach"][big] - 1)
+        err["harm"].append(fin["harmonic"][big] / exact["harm"][big] - 1)
+        err["sumd"].append(res.sumd[big] / exact["sumd"][big] - 1)
+    for key, e in err.items():
+        e = np.array(e)
+        rms = np.sqrt((e ** 2).mean(axis=0))
+        assert np.median(rms) <= 1.15 * bound, key
+        assert abs(np.median(e.mean(axis=0))) <= 3 * bound / math.sqrt(K), key
+    # small balls are counted by the small-range estimator almost exactly
+    res = orc.run(off, tgt, b, 42)
+    fin = orc.finalize(b, res.regs, res.sumd, res.harm)
+    small = exact["reach"] <= 8
+    if small.any():
+        assert np.median(_rel(fin["reachable"][small], exact["reach"][small])) < 0.05
+
+
+def test_averaging_runs_shrinks_error(orc, plain):
+    off, tgt, exact = plain
+    b, K = 4, 16
+    harm = []
+    for k in range(K):
+        res = orc.run(off, tgt, b, 1000 + k)
+        harm.append(res.harm)
+    harm = np.array(harm)
+    big = exact["reach"] >= 200
+    single = np.median(_rel(harm[0][big], exact["harm"][big]))
+    mean16 = np.median(_rel(harm.mean(axis=0)[big], exact["harm"][big]))
+    # error of a K-run mean ~ 1/sqrt(K) of one run's: allow 0.5 for K = 16
+    assert mean16 < 0.5 * single
+    assert single <= 1.06 / math.sqrt(1 << b) * 1.2
