@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 HyperBall step.
+
+One bench step is one whole HyperBall computation on the resident graph:
+re-initialise the counters (Algorithm 2, first loop), iterate to the
+fixpoint (every iteration: frontier, gather + union, estimator and
+accumulators), and finalise the four centralities into device buffers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Metric: arc-updates per second (arcs scanned by all iterations / time to
+fixpoint), plus time to fixpoint and the roofline fraction of the gather
+kernel.  The default workload is the encyclopedia-link-like graph: R-MAT
+(0.57, 0.19, 0.19, 0.05) with 4,206,785 nodes and 101,355,853 arcs drawn,
+scanned as its transpose, log2m = 6.  Under torchrun each rank runs an
+independent replica (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HyperBall arc-updates/s per step and % HBM roofline; time to fixpoint"
+UNIT = "arc-updates/s"
+
+WORKLOADS = {
+    "enwiki": dict(log2m=6, seed=42, desc="R-MAT(0.57,0.19,0.19,0.05) scale 23, 4,206,785 nodes, "
+                                         "101,355,853 arcs drawn, dedup, transpose scanned, log2m=6"),
+    "plain": dict(log2m=4, seed=42, desc="Zipf(2.1) out-degree on {1..1000}, 10,000 nodes, uniform "
+                                        "targets, transpose scanned, log2m=4"),
+    "web": dict(log2m=4, seed=42, desc="R-MAT scale 28 (268,435,456 nodes), edge factor 16, dedup, "
+                                      "transpose scanned, log2m=4, FP32 estimates"),
+}
+
+
+def make_graph(name, device):
+    from paper_1308_2144_gb300 import graphs
+    if name == "enwiki":
+        return graphs.enwiki_graph(device=device)
+    if name == "plain":
+        return graphs.plain_graph(device=device)
+    if name == "web":
+        return graphs.web_graph(device=device)
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------- helpers --
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(workload):
+    """DRAM traffic per gather-kernel launch from the committed ncu summary,
+    valid only while the kernel source is the one that was profiled."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}_traffic.txt")
+    src = os.path.join(ROOT, "paper_1308_2144_gb300", "csrc", "hb_step.cu")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if "=" in ln and not ln.startswith("#"):
+            k, v = ln.split("=", 1)
+            vals[k.strip()] = v.strip()
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if vals.get("source_sha256") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- the oracle --
+
+def cpu_oracle_sample(g_cpu, log2m, seed, budget_s=20.0, max_iters=3):
+    """The oracle, as it stands, on the host cores: its first iterations of
+    Algorithm 2 on the full graph (every node recomputed), bounded in time."""
+    import oracle
+    off, tgt = g_cpu
+    n = off.size - 1
+    c = oracle.init(n, log2m, seed)
+    sumd = np.zeros(n)
+    harm = np.zeros(n)
+    arcs, secs, iters = 0, 0.0, 0
+    for t in range(max_iters):
+        t0 = time.perf_counter()
+        c, _, _ = oracle.step(off, tgt, log2m, t, c, sumd, harm)
+        secs += time.perf_counter() - t0
+        arcs += tgt.size
+        iters += 1
+        if secs > budget_s:
+            break
+    return {"value": arcs / secs, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"first {iters} iteration(s) of Algorithm 2 on the full graph "
+                      f"({arcs} arc-updates in {secs:.2f} s, every node recomputed)"}
+
+
+# ------------------------------------------------------------------ arms --
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    g = make_graph(args.workload, dev)
+    off, tgt = g.numpy()
+    import oracle
+    n = off.size - 1
+    vals, secs_all = [], []
+    for k in range(args.warmup + args.steps):
+        c = oracle.init(n, wl["log2m"], wl["seed"] + k)
+        sumd, harm = np.zeros(n), np.zeros(n)
+        t0 = time.perf_counter()
+        oracle.step(off, tgt, wl["log2m"], 0, c, sumd, harm)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            secs_all.append(dt)
+    total = sum(secs_all)
+    value = tgt.size * len(secs_all) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(secs_all),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "n": int(n), "m": int(tgt.size),
+                   "step": "one full iteration of Algorithm 2 (every node recomputed) by the CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": "one iteration of Algorithm 2 on the full graph per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    from paper_1308_2144_gb300 import build, hyperball as hbl
+    build.build()
+    hbl.load()
+    wl = WORKLOADS[args.workload]
+    fp32 = args.fp32 or args.workload == "web"
+    stream = torch.cuda.current_stream()
+    g = make_graph(args.workload, "cuda")
+    n, m, log2m = g.n, g.m, wl["log2m"]
+    torch.cuda.synchronize()
+    opts = dict(log2m=log2m, seed=wl["seed"], n=n, fp32=fp32, frontier=args.frontier,
+                stream=stream, profile=True)
+    hb = hbl.HyperBall(g.offsets, g.targets, **opts)
+    cen = {k: torch.empty(n, dtype=torch.float64, device="cuda")
+           for k in ("closeness", "harmonic", "lin", "reachable")}
+
+    def one_run(seed):
+        hbl.hb_reset(hb._h, seed)
+        steps = hbl.hb_run_to_fixpoint(hb._h)
+        hbl.hb_get_centralities(hb._h, cen["closeness"], cen["harmonic"], cen["lin"], cen["reachable"])
+        info = hb.info()
+        return steps, info
+
+    for k in range(args.warmup):
+        one_run(wl["seed"] + k)
+    torch.cuda.synchronize()
+    launches0 = hb.info()["launches"]
+    arcs, kms, kbytes, klaunch, steps_list = 0, 0.0, 0.0, 0, []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for k in range(args.steps):
+            steps, info = one_run(wl["seed"] + args.warmup + k)
+            arcs += info["total_arcs"]
+            kms += info["kernel_ms"]
+            kbytes += info["kernel_bytes"]
+            klaunch += info["kernel_launches"]
+            steps_list.append(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    launches = hb.info()["launches"] - launches0
+    ms_max = max_over_ranks(ms, world)
+    arcs_all = sum_over_ranks(arcs, world)
+    value = arcs_all / (ms_max / 1e3)
+
+    # roofline of the gather kernel (events recorded by the library on this stream)
+    peak, peak_kind = measured_peaks()
+    achieved = (kbytes / klaunch) / ((kms / klaunch) / 1e3) / 1e9 if klaunch else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "kernel": "step_kernel (gather + union + estimator)",
+                "bytes_per_launch": kbytes / klaunch if klaunch else 0.0,
+                "ms_per_launch": kms / klaunch if klaunch else 0.0}
+
+    # end to end through the public API: host CSR in pinned memory, results
+    # back to pinned host memory, handle created and destroyed every step
+    off_h = g.offsets.cpu().pin_memory()
+    tgt_h = g.targets.cpu().pin_memory()
+    outs_h = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in cen}
+    e2e_steps = max(1, min(args.steps, 3))
+    e2e_arcs = 0
+    opts_h = dict(opts)
+    opts_h.pop("profile")
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=wl["seed"] + 100 + k))
+        h.run()
+        hbl.hb_get_centralities(h._h, outs_h["closeness"], outs_h["harmonic"], outs_h["lin"],
+                                outs_h["reachable"])
+        e2e_arcs += h.info()["total_arcs"]
+        h.close()
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e_val = sum_over_ranks(e2e_arcs, world) / e2e_s
+    h2d = off_h.numel() * off_h.element_size() + tgt_h.numel() * tgt_h.element_size()
+    d2h = 4 * n * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(g.numpy(), log2m, wl["seed"])
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "m": m, "log2m": log2m,
+                       "estimate": "fp32" if fp32 else "fp64", "accumulators": "fp64",
+                       "frontier": args.frontier,
+                       "iterations_to_fixpoint": steps_list,
+                       "arc_updates_per_step": arcs / args.steps,
+                       "time_to_fixpoint_ms": ms_max / args.steps,
+                       "l2": "inputs larger than L2 (no flush): counters 2 x %.0f MB, targets %.0f MB"
+                             % (n * (1 << log2m) / 1e6, m * 4 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    hb.close()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="enwiki")
+    ap.add_argument("--frontier", choices=["auto", "push", "pull", "off"], default="auto")
+    ap.add_argument("--fp32", action="store_true", help="precision form (FP32 estimates)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

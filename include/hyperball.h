@@ -1,0 +1,189 @@
+/*
+ * hyperball.h -- C ABI of the GB300 HyperBall library.
+ *
+ * HyperBall (Boldi & Vigna, "In-Core Computation of Geometric Centralities
+ * with HyperBall", arXiv:1308.2144) keeps one HyperLogLog counter of
+ * p = 2^log2m one-byte registers per node.  Each iteration sets every
+ * counter to the register-wise maximum of itself and its successors'
+ * counters (Sec. 4.2, Algorithm 2) and folds the change of each counter's
+ * size estimate into three per-node accumulators (Sec. 5); iterations stop
+ * after the first one that leaves every counter unchanged (Sec. 4.2).
+ * Closeness, Lin and harmonic centrality and the coreachable-set size
+ * follow (Sec. 3).
+ *
+ * Conventions for every call:
+ *   - Graphs are CSR: the successors of node v are
+ *     targets[offsets[v] .. offsets[v+1]-1]; offsets has n+1 entries with
+ *     offsets[0] = 0 and offsets[n] = m, non-decreasing; every target lies
+ *     in [0, n).  Self-loops and repeated arcs are accepted (union is
+ *     idempotent).  n must be below 2^31.
+ *   - The graph given is the one scanned: a node's counter collects its
+ *     successors.  The paper's (in-)centralities are distances *to* a node,
+ *     so pass the transpose G^T, or pass G with HB_TRANSPOSE (Sec. 5).
+ *   - Pointers may be host or device memory; the library tells them apart
+ *     with cudaPointerGetAttributes.  Inputs are copied unless
+ *     HB_BORROW_DEVICE_PTRS is set, in which case device inputs must stay
+ *     valid and unchanged until hb_destroy.  Outputs may be host or device
+ *     memory of the stated size; the call returns when they are written.
+ *   - The library owns every buffer it allocates (registers, flags,
+ *     accumulators) and frees them in hb_destroy.
+ *   - All device work runs on the stream in hb_options (NULL = the legacy
+ *     default stream).  A handle must not be used by two threads at once;
+ *     distinct handles are independent.
+ *   - Every call returns an hb_status.  On failure hb_last_error() gives a
+ *     message (thread-local).  A failed call leaves the handle as it was,
+ *     except HB_ERR_CUDA during a step, after which the handle is marked
+ *     unusable (HB_ERR_STATE on later calls).
+ */
+#ifndef HYPERBALL_H
+#define HYPERBALL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HB_OK = 0,
+    HB_ERR_INVALID = -1,        /* bad argument or malformed graph */
+    HB_ERR_OOM = -2,            /* device allocation failed */
+    HB_ERR_CUDA = -3,           /* a CUDA call failed */
+    HB_ERR_NOT_CONVERGED = -4,  /* max_steps iterations ran, state still valid */
+    HB_ERR_TIMEOUT = -5,        /* a bounded device-side wait gave up */
+    HB_ERR_STATE = -6           /* handle unusable or call out of order */
+} hb_status;
+
+/* hb_options.flags */
+#define HB_TRANSPOSE          0x1u  /* scan G^T: the library transposes the CSR on the device */
+#define HB_BORROW_DEVICE_PTRS 0x2u  /* device inputs are used in place, not copied */
+#define HB_FP32_ESTIMATE      0x4u  /* precision form: FP32 estimates and deltas, FP64 accumulators */
+#define HB_NO_RELABEL         0x8u  /* keep the caller's node order on the device (no degree sort) */
+#define HB_PROFILE            0x10u /* time the gather kernel of every iteration with CUDA events */
+
+/* hb_options.frontier: how the nodes to recompute are chosen each step
+ * (Sec. 5 / 5.1 modification tracking).  Results never depend on it. */
+#define HB_FRONTIER_AUTO 0  /* push from changed nodes when that is cheaper than a full scan */
+#define HB_FRONTIER_PULL 1  /* each node checks its successors' changed flags */
+#define HB_FRONTIER_PUSH 2  /* changed nodes mark their predecessors (needs the reverse CSR) */
+#define HB_FRONTIER_OFF  3  /* recompute every node at every step */
+
+typedef struct {
+    uint32_t flags;      /* HB_* flags above */
+    int32_t frontier;    /* HB_FRONTIER_* */
+    int32_t max_steps;   /* iteration cap for hb_run_to_fixpoint; <= 0 means 1<<20 */
+    void *stream;        /* cudaStream_t, or NULL */
+} hb_options;
+
+typedef struct hb_graph hb_graph;   /* opaque handle */
+
+/* Per-handle counters, for measurement and tests. */
+typedef struct {
+    int64_t n, m;                /* nodes and arcs of the scanned graph */
+    int32_t log2m;               /* b: p = 2^b registers per counter */
+    int32_t t;                   /* iterations executed so far */
+    int64_t last_changed;        /* nodes whose counter changed in the last iteration */
+    int64_t last_nodes;          /* nodes recomputed in the last iteration */
+    int64_t last_arcs;           /* arcs scanned in the last iteration (arc-updates) */
+    int64_t total_arcs;          /* arcs scanned since the counters were initialised */
+    int32_t last_sparse;         /* 1 if the last iteration used the changed-node frontier */
+    int32_t converged;           /* 1 once an iteration changed nothing */
+    int64_t device_bytes;        /* bytes of device memory the handle holds */
+    int64_t launches;            /* kernels launched by the handle since its creation */
+    int64_t kernel_launches;     /* HB_PROFILE: gather-kernel launches timed since the last reset */
+    double kernel_ms;            /* HB_PROFILE: their summed duration (CUDA events, same stream) */
+    double kernel_bytes;         /* HB_PROFILE: their summed algorithmic bytes (see below) */
+} hb_info;
+
+/* Algorithmic bytes of one gather-kernel launch, counted from the nodes it
+ * recomputes (N), their arcs (A) and the nodes that changed (C):
+ *     A * (4 + p)                 target index + successor counter per arc
+ *   + N * (8 + 2p + 1)            offset, own counter read, counter write, flag
+ *   + N * 4                       list entry (frontier iterations only)
+ *   + C * (4 + 32 + 2e)           list append, sumd/harm read+write, cached
+ *                                 estimate read+write (e = 8, or 4 in FP32) */
+
+/* Fill *opt with the defaults: flags 0, HB_FRONTIER_AUTO, max_steps 1<<20,
+ * stream NULL. */
+void hb_default_options(hb_options *opt);
+
+/* Build a handle for the CSR graph (offsets: n+1 int64, targets: m int32)
+ * and initialise every counter with add(c[v], v) (Sec. 4.2, Algorithm 2
+ * first loop), v hashed by SplitMix64 seeded with `seed`; the register
+ * index is the top log2m bits of the hash and the register value rho+ of
+ * the remaining bits (Sec. 4.1, Algorithm 1), capped at 64-log2m.
+ * log2m must lie in [4, 12] (p >= 16 as Sec. 4.1 assumes; 4096 is the
+ * largest p of Sec. 8).  The graph is validated on the device; a malformed
+ * graph gives HB_ERR_INVALID and no handle.  opt may be NULL (defaults). */
+hb_status hb_create(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                    int log2m, uint64_t seed, const hb_options *opt, hb_graph **out);
+
+/* Same with int32 offsets (graphs with m < 2^31). */
+hb_status hb_create32(const int32_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                      int log2m, uint64_t seed, const hb_options *opt, hb_graph **out);
+
+/* One iteration of Algorithm 2 at the current loop index t: every counter
+ * becomes the register-wise max of itself and its successors' counters,
+ * read from the previous iteration only (Jacobi, as the update file of
+ * Sec. 4.2 implies).  For each node whose counter changed, with
+ * d = size(new) - size(old) and the new layer at distance t+1:
+ *     sumd[v] += (t+1) * d,   harm[v] += d / (t+1)          (Sec. 5)
+ * *n_changed (may be NULL) receives the number of changed nodes.
+ * Calling it after convergence is allowed and changes nothing. */
+hb_status hb_step(hb_graph *g, int64_t *n_changed);
+
+/* Iterate until an iteration changes no counter (Sec. 4.2), at most
+ * max_steps iterations in total.  *steps (may be NULL) receives the number
+ * of iterations executed since initialisation, the final unchanged one
+ * included.  Returns HB_ERR_NOT_CONVERGED if the cap was reached first;
+ * the state is then valid and more steps may follow. */
+hb_status hb_run_to_fixpoint(hb_graph *g, int32_t *steps);
+
+/* Sec. 3 centralities from the Sec. 5 accumulators, n doubles each, in the
+ * caller's node order; any pointer may be NULL:
+ *     reachable = size(c[v])   (coreachable set on the original graph, v included)
+ *     closeness = 1/sumd[v], or 0 if sumd[v] == 0 (nothing else coreaches v)
+ *     lin       = reachable^2 / sumd[v], or 1 if sumd[v] == 0
+ *     harmonic  = harm[v] */
+hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic,
+                              double *lin, double *reachable);
+
+/* The raw accumulators sumd and harm (n doubles each, may be NULL). */
+hb_status hb_get_accumulators(hb_graph *g, double *sumd, double *harm);
+
+/* The current counters, n*p bytes, row v = node v's p registers. */
+hb_status hb_get_registers(hb_graph *g, uint8_t *out);
+
+/* Frontier of the last iteration, n bytes each, may be NULL:
+ * changed[v] = 1 if v's counter changed in it; must_check[v] = 1 if some
+ * successor of v changed in it, i.e. v may change in the next iteration
+ * (the modification tracking of Sec. 5 / 5.1). */
+hb_status hb_get_frontier(hb_graph *g, uint8_t *changed, uint8_t *must_check);
+
+/* Counters of the handle. */
+hb_status hb_get_info(hb_graph *g, hb_info *info);
+
+/* Re-initialise counters, accumulators and t (same graph, new seed). */
+hb_status hb_reset(hb_graph *g, uint64_t seed);
+
+/* Checkpoint: write t, counters, last frontier and accumulators (and the
+ * graph) to a file; hb_load rebuilds a handle that continues exactly
+ * where the saved one stopped. */
+hb_status hb_save(hb_graph *g, const char *path);
+hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out);
+
+/* Free every resource of the handle (NULL is allowed). */
+void hb_destroy(hb_graph *g);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *hb_last_error(void);
+
+/* Library version string. */
+const char *hb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYPERBALL_H */

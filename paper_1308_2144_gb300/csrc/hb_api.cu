@@ -1,0 +1,717 @@
+// hb_api.cu -- the C ABI of include/hyperball.h: argument checks, device
+// memory, the create-time pipeline (upload, validate, transpose, degree
+// relabelling, reverse CSR, plans, init) and the host side of iterations.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hb_internal.cuh"
+
+#include "../../include/hyperball.h"
+
+using namespace hb;
+
+namespace {
+
+thread_local std::string g_err;
+
+hb_status fail(hb_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+hb_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(HB_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// alpha_p of Flajolet, Fusy, Gandouet & Meunier (2007), the constant of
+// Sec. 4.1's size() (Algorithm 1).
+double hll_alpha(int p) {
+    switch (p) {
+        case 16: return 0.673;
+        case 32: return 0.697;
+        case 64: return 0.709;
+        default: return 0.7213 / (1.0 + 1.079 / (double)p);
+    }
+}
+
+struct DevMem {
+    std::vector<void *> blocks;
+    size_t bytes = 0;
+    cudaError_t err = cudaSuccess;
+    template <class T>
+    T *alloc(size_t count) {
+        if (err != cudaSuccess) return nullptr;
+        void *p = nullptr;
+        size_t sz = count * sizeof(T);
+        if (sz == 0) sz = 16;
+        err = cudaMalloc(&p, sz);
+        if (err != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        blocks.push_back(p);
+        bytes += sz;
+        return static_cast<T *>(p);
+    }
+    void release(void *p) {
+        for (size_t i = 0; i < blocks.size(); ++i)
+            if (blocks[i] == p) { cudaFree(p); blocks.erase(blocks.begin() + (long)i); return; }
+    }
+    void free_all() {
+        for (void *p : blocks) cudaFree(p);
+        blocks.clear();
+    }
+};
+
+}  // namespace
+
+struct hb_graph {
+    int64_t n = 0, m = 0;
+    int b = 4;
+    Layout y{};
+    uint64_t seed = 0;
+    hb_options opt{};
+    cudaStream_t s = nullptr;
+    bool fp32 = false, relabel = true, broken = false;
+    int step_grid = 0;
+    DevMem mem;
+    int64_t *off = nullptr;
+    int32_t *tgt = nullptr;
+    int64_t *roff = nullptr;
+    int32_t *rtgt = nullptr;
+    int32_t *perm = nullptr, *inv = nullptr;
+    Counters *ctr = nullptr;
+    Counters *ctr_host = nullptr;
+    int64_t seg_count[kSegs] = {0};
+    int64_t n_pos = 0;
+    int64_t heavy_total = 0;
+    StepArgs a{};
+    // host bookkeeping
+    int32_t t = 0;
+    bool converged = false;
+    int64_t last_changed = 0, last_nodes = 0, last_arcs = 0, total_arcs = 0;
+    int32_t last_sparse = 0;
+    int launches = 0;
+    bool profile = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int64_t kernel_launches = 0;
+    double kernel_ms = 0.0, kernel_bytes = 0.0;
+
+    ~hb_graph() {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        if (ctr_host) cudaFreeHost(ctr_host);
+        mem.free_all();
+    }
+};
+
+namespace {
+
+void default_opts(hb_options *o) {
+    o->flags = 0;
+    o->frontier = HB_FRONTIER_AUTO;
+    o->max_steps = 1 << 20;
+    o->stream = nullptr;
+}
+
+// Copy `bytes` from a host or device source into device memory.
+cudaError_t to_device(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyHostToDevice, s);
+}
+
+// Deliver a device result into a caller buffer (host or device).
+cudaError_t to_caller(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0 || !dst) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyDeviceToHost, s);
+}
+
+// Everything after the scanned CSR (g->off, g->tgt, owned) is in place:
+// segments, reverse CSR, state buffers, plans.  Does not initialise.
+hb_status finish_setup(hb_graph *g) {
+    cudaStream_t s = g->s;
+    const int64_t n = g->n, m = g->m;
+    const int P = 1 << g->b;
+    cudaError_t e = count_degree_segments(g->off, n, g->y, g->seg_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "degree segments");
+    int64_t seg_begin[kSegs];
+    int64_t run = 0;
+    for (int k = 0; k < kSegs; ++k) { seg_begin[k] = run; run += g->seg_count[k]; }
+    g->n_pos = run;
+    e = heavy_chunk_total(g->off, n, g->y, &g->heavy_total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "heavy chunks");
+
+    const bool want_reverse = g->opt.frontier == HB_FRONTIER_AUTO || g->opt.frontier == HB_FRONTIER_PUSH;
+    DevMem &M = g->mem;
+    if (want_reverse) {
+        g->roff = M.alloc<int64_t>(n + 1);
+        g->rtgt = M.alloc<int32_t>(m);
+        if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (reverse CSR)");
+        e = transpose_csr(g->off, g->tgt, n, m, g->roff, g->rtgt, s);
+        if (e != cudaSuccess) return cuda_fail(e, "reverse CSR");
+    }
+    StepArgs &a = g->a;
+    a = StepArgs{};
+    a.off = g->off;
+    a.tgt = g->tgt;
+    a.roff = g->roff;
+    a.rtgt = g->rtgt;
+    a.has_reverse = want_reverse ? 1 : 0;
+    a.regs[0] = M.alloc<uint8_t>((size_t)n * P);
+    a.regs[1] = M.alloc<uint8_t>((size_t)n * P);
+    a.sumd = M.alloc<double>(n);
+    a.harm = M.alloc<double>(n);
+    a.ecache = g->fp32 ? (void *)M.alloc<float>(n) : (void *)M.alloc<double>(n);
+    a.changed = M.alloc<uint8_t>(n);
+    a.mustbits = M.alloc<uint32_t>((n + 31) / 32 + 1);
+    a.clist[0] = M.alloc<int32_t>(n);
+    a.clist[1] = M.alloc<int32_t>(n);
+    const int64_t big_cap = (m / kBigRdeg + 1) < n ? (m / kBigRdeg + 1) : (n > 0 ? n : 1);
+    a.biglist[0] = M.alloc<int32_t>(big_cap);
+    a.biglist[1] = M.alloc<int32_t>(big_cap);
+    a.slist = M.alloc<int32_t>(g->n_pos);
+    Plan *plans = M.alloc<Plan>(2);
+    a.plan_dense = plans;
+    a.plan_sparse = plans + 1;
+    a.owner_dense = M.alloc<int32_t>(g->heavy_total);
+    a.owner_sparse = M.alloc<int32_t>(g->heavy_total);
+    a.cstart_dense = M.alloc<int64_t>(g->seg_count[0] + 1);
+    a.cstart_sparse = M.alloc<int64_t>(g->seg_count[0] + 1);
+    a.partial = M.alloc<uint8_t>((size_t)g->heavy_total * P);
+    a.arrive = M.alloc<uint32_t>(g->seg_count[0] + 1);
+    g->ctr = M.alloc<Counters>(1);
+    a.ctr = g->ctr;
+    double *lc64 = M.alloc<double>(P + 1);
+    float *lc32 = M.alloc<float>(P + 1);
+    a.lc64 = lc64;
+    a.lc32 = lc32;
+    int32_t *dense_list = nullptr;
+    if (!g->relabel) dense_list = M.alloc<int32_t>(g->n_pos);
+    if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (HyperBall state)");
+    if (cudaMallocHost(&g->ctr_host, sizeof(Counters)) != cudaSuccess)
+        return fail(HB_ERR_OOM, "out of pinned host memory");
+
+    const double alpha = hll_alpha(P);
+    a.alpha_pp = alpha * (double)P * (double)P;
+    a.scale = std::ldexp(1.0, g->b - 64);
+    a.c32 = (float)std::ldexp(a.alpha_pp, 64 - g->b);
+    // small-range switch: raw estimate <= 5p/2  <=>  X >= alpha 2^64 * 2/5
+    const unsigned __int128 Y = (unsigned __int128)std::ldexp(alpha, 64);
+    a.thr_x = (unsigned long long)((2 * Y + 4) / 5);
+    a.n = n;
+    a.n_pos = g->n_pos;
+    a.m = m;
+    for (int k = 0; k < kSegs; ++k) {
+        a.seg_begin[k] = seg_begin[k];
+        a.seg_lo[k] = g->y.lo[k];
+        a.seg_hi[k] = g->y.hi[k];
+    }
+    a.b = g->b;
+    a.frontier = g->opt.frontier;
+    a.sparse_frac = 0.25;
+    cudaMemsetAsync(a.arrive, 0, sizeof(uint32_t) * (g->seg_count[0] + 1), s);
+    cudaMemsetAsync(a.changed, 0, (size_t)(n > 0 ? n : 1), s);
+    if (dense_list) {
+        int64_t *sb_dev = M.alloc<int64_t>(kSegs);
+        unsigned long long *fill = M.alloc<unsigned long long>(kSegs);
+        if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (dense list)");
+        e = cudaMemcpyAsync(sb_dev, seg_begin, sizeof(seg_begin), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = build_dense_list(g->off, n, g->y, sb_dev, dense_list, fill, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "dense list");
+        M.release(sb_dev);
+        M.release(fill);
+    }
+    a.dense_list = dense_list;
+    e = launch_lc_tables(lc64, lc32, P, s);
+    if (e != cudaSuccess) return cuda_fail(e, "estimator tables");
+    e = launch_dense_plan(a, g->y, g->seg_count, const_cast<Plan *>(a.plan_dense),
+                          const_cast<int32_t *>(a.owner_dense), const_cast<int64_t *>(a.cstart_dense), s);
+    if (e != cudaSuccess) return cuda_fail(e, "dense plan");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g->step_grid = sms * step_blocks_per_sm(g->b, g->fp32);
+    return HB_OK;
+}
+
+hb_status init_state(hb_graph *g, uint64_t seed) {
+    g->seed = seed;
+    cudaError_t e = launch_init(g->a, g->perm, seed, g->fp32, g->s);
+    g->launches += g->n > 0 ? 2 : 1;
+    g->kernel_launches = 0;
+    g->kernel_ms = g->kernel_bytes = 0.0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    if (e != cudaSuccess) return cuda_fail(e, "init");
+    g->t = 0;
+    g->converged = false;
+    g->last_changed = g->last_nodes = g->last_arcs = g->total_arcs = 0;
+    g->last_sparse = 0;
+    return HB_OK;
+}
+
+template <class OffT>
+hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
+                      uint64_t seed, const hb_options *opt, hb_graph **out) {
+    if (!out) return fail(HB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (log2m < kMinLog2m || log2m > kMaxLog2m)
+        return fail(HB_ERR_INVALID, "log2m must lie in [4, 12]");
+    if (n < 0 || n >= (int64_t)1 << 31) return fail(HB_ERR_INVALID, "n must lie in [0, 2^31)");
+    if (m < 0 || (sizeof(OffT) == 4 && m >= (int64_t)1 << 31))
+        return fail(HB_ERR_INVALID, "m out of range for the offset type");
+    if (!offsets) return fail(HB_ERR_INVALID, "offsets is NULL");
+    if (m > 0 && !targets) return fail(HB_ERR_INVALID, "targets is NULL");
+    hb_options o;
+    if (opt) o = *opt; else default_opts(&o);
+    if (o.max_steps <= 0) o.max_steps = 1 << 20;
+    if (o.frontier < HB_FRONTIER_AUTO || o.frontier > HB_FRONTIER_OFF)
+        return fail(HB_ERR_INVALID, "unknown frontier policy");
+    cudaError_t e = cudaFree(nullptr);   // make sure a context exists
+    if (e != cudaSuccess) return cuda_fail(e, "CUDA context");
+
+    hb_graph *g = new hb_graph();
+    g->n = n;
+    g->m = m;
+    g->b = log2m;
+    g->y = make_layout(log2m);
+    g->opt = o;
+    g->s = static_cast<cudaStream_t>(o.stream);
+    g->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
+    g->relabel = (o.flags & HB_NO_RELABEL) == 0;
+    g->profile = (o.flags & HB_PROFILE) != 0;
+    if (g->profile && (cudaEventCreate(&g->ev[0]) != cudaSuccess || cudaEventCreate(&g->ev[1]) != cudaSuccess)) {
+        delete g;
+        return fail(HB_ERR_CUDA, "cannot create profiling events");
+    }
+    cudaStream_t s = g->s;
+    DevMem &M = g->mem;
+
+    // 1. input CSR on the device (int64 offsets)
+    const bool borrow = (o.flags & HB_BORROW_DEVICE_PTRS) != 0;
+    const bool off_dev = is_device_ptr(offsets), tgt_dev = m == 0 || is_device_ptr(targets);
+    int64_t *in_off = nullptr;
+    int32_t *in_tgt = nullptr;
+    bool own_in_off = true, own_in_tgt = true;
+    if (sizeof(OffT) == 8 && borrow && off_dev) {
+        in_off = const_cast<int64_t *>(reinterpret_cast<const int64_t *>(offsets));
+        own_in_off = false;
+    } else {
+        in_off = M.alloc<int64_t>(n + 1);
+        if (sizeof(OffT) == 4) {
+            int32_t *tmp = M.alloc<int32_t>(n + 1);
+            if (M.err == cudaSuccess) {
+                e = to_device(tmp, offsets, sizeof(int32_t) * (n + 1), s);
+                if (e == cudaSuccess) e = widen_offsets(tmp, in_off, n + 1, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                M.release(tmp);
+            }
+        } else if (M.err == cudaSuccess) {
+            e = to_device(in_off, offsets, sizeof(int64_t) * (n + 1), s);
+        }
+    }
+    if (borrow && tgt_dev) {
+        in_tgt = const_cast<int32_t *>(targets);
+        own_in_tgt = false;
+    } else {
+        in_tgt = M.alloc<int32_t>(m);
+        if (M.err == cudaSuccess) e = to_device(in_tgt, targets, sizeof(int32_t) * m, s);
+    }
+    if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory (graph)"); }
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "graph upload"); }
+
+    // 2. validation
+    unsigned long long *err_dev = M.alloc<unsigned long long>(1);
+    unsigned long long err_host = 0;
+    if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaMemsetAsync(err_dev, 0, sizeof(unsigned long long), s);
+    e = validate_csr(in_off, in_tgt, n, m, err_dev, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err_host, err_dev, sizeof(err_host), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    M.release(err_dev);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "validation"); }
+    if (err_host) {
+        delete g;
+        std::string why;
+        if (err_host & 1) why += " offsets[0] != 0;";
+        if (err_host & 2) why += " offsets[n] != m;";
+        if (err_host & 4) why += " offsets decrease;";
+        if (err_host & 8) why += " a target lies outside [0, n);";
+        return fail(HB_ERR_INVALID, "malformed CSR:" + why);
+    }
+
+    // 3. transpose on request (Sec. 5: the in-centralities scan G^T)
+    if (o.flags & HB_TRANSPOSE) {
+        int64_t *toff = M.alloc<int64_t>(n + 1);
+        int32_t *ttgt = M.alloc<int32_t>(m);
+        if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory (transpose)"); }
+        e = transpose_csr(in_off, in_tgt, n, m, toff, ttgt, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { delete g; return cuda_fail(e, "transpose"); }
+        if (own_in_off) M.release(in_off);
+        if (own_in_tgt) M.release(in_tgt);
+        in_off = toff; in_tgt = ttgt; own_in_off = own_in_tgt = true;
+    }
+
+    // 4. degree-sorted relabelling
+    if (g->relabel) {
+        g->perm = M.alloc<int32_t>(n);
+        g->inv = M.alloc<int32_t>(n);
+        int64_t *noff = M.alloc<int64_t>(n + 1);
+        int32_t *ntgt = M.alloc<int32_t>(m);
+        if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory (relabel)"); }
+        e = degree_sort(in_off, n, g->perm, g->inv, s);
+        if (e == cudaSuccess) e = relabel_csr(in_off, in_tgt, n, m, g->perm, g->inv, noff, ntgt, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) { delete g; return cuda_fail(e, "relabel"); }
+        if (own_in_off) M.release(in_off);
+        if (own_in_tgt) M.release(in_tgt);
+        g->off = noff;
+        g->tgt = ntgt;
+    } else {
+        g->off = in_off;
+        g->tgt = in_tgt;
+    }
+
+    hb_status st = finish_setup(g);
+    if (st == HB_OK) st = init_state(g, seed);
+    if (st != HB_OK) { delete g; return st; }
+    *out = g;
+    return HB_OK;
+}
+
+hb_status check(hb_graph *g) {
+    if (!g) return fail(HB_ERR_INVALID, "handle is NULL");
+    if (g->broken) return fail(HB_ERR_STATE, "handle unusable after a CUDA error");
+    return HB_OK;
+}
+
+const uint8_t *current_regs(hb_graph *g) { return g->a.regs[g->t & 1]; }
+
+}  // namespace
+
+extern "C" {
+
+void hb_default_options(hb_options *opt) {
+    if (opt) default_opts(opt);
+}
+
+hb_status hb_create(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
+                    uint64_t seed, const hb_options *opt, hb_graph **out) {
+    g_err.clear();
+    return create_impl<int64_t>(offsets, targets, n, m, log2m, seed, opt, out);
+}
+
+hb_status hb_create32(const int32_t *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
+                      uint64_t seed, const hb_options *opt, hb_graph **out) {
+    g_err.clear();
+    return create_impl<int32_t>(offsets, targets, n, m, log2m, seed, opt, out);
+}
+
+hb_status hb_step(hb_graph *g, int64_t *n_changed) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    cudaError_t e = launch_iteration(g->a, g->y, g->fp32, g->step_grid, g->s,
+                                     g->profile ? g->ev[0] : nullptr, g->profile ? g->ev[1] : nullptr,
+                                     &g->launches);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    if (e != cudaSuccess) {
+        g->broken = true;
+        return cuda_fail(e, "step");
+    }
+    const Counters &c = *g->ctr_host;
+    g->t = c.steps_done;
+    g->last_changed = (int64_t)c.n_changed;
+    g->last_sparse = c.mode;
+    if (c.mode == 1) {
+        int64_t nodes = 0;
+        for (int k = 0; k < kSegs; ++k) nodes += (int64_t)c.fill[k];
+        g->last_nodes = nodes;
+        g->last_arcs = (int64_t)c.arcs;
+    } else {
+        g->last_nodes = g->n_pos;
+        g->last_arcs = g->m;
+    }
+    g->total_arcs += g->last_arcs;
+    if (c.n_changed == 0) g->converged = true;
+    if (g->profile) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]) == cudaSuccess) {
+            const double p = (double)(1 << g->b);
+            const double esz = g->fp32 ? 4.0 : 8.0;
+            g->kernel_ms += ms;
+            g->kernel_launches += 1;
+            g->kernel_bytes += (double)g->last_arcs * (4.0 + p) +
+                               (double)g->last_nodes * (8.0 + 2.0 * p + 1.0 + (c.mode == 1 ? 4.0 : 0.0)) +
+                               (double)c.n_changed * (4.0 + 32.0 + 2.0 * esz);
+        }
+    }
+    if (n_changed) *n_changed = (int64_t)c.n_changed;
+    return HB_OK;
+}
+
+hb_status hb_run_to_fixpoint(hb_graph *g, int32_t *steps) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    while (!g->converged && g->t < g->opt.max_steps) {
+        st = hb_step(g, nullptr);
+        if (st != HB_OK) return st;
+    }
+    if (steps) *steps = g->t;
+    if (!g->converged) return fail(HB_ERR_NOT_CONVERGED, "max_steps reached before the fixpoint");
+    return HB_OK;
+}
+
+hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic, double *lin,
+                              double *reachable) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    const int64_t n = g->n;
+    double *outs[4] = {closeness, harmonic, lin, reachable};
+    double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    DevMem tmp;
+    for (int k = 0; k < 4; ++k) {
+        if (!outs[k]) continue;
+        dev[k] = is_device_ptr(outs[k]) ? outs[k] : tmp.alloc<double>(n);
+    }
+    if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = launch_finalize(g->a, current_regs(g), g->perm, g->fp32, dev[0], dev[1], dev[2],
+                                    dev[3], g->s);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (outs[k] && dev[k] != outs[k]) e = to_caller(outs[k], dev[k], sizeof(double) * n, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "centralities");
+    return HB_OK;
+}
+
+hb_status hb_get_accumulators(hb_graph *g, double *sumd, double *harm) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    const int64_t n = g->n;
+    double *outs[2] = {sumd, harm};
+    const double *src[2] = {g->a.sumd, g->a.harm};
+    DevMem tmp;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (!outs[k]) continue;
+        double *d = is_device_ptr(outs[k]) ? outs[k] : tmp.alloc<double>(n);
+        if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+        e = launch_gather_f64(src[k], g->inv, n, d, g->s);
+        if (e == cudaSuccess && d != outs[k]) e = to_caller(outs[k], d, sizeof(double) * n, g->s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "accumulators");
+    return HB_OK;
+}
+
+hb_status hb_get_registers(hb_graph *g, uint8_t *out) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    const size_t bytes = (size_t)g->n << g->b;
+    if (bytes == 0) return HB_OK;
+    if (!out) return fail(HB_ERR_INVALID, "out is NULL");
+    DevMem tmp;
+    uint8_t *d = is_device_ptr(out) ? out : tmp.alloc<uint8_t>(bytes);
+    if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = launch_gather_rows(current_regs(g), g->inv, g->n, 1 << g->b, d, g->s);
+    if (e == cudaSuccess && d != out) e = to_caller(out, d, bytes, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "registers");
+    return HB_OK;
+}
+
+hb_status hb_get_frontier(hb_graph *g, uint8_t *changed, uint8_t *must_check) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    const int64_t n = g->n;
+    DevMem tmp;
+    uint8_t *dc = changed ? (is_device_ptr(changed) ? changed : tmp.alloc<uint8_t>(n)) : nullptr;
+    uint8_t *dm = must_check ? (is_device_ptr(must_check) ? must_check : tmp.alloc<uint8_t>(n)) : nullptr;
+    if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = launch_frontier_out(g->a, g->inv, dc, dm, g->s);
+    if (e == cudaSuccess && dc && dc != changed) e = to_caller(changed, dc, n, g->s);
+    if (e == cudaSuccess && dm && dm != must_check) e = to_caller(must_check, dm, n, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "frontier");
+    return HB_OK;
+}
+
+hb_status hb_get_info(hb_graph *g, hb_info *info) {
+    if (!g || !info) return fail(HB_ERR_INVALID, "NULL argument");
+    info->n = g->n;
+    info->m = g->m;
+    info->log2m = g->b;
+    info->t = g->t;
+    info->last_changed = g->last_changed;
+    info->last_nodes = g->last_nodes;
+    info->last_arcs = g->last_arcs;
+    info->total_arcs = g->total_arcs;
+    info->last_sparse = g->last_sparse;
+    info->converged = g->converged ? 1 : 0;
+    info->device_bytes = (int64_t)g->mem.bytes;
+    info->launches = g->launches;
+    info->kernel_launches = g->kernel_launches;
+    info->kernel_ms = g->kernel_ms;
+    info->kernel_bytes = g->kernel_bytes;
+    return HB_OK;
+}
+
+hb_status hb_reset(hb_graph *g, uint64_t seed) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    return init_state(g, seed);
+}
+
+// ------------------------------------------------------------ checkpoint --
+
+namespace {
+constexpr uint64_t kMagic = 0x31304c4c41425948ULL;   // "HYBALL01"
+
+struct SaveHeader {
+    uint64_t magic;
+    int64_t n, m;
+    int32_t b, fp32, relabel, t;
+    uint64_t seed;
+    int32_t converged, frontier;
+    int64_t total_arcs;
+};
+
+bool write_dev(FILE *f, const void *dev, size_t bytes, cudaStream_t s) {
+    std::vector<char> buf(bytes);
+    if (bytes && cudaMemcpyAsync(buf.data(), dev, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return false;
+    return fwrite(buf.data(), 1, bytes, f) == bytes;
+}
+
+bool read_dev(FILE *f, void *dev, size_t bytes, cudaStream_t s) {
+    std::vector<char> buf(bytes);
+    if (fread(buf.data(), 1, bytes, f) != bytes) return false;
+    if (bytes && cudaMemcpyAsync(dev, buf.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return false;
+    return cudaStreamSynchronize(s) == cudaSuccess;
+}
+}  // namespace
+
+hb_status hb_save(hb_graph *g, const char *path) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    if (!path) return fail(HB_ERR_INVALID, "path is NULL");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(HB_ERR_INVALID, std::string("cannot open ") + path);
+    SaveHeader h{kMagic, g->n, g->m, g->b, g->fp32, g->relabel, g->t, g->seed,
+                 g->converged, g->opt.frontier, g->total_arcs};
+    const size_t P = (size_t)1 << g->b;
+    const size_t n = (size_t)g->n;
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1;
+    ok = ok && write_dev(f, g->off, sizeof(int64_t) * (n + 1), g->s);
+    ok = ok && write_dev(f, g->tgt, sizeof(int32_t) * g->m, g->s);
+    if (g->relabel) {
+        ok = ok && write_dev(f, g->perm, sizeof(int32_t) * n, g->s);
+        ok = ok && write_dev(f, g->inv, sizeof(int32_t) * n, g->s);
+    }
+    ok = ok && write_dev(f, current_regs(g), n * P, g->s);
+    ok = ok && write_dev(f, g->a.sumd, sizeof(double) * n, g->s);
+    ok = ok && write_dev(f, g->a.harm, sizeof(double) * n, g->s);
+    ok = ok && write_dev(f, g->a.ecache, (g->fp32 ? sizeof(float) : sizeof(double)) * n, g->s);
+    ok = ok && write_dev(f, g->a.changed, n, g->s);
+    ok = ok && write_dev(f, g->ctr, sizeof(Counters), g->s);
+    Counters c{};
+    if (ok) ok = cudaMemcpy(&c, g->ctr, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess;
+    // the last iteration's changed lists drive the next frontier
+    const int last = (g->t + 1) & 1;
+    ok = ok && write_dev(f, g->a.clist[last], sizeof(int32_t) * c.n_changed, g->s);
+    ok = ok && write_dev(f, g->a.biglist[last], sizeof(int32_t) * c.n_big, g->s);
+    fclose(f);
+    if (!ok) return fail(HB_ERR_CUDA, "checkpoint write failed");
+    return HB_OK;
+}
+
+hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
+    g_err.clear();
+    if (!path || !out) return fail(HB_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(HB_ERR_INVALID, std::string("cannot open ") + path);
+    SaveHeader h{};
+    if (fread(&h, sizeof(h), 1, f) != 1 || h.magic != kMagic) {
+        fclose(f);
+        return fail(HB_ERR_INVALID, "not a HyperBall checkpoint");
+    }
+    hb_options o;
+    if (opt) o = *opt; else default_opts(&o);
+    if (o.max_steps <= 0) o.max_steps = 1 << 20;
+    cudaFree(nullptr);
+    hb_graph *g = new hb_graph();
+    g->n = h.n; g->m = h.m; g->b = h.b; g->y = make_layout(h.b);
+    g->opt = o;
+    g->opt.frontier = h.frontier;
+    g->s = static_cast<cudaStream_t>(o.stream);
+    g->fp32 = h.fp32 != 0;
+    g->relabel = h.relabel != 0;
+    const size_t P = (size_t)1 << g->b, n = (size_t)g->n;
+    DevMem &M = g->mem;
+    g->off = M.alloc<int64_t>(n + 1);
+    g->tgt = M.alloc<int32_t>(g->m);
+    if (g->relabel) { g->perm = M.alloc<int32_t>(n); g->inv = M.alloc<int32_t>(n); }
+    bool ok = M.err == cudaSuccess;
+    ok = ok && read_dev(f, g->off, sizeof(int64_t) * (n + 1), g->s);
+    ok = ok && read_dev(f, g->tgt, sizeof(int32_t) * g->m, g->s);
+    if (ok && g->relabel) {
+        ok = read_dev(f, g->perm, sizeof(int32_t) * n, g->s) && read_dev(f, g->inv, sizeof(int32_t) * n, g->s);
+    }
+    if (!ok) { fclose(f); delete g; return fail(HB_ERR_INVALID, "truncated checkpoint or no memory"); }
+    hb_status st = finish_setup(g);
+    if (st == HB_OK) st = init_state(g, h.seed);
+    if (st != HB_OK) { fclose(f); delete g; return st; }
+    // restore the state of iteration t: counters into both buffers
+    g->t = h.t;
+    g->converged = h.converged != 0;
+    g->total_arcs = h.total_arcs;
+    ok = read_dev(f, g->a.regs[h.t & 1], n * P, g->s);
+    if (ok && n * P) ok = cudaMemcpy(g->a.regs[(h.t + 1) & 1], g->a.regs[h.t & 1], n * P,
+                                     cudaMemcpyDeviceToDevice) == cudaSuccess;
+    ok = ok && read_dev(f, g->a.sumd, sizeof(double) * n, g->s);
+    ok = ok && read_dev(f, g->a.harm, sizeof(double) * n, g->s);
+    ok = ok && read_dev(f, g->a.ecache, (g->fp32 ? sizeof(float) : sizeof(double)) * n, g->s);
+    ok = ok && read_dev(f, g->a.changed, n, g->s);
+    ok = ok && read_dev(f, g->ctr, sizeof(Counters), g->s);
+    Counters c{};
+    if (ok) ok = cudaMemcpy(&c, g->ctr, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess;
+    const int last = (h.t + 1) & 1;
+    ok = ok && read_dev(f, g->a.clist[last], sizeof(int32_t) * c.n_changed, g->s);
+    ok = ok && read_dev(f, g->a.biglist[last], sizeof(int32_t) * c.n_big, g->s);
+    fclose(f);
+    if (!ok) { delete g; return fail(HB_ERR_INVALID, "truncated checkpoint"); }
+    *out = g;
+    return HB_OK;
+}
+
+void hb_destroy(hb_graph *g) {
+    if (!g) return;
+    if (g->s) cudaStreamSynchronize(g->s);
+    else cudaDeviceSynchronize();
+    delete g;
+}
+
+const char *hb_last_error(void) { return g_err.c_str(); }
+
+const char *hb_version(void) { return "hyperball-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

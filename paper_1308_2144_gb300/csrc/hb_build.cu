@@ -1,0 +1,350 @@
+// hb_build.cu -- create-time device work: CSR validation, offset widening,
+// exclusive scans, transposition (Sec. 5: HyperBall runs on G^T for the
+// in-centralities), and the degree-sorted relabelling that lays nodes out
+// for the step kernel (heavy nodes first, then light degree classes).
+#include <cstdio>
+
+#include "hb_internal.cuh"
+
+namespace hb {
+
+namespace {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void scan_tile_sums(const int64_t *in, int64_t N, int64_t *sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t k = base + (int64_t)threadIdx.x * kScanItems + i;
+        if (k < N) s += in[k];
+    }
+    int64_t ex;
+    int64_t tot = block_excl_scan(s, ex);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void scan_tile_apply(const int64_t *in, int64_t *out, int64_t N, const int64_t *offs) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t k = base + (int64_t)threadIdx.x * kScanItems + i;
+        v[i] = k < N ? in[k] : 0;
+        s += v[i];
+    }
+    int64_t ex;
+    block_excl_scan(s, ex);
+    int64_t run = ex + (offs ? offs[blockIdx.x] : 0);
+    for (int i = 0; i < kScanItems; ++i) {
+        int64_t k = base + (int64_t)threadIdx.x * kScanItems + i;
+        if (k < N) out[k] = run;
+        run += v[i];
+    }
+}
+
+// ------------------------------------------------------------ validate --
+
+__global__ void validate_kernel(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                                unsigned long long *err) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        if (off[0] != 0) atomicOr(err, 1ULL);
+        if (off[n] != m) atomicOr(err, 2ULL);
+    }
+    for (int64_t v = tid; v < n; v += stride)
+        if (off[v + 1] < off[v]) { atomicOr(err, 4ULL); break; }
+    for (int64_t e = tid; e < m; e += stride) {
+        int32_t w = tgt[e];
+        if (w < 0 || (int64_t)w >= n) { atomicOr(err, 8ULL); break; }
+    }
+}
+
+__global__ void widen_kernel(const int32_t *in, int64_t *out, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int64_t)in[i];
+}
+
+// ----------------------------------------------------------- transpose --
+
+// Node u with off[u] <= e < off[u+1] (the last such u when degrees are 0).
+__device__ __forceinline__ int64_t arc_source(const int64_t *off, int64_t n, int64_t e) {
+    int64_t lo = 0, hi = n;   // off[lo] <= e < off[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (off[mid] <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void count_targets(const int32_t *tgt, int64_t m, unsigned long long *cnt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[tgt[e]], 1ULL);
+}
+
+__global__ void scatter_transpose(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                                  unsigned long long *cursor, int32_t *ttgt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = arc_source(off, n, e);
+        unsigned long long pos = atomicAdd(&cursor[tgt[e]], 1ULL);
+        ttgt[pos] = (int32_t)u;
+    }
+}
+
+// -------------------------------------------------------- degree sort --
+// Stable partition of nodes into descending degree buckets: quarter
+// octaves of deg-1, so every power-of-two class bound is a bucket bound;
+// degree-0 nodes last.
+
+constexpr int kBuckets = 128;
+constexpr int kPartThreads = 256;
+constexpr int kPartRounds = 16;
+constexpr int kPartTile = kPartThreads * kPartRounds;
+
+__device__ __forceinline__ int degree_bucket(int64_t d) {
+    if (d <= 0) return 120;
+    uint64_t x = (uint64_t)(d - 1);
+    int b;
+    if (x < 8) b = (int)x;
+    else {
+        int k = 63 - __clzll((long long)x);
+        int f = (int)((x >> (k - 2)) & 3);
+        b = 8 + (k - 3) * 4 + f;
+        if (b > 119) b = 119;
+    }
+    return 119 - b;   // larger degree, smaller key
+}
+
+__global__ void part_count(const int64_t *off, int64_t n, int64_t ntiles, int64_t *counts) {
+    __shared__ int hist[kBuckets];
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) hist[k] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < kPartTile; i += blockDim.x) {
+            int64_t v = tile * kPartTile + i;
+            if (v < n) atomicAdd(&hist[degree_bucket(off[v + 1] - off[v])], 1);
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) counts[(int64_t)k * ntiles + tile] = hist[k];
+        __syncthreads();
+    }
+}
+
+__global__ void part_scatter(const int64_t *off, int64_t n, int64_t ntiles, const int64_t *offs,
+                             int32_t *perm, int32_t *inv) {
+    __shared__ int64_t base[kBuckets];
+    __shared__ int wcnt[kPartThreads / 32][kBuckets];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) base[k] = offs[(int64_t)k * ntiles + tile];
+        __syncthreads();
+        for (int r = 0; r < kPartRounds; ++r) {
+            for (int k = threadIdx.x; k < (kPartThreads / 32) * kBuckets; k += blockDim.x)
+                (&wcnt[0][0])[k] = 0;
+            __syncthreads();
+            int64_t v = tile * kPartTile + (int64_t)r * kPartThreads + threadIdx.x;
+            bool valid = v < n;
+            int key = valid ? degree_bucket(off[v + 1] - off[v]) : -1;
+            unsigned peers = __match_any_sync(0xffffffffu, key);
+            int rank = __popc(peers & lanemask_lt());
+            if (valid && lane == __ffs(peers) - 1) wcnt[wid][key] = __popc(peers);
+            __syncthreads();
+            if (valid) {
+                int64_t pos = base[key] + rank;
+                for (int w = 0; w < wid; ++w) pos += wcnt[w][key];
+                perm[pos] = (int32_t)v;
+                inv[v] = (int32_t)pos;
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) {
+                int s = 0;
+                for (int w = 0; w < kPartThreads / 32; ++w) s += wcnt[w][k];
+                base[k] += s;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void permuted_degrees(const int64_t *off, const int32_t *perm, int64_t n, int64_t *deg) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = perm[v];
+        deg[v] = off[u + 1] - off[u];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) deg[n] = 0;
+}
+
+__global__ void relabel_arcs(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                             const int32_t *inv, const int64_t *noff, int32_t *ntgt) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t u = arc_source(off, n, e);
+        int64_t nu = inv[u];
+        ntgt[noff[nu] + (e - off[u])] = inv[tgt[e]];
+    }
+}
+
+// ------------------------------------------------------ degree segments --
+
+struct SegBounds {
+    int64_t lo[kSegs], hi[kSegs];
+};
+
+__device__ __forceinline__ int segment_of(int64_t d, const SegBounds &sb) {
+    for (int s = 0; s < kSegs; ++s)
+        if (d >= sb.lo[s] && d <= sb.hi[s]) return s;
+    return -1;   // degree 0
+}
+
+__global__ void seg_count_kernel(const int64_t *off, int64_t n, SegBounds sb, unsigned long long *cnt) {
+    __shared__ unsigned long long c[kSegs];
+    if (threadIdx.x < kSegs) c[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int s = segment_of(off[v + 1] - off[v], sb);
+        if (s >= 0) atomicAdd(&c[s], 1ULL);
+    }
+    __syncthreads();
+    if (threadIdx.x < kSegs && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], c[threadIdx.x]);
+}
+
+__global__ void dense_list_kernel(const int64_t *off, int64_t n, SegBounds sb, const int64_t *seg_begin,
+                                  int32_t *list, unsigned long long *fill) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int s = segment_of(off[v + 1] - off[v], sb);
+        if (s >= 0) {
+            unsigned long long pos = atomicAdd(&fill[s], 1ULL);
+            list[seg_begin[s] + (int64_t)pos] = (int32_t)v;
+        }
+    }
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+SegBounds bounds_of(const Layout &y) {
+    SegBounds sb;
+    for (int s = 0; s < kSegs; ++s) { sb.lo[s] = y.lo[s]; sb.hi[s] = y.hi[s]; }
+    return sb;
+}
+
+}  // namespace
+
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t N, cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    int64_t tiles = (N + kScanTile - 1) / kScanTile;
+    if (tiles == 1) {
+        scan_tile_apply<<<1, kScanThreads, 0, s>>>(in, out, N, nullptr);
+        return cudaGetLastError();
+    }
+    int64_t *sums = nullptr;
+    cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * tiles * 2, s);
+    if (e != cudaSuccess) return e;
+    scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, N, sums);
+    e = scan_exclusive_i64(sums, sums + tiles, tiles, s);
+    if (e == cudaSuccess) {
+        scan_tile_apply<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, N, sums + tiles);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(sums, s);
+    return e;
+}
+
+cudaError_t validate_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                         unsigned long long *err_dev, cudaStream_t s) {
+    validate_kernel<<<grid_for(n > m ? n : m, 256), 256, 0, s>>>(off, tgt, n, m, err_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaStream_t s) {
+    widen_kernel<<<grid_for(count, 256), 256, 0, s>>>(in, out, count);
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                          int64_t *toff, int32_t *ttgt, cudaStream_t s) {
+    unsigned long long *cnt = nullptr;
+    cudaError_t e = cudaMallocAsync(&cnt, sizeof(unsigned long long) * (n + 1), s);
+    if (e != cudaSuccess) return e;
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (n + 1), s);
+    if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, cnt);
+    e = scan_exclusive_i64(reinterpret_cast<int64_t *>(cnt), toff, n + 1, s);
+    if (e == cudaSuccess && m > 0) {
+        cudaMemcpyAsync(cnt, toff, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
+        scatter_transpose<<<grid_for(m, 256), 256, 0, s>>>(off, tgt, n, m, cnt, ttgt);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(cnt, s);
+    return e;
+}
+
+cudaError_t degree_sort(const int64_t *off, int64_t n, int32_t *perm, int32_t *inv, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int64_t ntiles = (n + kPartTile - 1) / kPartTile;
+    int64_t *counts = nullptr;
+    cudaError_t e = cudaMallocAsync(&counts, sizeof(int64_t) * kBuckets * ntiles * 2, s);
+    if (e != cudaSuccess) return e;
+    int g = (int)(ntiles < 152 * 8 ? ntiles : 152 * 8);
+    part_count<<<g, kPartThreads, 0, s>>>(off, n, ntiles, counts);
+    e = scan_exclusive_i64(counts, counts + kBuckets * ntiles, kBuckets * ntiles, s);
+    if (e == cudaSuccess) {
+        part_scatter<<<g, kPartThreads, 0, s>>>(off, n, ntiles, counts + kBuckets * ntiles, perm, inv);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(counts, s);
+    return e;
+}
+
+cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                        const int32_t *perm, const int32_t *inv, int64_t *noff, int32_t *ntgt,
+                        cudaStream_t s) {
+    int64_t *deg = nullptr;
+    cudaError_t e = cudaMallocAsync(&deg, sizeof(int64_t) * (n + 1), s);
+    if (e != cudaSuccess) return e;
+    permuted_degrees<<<grid_for(n + 1, 256), 256, 0, s>>>(off, perm, n, deg);
+    e = scan_exclusive_i64(deg, noff, n + 1, s);
+    if (e == cudaSuccess && m > 0) {
+        relabel_arcs<<<grid_for(m, 256), 256, 0, s>>>(off, tgt, n, m, inv, noff, ntgt);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(deg, s);
+    return e;
+}
+
+cudaError_t count_degree_segments(const int64_t *off, int64_t n, const Layout &y,
+                                  int64_t *seg_count_host, cudaStream_t s) {
+    unsigned long long *cnt = nullptr;
+    cudaError_t e = cudaMallocAsync(&cnt, sizeof(unsigned long long) * kSegs, s);
+    if (e != cudaSuccess) return e;
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kSegs, s);
+    if (n > 0) seg_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, bounds_of(y), cnt);
+    unsigned long long h[kSegs];
+    cudaMemcpyAsync(h, cnt, sizeof(h), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    cudaFreeAsync(cnt, s);
+    for (int k = 0; k < kSegs; ++k) seg_count_host[k] = (int64_t)h[k];
+    return e;
+}
+
+cudaError_t build_dense_list(const int64_t *off, int64_t n, const Layout &y,
+                             const int64_t *seg_begin, int32_t *list, unsigned long long *fill,
+                             cudaStream_t s) {
+    cudaMemsetAsync(fill, 0, sizeof(unsigned long long) * kSegs, s);
+    if (n > 0) dense_list_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, bounds_of(y), seg_begin, list, fill);
+    return cudaGetLastError();
+}
+
+}  // namespace hb

@@ -1,0 +1,308 @@
+// hb_internal.cuh -- types and device helpers shared by the library's
+// translation units.  Nothing here is part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hb {
+
+constexpr int kWarp = 32;
+constexpr int kMaxLog2m = 12;
+constexpr int kMinLog2m = 4;
+constexpr int kSegs = 7;          // segment 0: heavy nodes; 1..6: light classes
+constexpr int kArcsPerSlot = 4;   // class sizing: about this many arcs per lane slot
+constexpr int kStepThreads = 256;
+constexpr int kBigRdeg = 1024;    // changed nodes with more predecessors are pushed grid-wide
+
+// Per-p layout of a counter across the lanes of a warp.  A counter of P
+// bytes is CH 16-byte chunks; L lanes ("chunk lanes") hold one arc's
+// counter, CPL chunks each.  A team of T = L * S lanes works on one node,
+// its S slots taking every S-th arc.
+template <int LOG2P>
+struct Cfg {
+    static constexpr int P = 1 << LOG2P;
+    static constexpr int CH = P / 16;
+    static constexpr int LOGL = (LOG2P - 4) < 5 ? (LOG2P - 4) : 5;
+    static constexpr int L = 1 << LOGL;
+    static constexpr int CPL = CH / L;
+    static constexpr int LOGSMAX = 5 - LOGL;      // a full warp has 2^LOGSMAX slots
+    static constexpr int SMAX = 1 << LOGSMAX;
+    static constexpr int NLIGHT = LOGSMAX + 1;    // light classes, slots SMAX, SMAX/2, ..., 1
+    static constexpr int64_t CHUNK = 64 * SMAX;   // arcs per heavy-node chunk
+    static constexpr int64_t HEAVY = 2 * CHUNK;   // degree above which a node is split
+};
+
+// Host-side copy of the same numbers for a runtime log2m.
+struct Layout {
+    int log2m, P, logL, L, logSmax, nlight;
+    int64_t chunk, heavy;
+    // degree bounds of segment s: nodes with lo[s] <= deg <= hi[s]
+    int64_t lo[kSegs], hi[kSegs];
+};
+
+inline Layout make_layout(int log2m) {
+    Layout y{};
+    y.log2m = log2m;
+    y.P = 1 << log2m;
+    y.logL = (log2m - 4) < 5 ? (log2m - 4) : 5;
+    y.L = 1 << y.logL;
+    y.logSmax = 5 - y.logL;
+    y.nlight = y.logSmax + 1;
+    y.chunk = 64LL << y.logSmax;
+    y.heavy = 2 * y.chunk;
+    y.lo[0] = y.heavy + 1;
+    y.hi[0] = INT64_MAX;
+    for (int j = 0; j < y.nlight; ++j) {
+        int64_t s = 1LL << (y.logSmax - j);
+        y.hi[j + 1] = (j == 0) ? y.heavy : kArcsPerSlot * s;
+        y.lo[j + 1] = (j == y.nlight - 1) ? 1 : kArcsPerSlot * s / 2 + 1;
+    }
+    for (int s = y.nlight + 1; s < kSegs; ++s) { y.lo[s] = 1; y.hi[s] = 0; }
+    return y;
+}
+
+// Work plan of one step: which nodes are recomputed and how they map onto
+// warp items.  Segment s occupies list positions [seg_begin[s], seg_begin[s]
+// + count[s]).  Items [0, heavy_chunks) are chunks of segment-0 nodes; then
+// come the light segments, item_begin[j] .. item_begin[j+1]-1 for light
+// class j (segment j+1).
+struct Plan {
+    int64_t count[kSegs];
+    int64_t heavy_chunks;
+    int64_t item_begin[kSegs];
+    int64_t items;
+    int64_t nodes;
+    int64_t arcs;
+};
+
+// Device counters of the running step.  "cur" fields are produced by the
+// step being executed, "prev" fields are those of the step before.
+struct Counters {
+    unsigned long long n_changed;      // also the length of the changed list
+    unsigned long long push_arcs;      // sum of predecessor counts of changed nodes
+    unsigned long long n_big;          // changed nodes with > kBigRdeg predecessors
+    unsigned long long fill[kSegs];    // sparse list fill per segment
+    unsigned long long arcs;           // arcs scanned by the sparse list
+    unsigned long long prev_changed;
+    unsigned long long prev_push_arcs;
+    unsigned long long prev_big;
+    int32_t mode;                      // 0 = dense (all nodes), 1 = sparse (frontier list)
+    int32_t t;                         // loop index of the step being run
+    int32_t steps_done;                // iterations completed
+    int32_t converged;
+    unsigned long long err;            // nonzero: a device-side check failed
+};
+
+// Everything the step kernels read, passed by value.  Buffers that
+// alternate between iterations come in pairs indexed by the parity of the
+// loop index t, which the kernels read from the device counters, so the
+// same launch sequence serves every iteration (and can be captured once
+// into a CUDA graph).
+struct StepArgs {
+    const int64_t *off;
+    const int32_t *tgt;
+    const int64_t *roff;          // reverse CSR offsets (may be null)
+    const int32_t *rtgt;
+    uint8_t *regs[2];             // counters: iteration t reads regs[t&1], writes regs[(t+1)&1]
+    double *sumd;
+    double *harm;
+    void *ecache;                 // double[n] (FP64 form) or float[n] (FP32 form)
+    uint8_t *changed;             // 1 if the node changed in the last iteration
+    uint32_t *mustbits;           // frontier bitmap of the running iteration
+    int32_t *clist[2];            // changed nodes, appended by iteration t into clist[t&1]
+    int32_t *biglist[2];          // changed nodes with many predecessors, same pairing
+    const int32_t *dense_list;    // node of each dense position (null: position = node)
+    int32_t *slist;               // sparse list, laid out by segment
+    const Plan *plan_dense;
+    Plan *plan_sparse;
+    const int32_t *owner_dense;   // heavy chunk -> heavy index
+    const int64_t *cstart_dense;  // heavy index -> first chunk
+    int32_t *owner_sparse;
+    int64_t *cstart_sparse;
+    uint8_t *partial;             // per heavy chunk partial counter
+    uint32_t *arrive;             // per heavy index arrival count
+    Counters *ctr;
+    const double *lc64;           // p ln(p/V), V = 0..p
+    const float *lc32;
+    double alpha_pp;              // alpha_p p^2
+    float c32;                    // alpha_p p^2 2^(64-b) as float
+    unsigned long long thr_x;     // small-range switch in fixed point
+    double scale;                 // 2^(b-64)
+    int64_t n;
+    int64_t n_pos;                // nodes of nonzero degree
+    int64_t m;
+    int64_t seg_begin[kSegs];
+    int64_t seg_lo[kSegs];
+    int64_t seg_hi[kSegs];
+    int32_t b;
+    int32_t frontier;             // HB_FRONTIER_* policy
+    int32_t has_reverse;          // roff/rtgt present
+    double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
+};
+
+// ------------------------------------------------------------ helpers --
+
+__device__ __forceinline__ uint4 vmax16(uint4 a, uint4 b) {
+    return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z),
+                      __vmaxu4(a.w, b.w));
+}
+
+__device__ __forceinline__ bool ne16(uint4 a, uint4 b) {
+    return ((a.x ^ b.x) | (a.y ^ b.y) | (a.z ^ b.z) | (a.w ^ b.w)) != 0u;
+}
+
+__device__ __forceinline__ uint4 shfl_xor16(uint4 a, int o) {
+    a.x = __shfl_xor_sync(0xffffffffu, a.x, o);
+    a.y = __shfl_xor_sync(0xffffffffu, a.y, o);
+    a.z = __shfl_xor_sync(0xffffffffu, a.z, o);
+    a.w = __shfl_xor_sync(0xffffffffu, a.w, o);
+    return a;
+}
+
+// Counter loads: the read buffer does not change during a step.
+__device__ __forceinline__ uint4 ld_counter(const uint8_t *p) {
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// Targets are streamed once per step.
+__device__ __forceinline__ int32_t ld_stream(const int32_t *p) { return __ldcs(p); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// SplitMix64 output number v+1 of a generator seeded with `seed`
+// (Steele, Lea & Flood 2014): the node hash h of Sec. 4.1.
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t v) {
+    uint64_t z = seed + (v + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Register index = top b bits; rho+ = leading zeros of the other 64-b bits
+// plus one, capped at 64-b (Sec. 4.1, Algorithm 1).
+__device__ __forceinline__ void hash_to_register(uint64_t x, int b, uint32_t &idx, uint32_t &rho) {
+    idx = (uint32_t)(x >> (64 - b));
+    uint64_t rest = x << b;
+    uint32_t lz = rest == 0 ? 64u : (uint32_t)__clzll((long long)rest);
+    uint32_t r = lz + 1;
+    uint32_t cap = (uint32_t)(64 - b);
+    rho = r < cap ? r : cap;
+}
+
+// Zero-register count and fixed-point sum of 2^(64-b-M) over the 16 bytes
+// of one chunk.
+__device__ __forceinline__ void chunk_sums(uint4 c, int b, uint32_t &V, unsigned long long &S) {
+    const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+    const int sh = 64 - b;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            uint32_t M = (w[k] >> (8 * j)) & 0xffu;
+            if (M == 0) V += 1;
+            else S += 1ULL << (sh - (int)M);
+        }
+    }
+}
+
+// Sec. 4.1 estimate in double from (V, S): alpha_p p^2 / (V + S 2^(b-64)),
+// replaced by linear counting p ln(p/V) when it is <= 5p/2 and V > 0.  The
+// operations and their rounding follow the definition one by one.
+__device__ __forceinline__ double estimate64(uint32_t V, unsigned long long S, int P,
+                                             double alpha_pp, double scale, const double *lc64) {
+    double sum = __dadd_rn((double)V, __dmul_rn(__ull2double_rn(S), scale));
+    double E = __ddiv_rn(alpha_pp, sum);
+    if (E <= 2.5 * (double)P && V > 0) E = lc64[V];
+    return E;
+}
+
+// Precision form: the switch is taken on the exact fixed-point sum
+// X = V 2^(64-b) + S (X >= thr_x <=> raw estimate <= 5p/2), the estimate in
+// FP32.  V == P (an empty counter) gives 0.
+__device__ __forceinline__ float estimate32(uint32_t V, unsigned long long S, int P, int b,
+                                            float c32, unsigned long long thr_x, const float *lc32) {
+    if (V == (uint32_t)P) return 0.0f;
+    unsigned long long X = ((unsigned long long)V << (64 - b)) + S;
+    if (V > 0 && X >= thr_x) return lc32[V];
+    return __fdiv_rn(c32, __ull2float_rn(X));
+}
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the block total.
+__device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t &excl) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t wtotal;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    int64_t inc = warp_incl_scan(x);
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = lane < nw ? wsum[lane] : 0;
+        int64_t wi = warp_incl_scan(w);
+        if (lane < nw) wsum[lane] = wi - w;
+        if (lane == 31) wtotal = wi;   // nw <= 32
+    }
+    __syncthreads();
+    excl = inc - x + wsum[wid];
+    int64_t total = wtotal;
+    __syncthreads();
+    return total;
+}
+
+// ----------------------------------------------------------- launchers --
+// (defined in hb_build.cu / hb_step.cu; all take the stream last)
+
+cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t N, cudaStream_t s);
+cudaError_t validate_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                         unsigned long long *err_dev, cudaStream_t s);
+cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaStream_t s);
+cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                          int64_t *toff, int32_t *ttgt, cudaStream_t s);
+cudaError_t degree_sort(const int64_t *off, int64_t n, int32_t *perm, int32_t *inv, cudaStream_t s);
+cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                        const int32_t *perm, const int32_t *inv, int64_t *noff, int32_t *ntgt,
+                        cudaStream_t s);
+cudaError_t count_degree_segments(const int64_t *off, int64_t n, const Layout &y,
+                                  int64_t *seg_count_host, cudaStream_t s);
+cudaError_t build_dense_list(const int64_t *off, int64_t n, const Layout &y,
+                             const int64_t *seg_begin, int32_t *list, unsigned long long *fill,
+                             cudaStream_t s);
+
+cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, int64_t *total_host,
+                              cudaStream_t s);
+cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, bool fp32,
+                        cudaStream_t s);
+cudaError_t launch_dense_plan(const StepArgs &a, const Layout &y, const int64_t *seg_count,
+                              Plan *plan, int32_t *owner, int64_t *cstart, cudaStream_t s);
+// One iteration: the whole launch sequence, sizes read on the device.
+cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int step_grid,
+                             cudaStream_t s, cudaEvent_t ev_before = nullptr,
+                             cudaEvent_t ev_after = nullptr, int *launches = nullptr);
+int step_blocks_per_sm(int log2m, bool fp32);
+cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_t *perm, bool fp32,
+                            double *closeness, double *harmonic, double *lin, double *reachable,
+                            cudaStream_t s);
+cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *inv, int64_t n, int P,
+                               uint8_t *out, cudaStream_t s);
+cudaError_t launch_gather_f64(const double *src, const int32_t *inv, int64_t n, double *out,
+                              cudaStream_t s);
+cudaError_t launch_frontier_out(const StepArgs &a, const int32_t *inv, uint8_t *changed,
+                                uint8_t *must, cudaStream_t s);
+cudaError_t launch_lc_tables(double *lc64, float *lc32, int P, cudaStream_t s);
+
+}  // namespace hb

@@ -1,0 +1,321 @@
+"""ctypes binding of the HyperBall C ABI (``include/hyperball.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libhyperball.so``.  The functions keep the C names
+(``hb_create``, ``hb_step``, ``hb_run_to_fixpoint``, ``hb_get_centralities``,
+...); tensors are passed by ``data_ptr()`` (device) or as host buffers (CPU
+tensors, numpy arrays), and streams as ``torch.cuda.Stream``.  If the
+library is missing or cannot load, these functions raise: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhyperball.so")
+
+HB_OK = 0
+HB_ERR_INVALID = -1
+HB_ERR_OOM = -2
+HB_ERR_CUDA = -3
+HB_ERR_NOT_CONVERGED = -4
+HB_ERR_TIMEOUT = -5
+HB_ERR_STATE = -6
+
+HB_TRANSPOSE = 0x1
+HB_BORROW_DEVICE_PTRS = 0x2
+HB_FP32_ESTIMATE = 0x4
+HB_NO_RELABEL = 0x8
+HB_PROFILE = 0x10
+
+FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
+
+# every symbol include/hyperball.h declares
+EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
+           "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
+           "hb_get_info", "hb_reset", "hb_save", "hb_load", "hb_destroy", "hb_last_error",
+           "hb_version"]
+
+
+class HBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class HBNotConverged(HBError):
+    pass
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("frontier", ctypes.c_int32),
+                ("max_steps", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("log2m", ctypes.c_int32),
+                ("t", ctypes.c_int32), ("last_changed", ctypes.c_int64),
+                ("last_nodes", ctypes.c_int64), ("last_arcs", ctypes.c_int64),
+                ("total_arcs", ctypes.c_int64), ("last_sparse", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_double), ("kernel_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+
+
+def load():
+    """Load libhyperball.so (build it first with ``paper_1308_2144_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing; build it with "
+                               "`python -m paper_1308_2144_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        st = ctypes.c_int
+        L.hb_default_options.restype = None
+        L.hb_default_options.argtypes = [ctypes.POINTER(Options)]
+        for name in ("hb_create", "hb_create32"):
+            f = getattr(L, name)
+            f.restype = st
+            f.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                          ctypes.POINTER(Options), ctypes.POINTER(_vp)]
+        L.hb_step.restype = st
+        L.hb_step.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64)]
+        L.hb_run_to_fixpoint.restype = st
+        L.hb_run_to_fixpoint.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+        L.hb_get_centralities.restype = st
+        L.hb_get_centralities.argtypes = [_vp, _vp, _vp, _vp, _vp]
+        L.hb_get_accumulators.restype = st
+        L.hb_get_accumulators.argtypes = [_vp, _vp, _vp]
+        L.hb_get_registers.restype = st
+        L.hb_get_registers.argtypes = [_vp, _vp]
+        L.hb_get_frontier.restype = st
+        L.hb_get_frontier.argtypes = [_vp, _vp, _vp]
+        L.hb_get_info.restype = st
+        L.hb_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
+        L.hb_reset.restype = st
+        L.hb_reset.argtypes = [_vp, ctypes.c_uint64]
+        L.hb_save.restype = st
+        L.hb_save.argtypes = [_vp, ctypes.c_char_p]
+        L.hb_load.restype = st
+        L.hb_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(Options), ctypes.POINTER(_vp)]
+        L.hb_destroy.restype = None
+        L.hb_destroy.argtypes = [_vp]
+        L.hb_last_error.restype = ctypes.c_char_p
+        L.hb_last_error.argtypes = []
+        L.hb_version.restype = ctypes.c_char_p
+        L.hb_version.argtypes = []
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status == HB_OK:
+        return
+    msg = load().hb_last_error().decode(errors="replace")
+    if status == HB_ERR_NOT_CONVERGED:
+        raise HBNotConverged(status, msg)
+    raise HBError(status, msg)
+
+
+def _ptr(x):
+    """Pointer of a tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"expected a tensor or an ndarray, got {type(x)}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
+                 max_steps=1 << 20, stream=None, profile=False) -> Options:
+    o = Options()
+    load().hb_default_options(ctypes.byref(o))
+    o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
+               | (HB_FP32_ESTIMATE if fp32 else 0) | (0 if relabel else HB_NO_RELABEL)
+               | (HB_PROFILE if profile else 0))
+    o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
+    o.max_steps = int(max_steps)
+    o.stream = _stream_ptr(stream)
+    return o
+
+
+# ------------------------------------------------------------ C-ABI calls --
+
+def hb_create(offsets, targets, n: int, m: int, log2m: int, seed: int, options: Options | None = None):
+    """Create a handle; int64 offsets use hb_create, int32 offsets hb_create32."""
+    L = load()
+    h = _vp()
+    dt = offsets.dtype
+    is32 = dt in (torch.int32, np.int32)
+    fn = L.hb_create32 if is32 else L.hb_create
+    _check(fn(_ptr(offsets), _ptr(targets), int(n), int(m), int(log2m), int(seed) & (2**64 - 1),
+              ctypes.byref(options) if options is not None else None, ctypes.byref(h)))
+    return h
+
+
+def hb_step(h) -> int:
+    k = ctypes.c_int64()
+    _check(load().hb_step(h, ctypes.byref(k)))
+    return int(k.value)
+
+
+def hb_run_to_fixpoint(h) -> int:
+    s = ctypes.c_int32()
+    _check(load().hb_run_to_fixpoint(h, ctypes.byref(s)))
+    return int(s.value)
+
+
+def hb_get_centralities(h, closeness=None, harmonic=None, lin=None, reachable=None):
+    _check(load().hb_get_centralities(h, _ptr(closeness), _ptr(harmonic), _ptr(lin), _ptr(reachable)))
+
+
+def hb_get_accumulators(h, sumd=None, harm=None):
+    _check(load().hb_get_accumulators(h, _ptr(sumd), _ptr(harm)))
+
+
+def hb_get_registers(h, out):
+    _check(load().hb_get_registers(h, _ptr(out)))
+
+
+def hb_get_frontier(h, changed=None, must_check=None):
+    _check(load().hb_get_frontier(h, _ptr(changed), _ptr(must_check)))
+
+
+def hb_get_info(h) -> dict:
+    info = Info()
+    _check(load().hb_get_info(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def hb_reset(h, seed: int):
+    _check(load().hb_reset(h, int(seed) & (2**64 - 1)))
+
+
+def hb_save(h, path: str):
+    _check(load().hb_save(h, path.encode()))
+
+
+def hb_load(path: str, options: Options | None = None):
+    h = _vp()
+    _check(load().hb_load(path.encode(), ctypes.byref(options) if options is not None else None,
+                          ctypes.byref(h)))
+    return h
+
+
+def hb_destroy(h):
+    if h:
+        load().hb_destroy(h)
+
+
+def hb_version() -> str:
+    return load().hb_version().decode()
+
+
+# ------------------------------------------------------------- convenience --
+
+class HyperBall:
+    """One graph's HyperBall state on the GPU (owns an hb_graph handle).
+
+    ``offsets``/``targets`` describe the scanned graph S in CSR form (torch
+    tensors on the GPU or the CPU, or numpy arrays); pass ``transpose=True``
+    to hand over G and scan G^T (the in-centralities of Sec. 3).
+    """
+
+    def __init__(self, offsets, targets, log2m: int = 4, seed: int = 42, n: int | None = None,
+                 **opts):
+        self.n = int(offsets.shape[0] - 1) if n is None else int(n)
+        self.m = int(targets.shape[0])
+        self.log2m = log2m
+        self.p = 1 << log2m
+        self.options = make_options(**opts)
+        self._h = hb_create(offsets, targets, self.n, self.m, log2m, seed, self.options)
+
+    @classmethod
+    def from_graph(cls, g, **kw):
+        return cls(g.offsets, g.targets, n=g.n, **kw)
+
+    def step(self) -> int:
+        return hb_step(self._h)
+
+    def run(self) -> int:
+        return hb_run_to_fixpoint(self._h)
+
+    def info(self) -> dict:
+        return hb_get_info(self._h)
+
+    def reset(self, seed: int):
+        hb_reset(self._h, seed)
+
+    def _out(self, shape, dtype, device):
+        return torch.empty(shape, dtype=dtype, device=device)
+
+    def centralities(self, device="cuda") -> dict:
+        out = {k: self._out(self.n, torch.float64, device)
+               for k in ("closeness", "harmonic", "lin", "reachable")}
+        hb_get_centralities(self._h, out["closeness"], out["harmonic"], out["lin"], out["reachable"])
+        return out
+
+    def accumulators(self, device="cuda"):
+        sumd = self._out(self.n, torch.float64, device)
+        harm = self._out(self.n, torch.float64, device)
+        hb_get_accumulators(self._h, sumd, harm)
+        return sumd, harm
+
+    def registers(self, device="cuda") -> torch.Tensor:
+        out = self._out((self.n, self.p), torch.uint8, device)
+        hb_get_registers(self._h, out)
+        return out
+
+    def frontier(self, device="cuda"):
+        ch = self._out(self.n, torch.uint8, device)
+        mk = self._out(self.n, torch.uint8, device)
+        hb_get_frontier(self._h, ch, mk)
+        return ch, mk
+
+    def save(self, path: str):
+        hb_save(self._h, path)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            hb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

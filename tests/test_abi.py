@@ -1,0 +1,79 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/hyperball.h declares; argument errors are caught on the host before
+any device work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1308_2144_gb300 import build, hyperball as hbl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return hbl.load()
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hb_\w+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared("hyperball.h")
+    assert "hb_create" in names and "hb_run_to_fixpoint" in names
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(hbl.EXPORTS) == sorted(n for n in names if n in hbl.EXPORTS)
+
+
+def test_library_is_built_for_sm103a():
+    out = build.nvcc()
+    assert os.path.exists(out)
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_version_string(lib):
+    assert "sm_103a" in hbl.hb_version()
+
+
+def test_default_options(lib):
+    o = hbl.Options()
+    lib.hb_default_options(ctypes.byref(o))
+    assert o.flags == 0 and o.frontier == 0 and o.max_steps == 1 << 20 and not o.stream
+
+
+@pytest.mark.parametrize("log2m", [0, 3, 13, 20])
+def test_log2m_out_of_range_is_rejected_on_host(lib, log2m):
+    off = np.array([0, 1, 1], dtype=np.int64)
+    tgt = np.array([1], dtype=np.int32)
+    with pytest.raises(hbl.HBError) as e:
+        hbl.hb_create(off, tgt, 2, 1, log2m, 42)
+    assert e.value.status == hbl.HB_ERR_INVALID
+    assert "log2m" in str(e.value)
+
+
+def test_bad_sizes_are_rejected_on_host(lib):
+    off = np.array([0, 1], dtype=np.int64)
+    tgt = np.array([0], dtype=np.int32)
+    for n, m in ((-1, 1), (2**31, 1), (1, -5)):
+        with pytest.raises(hbl.HBError) as e:
+            hbl.hb_create(off, tgt, n, m, 4, 1)
+        assert e.value.status == hbl.HB_ERR_INVALID
+    off32 = off.astype(np.int32)
+    with pytest.raises(hbl.HBError):
+        hbl.hb_create(off32, tgt, 1, 2**31, 4, 1)
+    with pytest.raises(hbl.HBError):
+        hbl.hb_create(off, tgt, 1, 1, 4, 1, hbl.make_options(frontier=7))
+
+
+def test_null_handle_is_rejected(lib):
+    assert lib.hb_step(None, None) == hbl.HB_ERR_INVALID
+    assert lib.hb_get_registers(None, None) == hbl.HB_ERR_INVALID
+    lib.hb_destroy(None)

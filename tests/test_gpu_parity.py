@@ -1,0 +1,310 @@
+"""GPU path against the oracle, element by element, through the C ABI.
+
+Bar: registers, changed sets, must-check sets and iteration counts
+bit-exact; FP64 accumulators and centralities within 1e-9 relative (the
+only difference allowed is the last bit of the natural logarithm in the
+small-range estimator: glibc and CUDA's log may differ by an ulp).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1308_2144_gb300 import graphs
+from paper_1308_2144_gb300 import hyperball as hbl
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1308_2144_gb300 import build
+    build.build()
+    hbl.load()
+
+
+def close(a, b, rtol=RTOL):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    assert a.shape == b.shape
+    np.testing.assert_allclose(a, b, rtol=rtol, atol=0)
+
+
+def to_dev(off, tgt):
+    return torch.from_numpy(np.ascontiguousarray(off)).cuda(), torch.from_numpy(np.ascontiguousarray(tgt)).cuda()
+
+
+def walk_parity(orc, off, tgt, b, seed, check_every_step=True, **opts):
+    """Run GPU and oracle side by side, one iteration at a time."""
+    n = off.size - 1
+    d_off, d_tgt = to_dev(off, tgt)
+    hb = hbl.HyperBall(d_off, d_tgt, log2m=b, seed=seed, n=n, **opts)
+    c = orc.init(n, b, seed)
+    sumd = np.zeros(n)
+    harm = np.zeros(n)
+    assert np.array_equal(hb.registers().cpu().numpy(), c)
+    t = 0
+    while True:
+        nxt, ch, k = orc.step(off, tgt, b, t, c, sumd, harm)
+        kg = hb.step()
+        assert kg == k, (t, kg, k)
+        if check_every_step or k == 0:
+            assert np.array_equal(hb.registers().cpu().numpy(), nxt), t
+            gch, gmust = hb.frontier()
+            assert np.array_equal(gch.cpu().numpy(), ch), t
+            assert np.array_equal(gmust.cpu().numpy(), orc.must_check(off, tgt, ch)), t
+            gs, gh = hb.accumulators()
+            close(gs.cpu().numpy(), sumd)
+            close(gh.cpu().numpy(), harm)
+        c = nxt
+        t += 1
+        if k == 0:
+            break
+    info = hb.info()
+    assert info["t"] == t and info["converged"] == 1
+    fin = orc.finalize(b, c, sumd, harm)
+    cen = {k: v.cpu().numpy() for k, v in hb.centralities().items()}
+    for key in ("closeness", "harmonic", "lin", "reachable"):
+        close(cen[key], fin[key])
+    hb.close()
+    return t
+
+
+# ------------------------------------------------------------- workloads --
+
+@pytest.fixture(scope="module")
+def plain():
+    return graphs.plain_graph(n=10_000, seed=1).numpy()
+
+
+def test_plain_workload_every_step(orc, plain):
+    """The 10,000-node Zipf(2.1) workload, log2m = 4, hash seed 42."""
+    off, tgt = plain
+    steps = walk_parity(orc, off, tgt, 4, 42)
+    assert steps > 3
+
+
+@pytest.mark.parametrize("b", list(range(4, 13)))
+def test_every_log2m(orc, b):
+    off, tgt = graphs.plain_graph(n=1500, seed=b).numpy()
+    walk_parity(orc, off, tgt, b, 1000 + b)
+
+
+@pytest.mark.parametrize("frontier", ["auto", "push", "pull", "off"])
+@pytest.mark.parametrize("relabel", [True, False])
+def test_frontier_policies_and_layouts(orc, frontier, relabel):
+    off, tgt = graphs.rmat_graph(scale=12, edge_factor=8, seed=21).numpy()
+    walk_parity(orc, off, tgt, 5, 77, frontier=frontier, relabel=relabel)
+
+
+def _degree_boundary_graph(b, seed=3):
+    """Nodes whose degrees sit on every class boundary of the step kernel:
+    0, 1, 4, 5, 8, 9, ..., the heavy threshold +-1, several heavy chunks."""
+    p = 1 << b
+    L = min(p // 16, 32)
+    smax = 32 // L
+    chunk = 64 * smax
+    heavy = 2 * chunk
+    degs = [0, 1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129,
+            heavy - 1, heavy, heavy + 1, 3 * chunk + 5, 7 * chunk]
+    degs = sorted(set(d for d in degs if d >= 0))
+    n = max(4 * max(degs), 5000)
+    rng = np.random.default_rng(seed)
+    edges = []
+    for i, d in enumerate(degs):
+        for tgt in rng.choice(n, size=d, replace=False):
+            edges.append((i, int(tgt)))
+    for v in range(len(degs), n):   # background: small random out-degrees
+        for tgt in rng.integers(0, n, size=int(rng.integers(0, 4))):
+            edges.append((v, int(tgt)))
+    return graphs.from_edges(n, edges, keep_all=True).numpy()
+
+
+@pytest.mark.parametrize("b", [4, 6, 9, 12])
+def test_degree_class_boundaries(orc, b):
+    off, tgt = _degree_boundary_graph(b)
+    walk_parity(orc, off, tgt, b, 5, check_every_step=(b <= 6))
+
+
+def test_hub_with_many_predecessors(orc):
+    # one node reached from almost every node: exercises the grid-wide push
+    n = 6000
+    rng = np.random.default_rng(8)
+    edges = [(v, 0) for v in range(1, n)] + [(0, int(w)) for w in rng.integers(1, n, 50)]
+    edges += [(int(u), int(w)) for u, w in rng.integers(1, n, size=(3 * n, 2))]
+    off, tgt = graphs.from_edges(n, edges, keep_all=False).numpy()
+    walk_parity(orc, off, tgt, 4, 9, frontier="push")
+
+
+@pytest.mark.parametrize("name", ["path", "cycle", "star_out", "star_in", "complete", "loops_dups",
+                                  "isolated"])
+def test_small_structured_graphs(orc, name):
+    from tests.test_oracle_hyperball import SMALL
+    off, tgt = SMALL[name]
+    walk_parity(orc, off, tgt, 4, 42)
+
+
+def test_empty_graph():
+    off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tgt = torch.zeros(0, dtype=torch.int32, device="cuda")
+    hb = hbl.HyperBall(off, tgt, log2m=4, seed=1, n=0)
+    assert hb.run() == 1
+    assert hb.registers().numel() == 0
+    hb.close()
+
+
+# ------------------------------------------------------------ interfaces --
+
+def test_host_and_device_pointers_int32_and_int64(orc, plain):
+    off, tgt = plain
+    ref = orc.run(off, tgt, 4, 42)
+    variants = [
+        dict(offsets=off, targets=tgt),                                        # host, int64
+        dict(offsets=off.astype(np.int32), targets=tgt),                        # host, int32
+        dict(offsets=torch.from_numpy(off.astype(np.int32)).cuda(), targets=torch.from_numpy(tgt).cuda()),
+        dict(offsets=torch.from_numpy(off).cuda(), targets=torch.from_numpy(tgt).cuda(), borrow=True),
+    ]
+    for v in variants:
+        o, t_ = v.pop("offsets"), v.pop("targets")
+        hb = hbl.HyperBall(o, t_, log2m=4, seed=42, n=off.size - 1, **v)
+        assert hb.run() == ref.steps
+        assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+        s, h = hb.accumulators(device="cpu")
+        close(s.numpy(), ref.sumd)
+        close(h.numpy(), ref.harm)
+        hb.close()
+
+
+def test_transpose_flag_matches_transposed_input(orc):
+    g = graphs.rmat_graph(scale=11, edge_factor=6, seed=5)        # this is S = G^T
+    gt = graphs.transpose(g)                                        # G
+    off, tgt = g.numpy()
+    ref = orc.run(off, tgt, 6, 3)
+    o2, t2 = gt.numpy()
+    hb = hbl.HyperBall(*to_dev(o2, t2), log2m=6, seed=3, n=g.n, transpose=True)
+    assert hb.run() == ref.steps
+    assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+    hb.close()
+
+
+def test_max_steps_and_continue(orc, plain):
+    off, tgt = plain
+    ref = orc.run(off, tgt, 4, 42)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=42, n=off.size - 1, max_steps=2)
+    with pytest.raises(hbl.HBNotConverged):
+        hb.run()
+    assert hb.info()["t"] == 2
+    while hb.step() != 0:
+        pass
+    assert hb.info()["t"] == ref.steps
+    assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+    hb.close()
+
+
+def test_step_after_convergence_changes_nothing(orc, plain):
+    off, tgt = plain
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=42, n=off.size - 1)
+    hb.run()
+    regs = hb.registers().cpu().numpy()
+    s0, h0 = hb.accumulators(device="cpu")
+    assert hb.step() == 0
+    assert np.array_equal(hb.registers().cpu().numpy(), regs)
+    s1, h1 = hb.accumulators(device="cpu")
+    assert torch.equal(s0, s1) and torch.equal(h0, h1)
+    hb.close()
+
+
+def test_reset_equals_fresh_handle(orc, plain):
+    off, tgt = plain
+    ref = orc.run(off, tgt, 4, 1234)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=42, n=off.size - 1)
+    hb.run()
+    hb.reset(1234)
+    assert hb.run() == ref.steps
+    assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+    hb.close()
+
+
+@pytest.mark.parametrize("frontier", ["auto", "pull"])
+def test_checkpoint_resume_is_bit_identical(tmp_path, plain, frontier):
+    off, tgt = plain
+    full = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=42, n=off.size - 1, frontier=frontier)
+    full.run()
+    a = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=42, n=off.size - 1, frontier=frontier)
+    for _ in range(3):
+        a.step()
+    path = str(tmp_path / "hb.ckpt")
+    a.save(path)
+    a.close()
+    h = hbl.hb_load(path, hbl.make_options(frontier=frontier))
+    b = hbl.HyperBall.__new__(hbl.HyperBall)
+    b._h, b.n, b.p, b.log2m = h, off.size - 1, 16, 4
+    b.run()
+    assert b.info()["t"] == full.info()["t"]
+    assert torch.equal(b.registers(), full.registers())
+    for x, y in zip(b.accumulators(), full.accumulators()):
+        assert torch.equal(x, y)
+    b.close()
+    full.close()
+
+
+@pytest.mark.parametrize("bad", ["first", "last", "decrease", "target_high", "target_neg"])
+def test_malformed_csr_is_rejected(bad):
+    off = np.array([0, 2, 3, 5, 6], dtype=np.int64)
+    tgt = np.array([1, 2, 0, 3, 1, 2], dtype=np.int32)
+    n, m = 4, 6
+    if bad == "first":
+        off[0] = 1
+    elif bad == "last":
+        off[-1] = 5
+    elif bad == "decrease":
+        off[2] = 1
+    elif bad == "target_high":
+        tgt[3] = 4
+    else:
+        tgt[0] = -1
+    with pytest.raises(hbl.HBError) as e:
+        hbl.hb_create(torch.from_numpy(off).cuda(), torch.from_numpy(tgt).cuda(), n, m, 4, 1)
+    assert e.value.status == hbl.HB_ERR_INVALID
+
+
+# --------------------------------------------------------- precision form --
+
+def test_fp32_estimate_form(orc, plain):
+    """FP32 estimates and deltas, FP64 accumulators: registers, changed sets
+    and iteration counts stay bit-exact; accumulators within the FP32 bound
+    (per step, each estimate has relative error <= 2^-22, so the sum of
+    distances moves by at most 2^-21 * reach * steps^2 and the harmonic sum
+    by 2^-21 * reach * (1 + ln steps))."""
+    off, tgt = plain
+    n = off.size - 1
+    ref = orc.run(off, tgt, 4, 42, keep_changed=True)
+    fin = orc.finalize(4, ref.regs, ref.sumd, ref.harm)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=42, n=n, fp32=True)
+    t = 0
+    while True:
+        k = hb.step()
+        ch, _ = hb.frontier()
+        assert np.array_equal(ch.cpu().numpy(), ref.changed_hist[t])
+        t += 1
+        if k == 0:
+            break
+    assert t == ref.steps
+    assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+    s, h = (x.cpu().numpy() for x in hb.accumulators())
+    T = ref.steps
+    reach = fin["reachable"]
+    bound_s = 2.0 ** -21 * reach * T * T + 1e-12
+    bound_h = 2.0 ** -21 * reach * (1 + math.log(T)) + 1e-12
+    assert np.all(np.abs(s - ref.sumd) <= bound_s)
+    assert np.all(np.abs(h - ref.harm) <= bound_h)
+    cen = {k: v.cpu().numpy() for k, v in hb.centralities().items()}
+    rel = np.abs(cen["reachable"] - reach) / reach
+    assert rel.max() < 2e-7
+    hb.close()
