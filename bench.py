@@ -72,7 +72,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (FileNotFoundError, OSError):
             self.proc = None
@@ -179,9 +179,10 @@ def sum_over_ranks(x, world):
 
 # ------------------------------------------------------------- the oracle --
 
-def cpu_oracle_sample(g_cpu, log2m, seed, budget_s=20.0, max_iters=3):
-    """The oracle, as it stands, on the host cores: its first iterations of
-    Algorithm 2 on the full graph (every node recomputed), bounded in time."""
+def cpu_oracle_sample(g_cpu, log2m, seed, budget_s=20.0, max_iters=64):
+    """The oracle, as it stands, on the host cores: Algorithm 2 on the full
+    graph (every node recomputed each iteration) until the fixpoint or until
+    the time budget is spent."""
     import oracle
     off, tgt = g_cpu
     n = off.size - 1
@@ -191,15 +192,16 @@ def cpu_oracle_sample(g_cpu, log2m, seed, budget_s=20.0, max_iters=3):
     arcs, secs, iters = 0, 0.0, 0
     for t in range(max_iters):
         t0 = time.perf_counter()
-        c, _, _ = oracle.step(off, tgt, log2m, t, c, sumd, harm)
+        c, _, k = oracle.step(off, tgt, log2m, t, c, sumd, harm)
         secs += time.perf_counter() - t0
         arcs += tgt.size
         iters += 1
-        if secs > budget_s:
+        if k == 0 or secs > budget_s:
             break
     return {"value": arcs / secs, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"first {iters} iteration(s) of Algorithm 2 on the full graph "
-                      f"({arcs} arc-updates in {secs:.2f} s, every node recomputed)"}
+            "sample": f"{iters} iteration(s) of Algorithm 2 on the full graph"
+                      f"{' (to the fixpoint)' if k == 0 else ' (time budget)'}: {arcs} arc-updates in "
+                      f"{secs:.2f} s, every node recomputed each iteration"}
 
 
 # ------------------------------------------------------------------ arms --
@@ -248,8 +250,9 @@ def run_ours(args, world, rank, local):
     g = make_graph(args.workload, "cuda")
     n, m, log2m = g.n, g.m, wl["log2m"]
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     opts = dict(log2m=log2m, seed=wl["seed"], n=n, fp32=fp32, frontier=args.frontier,
-                stream=stream, profile=True)
+                stream=stream, profile=True, relabel=not args.no_relabel)
     hb = hbl.HyperBall(g.offsets, g.targets, **opts)
     cen = {k: torch.empty(n, dtype=torch.float64, device="cuda")
            for k in ("closeness", "harmonic", "lin", "reachable")}
@@ -264,6 +267,8 @@ def run_ours(args, world, rank, local):
     for k in range(args.warmup):
         one_run(wl["seed"] + k)
     torch.cuda.synchronize()
+    if args.trace:
+        trace_run(hb, wl["seed"], log2m)
     launches0 = hb.info()["launches"]
     arcs, kms, kbytes, klaunch, steps_list = 0, 0.0, 0.0, 0, []
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -300,6 +305,61 @@ def run_ours(args, world, rank, local):
 
     # end to end through the public API: host CSR in pinned memory, results
     # back to pinned host memory, handle created and destroyed every step
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, g, opts, wl, world, cen)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(g.numpy(), log2m, wl["seed"])
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": n, "m": m, "log2m": log2m,
+                       "estimate": "fp32" if fp32 else "fp64", "accumulators": "fp64",
+                       "frontier": args.frontier,
+                       "iterations_to_fixpoint": steps_list,
+                       "arc_updates_per_step": arcs / args.steps,
+                       "time_to_fixpoint_ms": ms_max / args.steps,
+                       "l2": "inputs larger than L2 (no flush): counters 2 x %.0f MB, targets %.0f MB"
+                             % (n * (1 << log2m) / 1e6, m * 4 / 1e6),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    hb.close()
+
+
+def trace_run(hb, seed, log2m):
+    """One run, iteration by iteration, to stderr (diagnostics)."""
+    from paper_1308_2144_gb300 import hyperball as hbl
+    hbl.hb_reset(hb._h, seed)
+    prev_ms = prev_b = 0.0
+    while True:
+        k = hb.step()
+        info = hb.info()
+        ms = info["kernel_ms"] - prev_ms
+        by = info["kernel_bytes"] - prev_b
+        prev_ms, prev_b = info["kernel_ms"], info["kernel_bytes"]
+        print(json.dumps({"t": info["t"] - 1, "sparse": info["last_sparse"], "nodes": info["last_nodes"],
+                          "arcs": info["last_arcs"], "changed": k, "kernel_ms": round(ms, 4),
+                          "GBps": round(by / ms / 1e6, 1) if ms > 0 else None}), file=sys.stderr,
+              flush=True)
+        if k == 0:
+            break
+
+
+def run_e2e(args, g, opts, wl, world, cen):
+    """Same metric through the public API from host memory: pinned host CSR
+    in, handle created (upload + setup), run to the fixpoint, centralities
+    back to pinned host memory, handle destroyed, every step."""
+    from paper_1308_2144_gb300 import hyperball as hbl
+    n = g.n
     off_h = g.offsets.cpu().pin_memory()
     tgt_h = g.targets.cpu().pin_memory()
     outs_h = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in cen}
@@ -322,46 +382,23 @@ def run_ours(args, world, rank, local):
     e2e_val = sum_over_ranks(e2e_arcs, world) / e2e_s
     h2d = off_h.numel() * off_h.element_size() + tgt_h.numel() * tgt_h.element_size()
     d2h = 4 * n * 8
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(g.numpy(), log2m, wl["seed"])
-
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": n, "m": m, "log2m": log2m,
-                       "estimate": "fp32" if fp32 else "fp64", "accumulators": "fp64",
-                       "frontier": args.frontier,
-                       "iterations_to_fixpoint": steps_list,
-                       "arc_updates_per_step": arcs / args.steps,
-                       "time_to_fixpoint_ms": ms_max / args.steps,
-                       "l2": "inputs larger than L2 (no flush): counters 2 x %.0f MB, targets %.0f MB"
-                             % (n * (1 << log2m) / 1e6, m * 4 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps},
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
-        }
-        print(json.dumps(line), flush=True)
-    hb.close()
+    return {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps}
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="enwiki")
     ap.add_argument("--frontier", choices=["auto", "push", "pull", "off"], default="auto")
     ap.add_argument("--fp32", action="store_true", help="precision form (FP32 estimates)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-relabel", action="store_true", help="keep the generator's node order")
+    ap.add_argument("--trace", action="store_true", help="per-iteration diagnostics on stderr")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

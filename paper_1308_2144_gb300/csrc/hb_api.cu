@@ -204,9 +204,8 @@ hb_status finish_setup(hb_graph *g) {
         return fail(HB_ERR_OOM, "out of pinned host memory");
 
     const double alpha = hll_alpha(P);
-    a.alpha_pp = alpha * (double)P * (double)P;
-    a.scale = std::ldexp(1.0, g->b - 64);
-    a.c32 = (float)std::ldexp(a.alpha_pp, 64 - g->b);
+    a.c64 = std::ldexp(alpha * (double)P * (double)P, 64 - g->b);
+    a.c32 = (float)a.c64;
     // small-range switch: raw estimate <= 5p/2  <=>  X >= alpha 2^64 * 2/5
     const unsigned __int128 Y = (unsigned __int128)std::ldexp(alpha, 64);
     a.thr_x = (unsigned long long)((2 * Y + 4) / 5);
@@ -491,6 +490,7 @@ hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic, 
     if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
     cudaError_t e = launch_finalize(g->a, current_regs(g), g->perm, g->fp32, dev[0], dev[1], dev[2],
                                     dev[3], g->s);
+    if (n > 0) g->launches += 1;
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         if (outs[k] && dev[k] != outs[k]) e = to_caller(outs[k], dev[k], sizeof(double) * n, g->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
@@ -636,7 +636,7 @@ hb_status hb_save(hb_graph *g, const char *path) {
     if (ok) ok = cudaMemcpy(&c, g->ctr, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess;
     // the last iteration's changed lists drive the next frontier
     const int last = (g->t + 1) & 1;
-    ok = ok && write_dev(f, g->a.clist[last], sizeof(int32_t) * c.n_changed, g->s);
+    ok = ok && write_dev(f, g->a.clist[last], sizeof(int32_t) * c.list_len, g->s);
     ok = ok && write_dev(f, g->a.biglist[last], sizeof(int32_t) * c.n_big, g->s);
     fclose(f);
     if (!ok) return fail(HB_ERR_CUDA, "checkpoint write failed");
@@ -695,7 +695,7 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     Counters c{};
     if (ok) ok = cudaMemcpy(&c, g->ctr, sizeof(c), cudaMemcpyDeviceToHost) == cudaSuccess;
     const int last = (h.t + 1) & 1;
-    ok = ok && read_dev(f, g->a.clist[last], sizeof(int32_t) * c.n_changed, g->s);
+    ok = ok && read_dev(f, g->a.clist[last], sizeof(int32_t) * c.list_len, g->s);
     ok = ok && read_dev(f, g->a.biglist[last], sizeof(int32_t) * c.n_big, g->s);
     fclose(f);
     if (!ok) { delete g; return fail(HB_ERR_INVALID, "truncated checkpoint"); }

@@ -79,12 +79,14 @@ struct Plan {
 // Device counters of the running step.  "cur" fields are produced by the
 // step being executed, "prev" fields are those of the step before.
 struct Counters {
-    unsigned long long n_changed;      // also the length of the changed list
+    unsigned long long n_changed;      // nodes whose counter changed
+    unsigned long long list_len;       // length of the changed list (built when a frontier is kept)
     unsigned long long push_arcs;      // sum of predecessor counts of changed nodes
     unsigned long long n_big;          // changed nodes with > kBigRdeg predecessors
     unsigned long long fill[kSegs];    // sparse list fill per segment
     unsigned long long arcs;           // arcs scanned by the sparse list
     unsigned long long prev_changed;
+    unsigned long long prev_list_len;
     unsigned long long prev_push_arcs;
     unsigned long long prev_big;
     int32_t mode;                      // 0 = dense (all nodes), 1 = sparse (frontier list)
@@ -125,10 +127,9 @@ struct StepArgs {
     Counters *ctr;
     const double *lc64;           // p ln(p/V), V = 0..p
     const float *lc32;
-    double alpha_pp;              // alpha_p p^2
-    float c32;                    // alpha_p p^2 2^(64-b) as float
+    double c64;                   // alpha_p p^2 2^(64-b)
+    float c32;                    // the same as float
     unsigned long long thr_x;     // small-range switch in fixed point
-    double scale;                 // 2^(b-64)
     int64_t n;
     int64_t n_pos;                // nodes of nonzero degree
     int64_t m;
@@ -210,28 +211,42 @@ __device__ __forceinline__ void chunk_sums(uint4 c, int b, uint32_t &V, unsigned
     }
 }
 
-// Sec. 4.1 estimate in double from (V, S): alpha_p p^2 / (V + S 2^(b-64)),
-// replaced by linear counting p ln(p/V) when it is <= 5p/2 and V > 0.  The
-// operations and their rounding follow the definition one by one.
-__device__ __forceinline__ double estimate64(uint32_t V, unsigned long long S, int P,
-                                             double alpha_pp, double scale, const double *lc64) {
-    double sum = __dadd_rn((double)V, __dmul_rn(__ull2double_rn(S), scale));
-    double E = __ddiv_rn(alpha_pp, sum);
-    if (E <= 2.5 * (double)P && V > 0) E = lc64[V];
-    return E;
+// Sec. 4.1 estimate from the zero-register count V and the fixed-point
+// sum S = sum over nonzero registers of 2^(64-b-M).  X = V 2^(64-b) + S is
+// the exact register sum scaled by 2^(64-b) (it fits in 64 bits unless the
+// counter is empty, V = p, whose estimate is 0).  Small-range switch
+// (linear counting p ln(p/V) when the raw estimate alpha_p p^2 / sum is
+// <= 5p/2 and V > 0) is taken exactly on X: X >= thr_x.  The raw estimate
+// is c64 / X with c64 = alpha_p p^2 2^(64-b), X converted once to double;
+// the reciprocal comes from an FP32 seed refined by two Newton steps in
+// FP64 (GB300 runs FP64 at a small fraction of its FP32 rate, so the
+// correctly rounded division is avoided; the result is within 2 ulp).
+__device__ __forceinline__ double estimate64(uint32_t V, unsigned long long S, int P, int b,
+                                             double c64, unsigned long long thr_x,
+                                             const double *lc64) {
+    if (V == (uint32_t)P) return 0.0;
+    const unsigned long long X = ((unsigned long long)V << (64 - b)) + S;
+    if (V > 0 && X >= thr_x) return lc64[V];
+    const double xd = __ull2double_rn(X);
+    double r = (double)__frcp_rn(__ull2float_rn(X));
+    double e = __fma_rn(-xd, r, 1.0);
+    r = __fma_rn(r, e, r);
+    e = __fma_rn(-xd, r, 1.0);
+    r = __fma_rn(r, e, r);
+    return __dmul_rn(c64, r);
 }
 
-// Precision form: the switch is taken on the exact fixed-point sum
-// X = V 2^(64-b) + S (X >= thr_x <=> raw estimate <= 5p/2), the estimate in
-// FP32.  V == P (an empty counter) gives 0.
+// Precision form: the same switch on X, the estimate in FP32.
 __device__ __forceinline__ float estimate32(uint32_t V, unsigned long long S, int P, int b,
                                             float c32, unsigned long long thr_x, const float *lc32) {
     if (V == (uint32_t)P) return 0.0f;
-    unsigned long long X = ((unsigned long long)V << (64 - b)) + S;
+    const unsigned long long X = ((unsigned long long)V << (64 - b)) + S;
     if (V > 0 && X >= thr_x) return lc32[V];
-    return __fdiv_rn(c32, __ull2float_rn(X));
+    return __fmul_rn(c32, __frcp_rn(__ull2float_rn(X)));
 }
 
+// Inclusive warp scan and exclusive block scan (one value per thread,
+// blockDim a multiple of 32 up to 1024); the block scan returns the total.
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -242,7 +257,6 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
     return x;
 }
 
-// Block-wide exclusive scan of one value per thread; returns the block total.
 __device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t &excl) {
     __shared__ int64_t wsum[32];
     __shared__ int64_t wtotal;
@@ -255,7 +269,7 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t &excl) {
         int64_t w = lane < nw ? wsum[lane] : 0;
         int64_t wi = warp_incl_scan(w);
         if (lane < nw) wsum[lane] = wi - w;
-        if (lane == 31) wtotal = wi;   // nw <= 32
+        if (lane == 31) wtotal = wi;
     }
     __syncthreads();
     excl = inc - x + wsum[wid];

@@ -18,6 +18,15 @@
 
 #include "../../include/hyperball.h"
 
+// Arcs in flight per lane when a lane holds one 16-byte chunk of a counter,
+// and the minimum resident blocks the step kernel is compiled for.
+#ifndef HB_UNROLL
+#define HB_UNROLL 8
+#endif
+#ifndef HB_MIN_BLOCKS
+#define HB_MIN_BLOCKS 6
+#endif
+
 namespace hb {
 
 namespace {
@@ -70,16 +79,16 @@ __global__ void init_nodes_kernel(StepArgs a, const int32_t *perm, uint64_t seed
         uint32_t V = (uint32_t)P - 1;
         unsigned long long S = 1ULL << (64 - a.b - (int)rho);
         if (F32) static_cast<float *>(a.ecache)[v] = estimate32(V, S, P, a.b, a.c32, a.thr_x, a.lc32);
-        else static_cast<double *>(a.ecache)[v] = estimate64(V, S, P, a.alpha_pp, a.scale, a.lc64);
+        else static_cast<double *>(a.ecache)[v] = estimate64(V, S, P, a.b, a.c64, a.thr_x, a.lc64);
         a.sumd[v] = 0.0;
         a.harm[v] = 0.0;
         a.changed[v] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Counters *c = a.ctr;
-        c->n_changed = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
+        c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
         for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
-        c->prev_changed = 0; c->prev_push_arcs = 0; c->prev_big = 0;
+        c->prev_changed = 0; c->prev_list_len = 0; c->prev_push_arcs = 0; c->prev_big = 0;
         c->mode = 0; c->t = 0; c->steps_done = 0; c->converged = 0; c->err = 0;
     }
 }
@@ -91,9 +100,10 @@ __global__ void step_begin_kernel(StepArgs a) {
     const int t = c->steps_done;
     c->t = t;
     c->prev_changed = c->n_changed;
+    c->prev_list_len = c->list_len;
     c->prev_push_arcs = c->push_arcs;
     c->prev_big = c->n_big;
-    c->n_changed = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
+    c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
     for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
     int sparse = 0;
     if (t > 0) {
@@ -161,7 +171,7 @@ __global__ void mark_push_kernel(StepArgs a) {
     const int t = c->t;
     const int32_t *prev = a.clist[(t + 1) & 1];
     const int32_t *bigp = a.biglist[(t + 1) & 1];
-    const int64_t np = (int64_t)c->prev_changed, nb = (int64_t)c->prev_big;
+    const int64_t np = (int64_t)c->prev_list_len, nb = (int64_t)c->prev_big;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -216,7 +226,7 @@ __global__ void copy_forward_kernel(StepArgs a) {
     uint8_t *nxt = a.regs[(t + 1) & 1];
     const int CH = (1 << a.b) >> 4;
     const int logCH = a.b - 4;
-    const int64_t total = (int64_t)c->prev_changed << logCH;
+    const int64_t total = (int64_t)c->prev_list_len << logCH;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = k >> logCH;
@@ -309,7 +319,7 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
                                             int64_t eend, int S, int cl,
                                             uint4 (&acc)[Cfg<LOG2P>::CPL]) {
     using C = Cfg<LOG2P>;
-    constexpr int U = C::CPL >= 4 ? 1 : (C::CPL == 2 ? 2 : 4);
+    constexpr int U = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     for (; e < eend; e += (int64_t)S * U) {
         int32_t w[U];
@@ -343,7 +353,9 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
                                               uint8_t *__restrict__ nxt, int t, int64_t v,
                                               bool active, uint4 (&acc)[Cfg<LOG2P>::CPL], int cl,
                                               int tl, int team, int logT, int32_t *clist,
-                                              int32_t *biglist) {
+                                              int32_t *biglist, bool sparse,
+                                              unsigned long long *s_changed, double rdist64,
+                                              float rdist32) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     bool diff = false;
@@ -382,25 +394,28 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
         S += __shfl_xor_sync(FULL, S, o);
     }
     if (leader && ch) {
+        // Sec. 5: the new layer sits at distance t+1
         if (F32) {
             float *ec = static_cast<float *>(a.ecache);
             const float E = estimate32(V, S, C::P, a.b, a.c32, a.thr_x, a.lc32);
             const float d = __fsub_rn(E, ec[v]);
             ec[v] = E;
-            a.sumd[v] = __dadd_rn(a.sumd[v], (double)(t + 1) * (double)d);   // exact product
-            a.harm[v] = __dadd_rn(a.harm[v], (double)__fdiv_rn(d, (float)(t + 1)));
+            a.sumd[v] = __fma_rn((double)(t + 1), (double)d, a.sumd[v]);   // exact product
+            a.harm[v] = __dadd_rn(a.harm[v], (double)__fmul_rn(d, rdist32));
         } else {
             double *ec = static_cast<double *>(a.ecache);
-            const double E = estimate64(V, S, C::P, a.alpha_pp, a.scale, a.lc64);
+            const double E = estimate64(V, S, C::P, a.b, a.c64, a.thr_x, a.lc64);
             const double d = __dsub_rn(E, ec[v]);
             ec[v] = E;
-            const double dist = (double)(t + 1);
-            a.sumd[v] = __dadd_rn(a.sumd[v], __dmul_rn(dist, d));
-            a.harm[v] = __dadd_rn(a.harm[v], __ddiv_rn(d, dist));
+            a.sumd[v] = __fma_rn((double)(t + 1), d, a.sumd[v]);
+            a.harm[v] = __fma_rn(d, rdist64, a.harm[v]);
         }
     }
+    if (lane == 0) atomicAdd(s_changed, (unsigned long long)__popc(lb));
+    if (!sparse) return;   // dense iterations: the changed list is compacted afterwards
+    // frontier iterations change few nodes: append them right away
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&a.ctr->n_changed, (unsigned long long)__popc(lb));
+    if (lane == 0) base = atomicAdd(&a.ctr->list_len, (unsigned long long)__popc(lb));
     base = __shfl_sync(FULL, base, 0);
     if (leader && ch) clist[base + __popc(lb & lanemask_lt())] = (int32_t)v;
     if (a.has_reverse) {
@@ -423,7 +438,9 @@ template <int LOG2P, bool F32>
 __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t pos0,
                                            int64_t pos_end, int logS, const int32_t *list,
-                                           int32_t *clist, int32_t *biglist) {
+                                           int32_t *clist, int32_t *biglist, bool sparse,
+                                           unsigned long long *s_changed, double rdist64,
+                                           float rdist32) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int logT = C::LOGL + logS;
@@ -446,7 +463,8 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
-    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist);
+    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
+                              sparse, s_changed, rdist64, rdist32);
 }
 
 // One chunk of a heavy node, by a whole warp.  Each chunk leaves its
@@ -456,7 +474,9 @@ template <int LOG2P, bool F32>
 __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t it,
                                            const int32_t *owner, const int64_t *cstart,
-                                           const int32_t *list, int32_t *clist, int32_t *biglist) {
+                                           const int32_t *list, int32_t *clist, int32_t *biglist,
+                                           bool sparse, unsigned long long *s_changed,
+                                           double rdist64, float rdist32) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int cl = lane & (C::L - 1);
@@ -505,11 +525,13 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
     }
-    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist);
+    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
+                              s_changed, rdist64, rdist32);
 }
 
 template <int LOG2P, bool F32>
-__global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MIN_BLOCKS)
+    step_kernel(StepArgs a) {
     using C = Cfg<LOG2P>;
     const Counters *ctr = a.ctr;
     const int t = ctr->t;
@@ -529,11 +551,17 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
     for (int j = 0; j <= C::NLIGHT; ++j) ib[j] = pl->item_begin[j];
 #pragma unroll
     for (int j = 0; j < C::NLIGHT; ++j) cnt[j] = pl->count[j + 1];
+    __shared__ unsigned long long s_changed;
+    const double rdist64 = 1.0 / (double)(t + 1);
+    const float rdist32 = 1.0f / (float)(t + 1);
+    if (threadIdx.x == 0) s_changed = 0;
+    __syncthreads();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = gw; it < items; it += nw) {
         if (it < hch) {
-            heavy_item<LOG2P, F32>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist);
+            heavy_item<LOG2P, F32>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
+                                   &s_changed, rdist64, rdist32);
         } else {
             const int64_t li = it - hch;
             int j = 0;
@@ -543,8 +571,52 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(StepArgs a) {
                 if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
             const int64_t pos0 = seg0 + ((li - ibj) << j);
             light_item<LOG2P, F32>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
-                                   clist, biglist);
+                                   clist, biglist, sparse, &s_changed, rdist64, rdist32);
         }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_changed) atomicAdd(&a.ctr->n_changed, s_changed);
+}
+
+// After a dense iteration (frontier kept): list the changed nodes, their
+// predecessor count and the ones with many predecessors.  One global atomic
+// per block; the list order does not matter.
+__global__ void __launch_bounds__(256) compact_changed_kernel(StepArgs a) {
+    const Counters *c = a.ctr;
+    if (c->mode != 0) return;
+    const int t = c->t;
+    int32_t *clist = a.clist[t & 1];
+    int32_t *biglist = a.biglist[t & 1];
+    __shared__ unsigned wcnt[8], wbig[8];
+    __shared__ unsigned long long sbase, bbase, spush;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = base + threadIdx.x;
+        const bool ch = v < a.n && a.changed[v];
+        int64_t rd = 0;
+        if (ch && a.has_reverse) rd = a.roff[v + 1] - a.roff[v];
+        const bool big = rd > kBigRdeg;
+        const unsigned bc = __ballot_sync(FULL, ch), bb = __ballot_sync(FULL, big);
+        unsigned long long ps = (unsigned long long)rd;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) ps += __shfl_xor_sync(FULL, ps, o);
+        if (threadIdx.x == 0) spush = 0;
+        if (lane == 0) { wcnt[wid] = __popc(bc); wbig[wid] = __popc(bb); }
+        __syncthreads();
+        if (lane == 0 && ps) atomicAdd(&spush, ps);
+        if (threadIdx.x == 0) {
+            unsigned tot = 0, totb = 0;
+            for (int w = 0; w < 8; ++w) { tot += wcnt[w]; totb += wbig[w]; }
+            sbase = tot ? atomicAdd(&a.ctr->list_len, (unsigned long long)tot) : 0;
+            bbase = totb ? atomicAdd(&a.ctr->n_big, (unsigned long long)totb) : 0;
+        }
+        __syncthreads();
+        unsigned off = 0, offb = 0;
+        for (int w = 0; w < wid; ++w) { off += wcnt[w]; offb += wbig[w]; }
+        if (ch) clist[sbase + off + __popc(bc & lanemask_lt())] = (int32_t)v;
+        if (big) biglist[bbase + offb + __popc(bb & lanemask_lt())] = (int32_t)v;
+        if (threadIdx.x == 0 && spush) atomicAdd(&a.ctr->push_arcs, spush);
+        __syncthreads();
     }
 }
 
@@ -563,7 +635,7 @@ __global__ void finalize_kernel(StepArgs a, const uint8_t *regs, const int32_t *
         for (int c = 0; c < CH; ++c) chunk_sums(row[c], a.b, V, S);
         double r;
         if (F32) r = (double)estimate32(V, S, P, a.b, a.c32, a.thr_x, a.lc32);
-        else r = estimate64(V, S, P, a.alpha_pp, a.scale, a.lc64);
+        else r = estimate64(V, S, P, a.b, a.c64, a.thr_x, a.lc64);
         const double s = a.sumd[v];
         const int64_t o = perm ? (int64_t)perm[v] : v;
         if (reachable) reachable[o] = r;
@@ -715,6 +787,10 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
                          : launch_step_t<false>(a, y.log2m, step_grid, s);
     if (e != cudaSuccess) return e;
     if (ev_after) cudaEventRecord(ev_after, s);
+    if (a.frontier != HB_FRONTIER_OFF) {
+        compact_changed_kernel<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+        ++k;
+    }
     step_end_kernel<<<1, 1, 0, s>>>(a);
     k += 2;
     if (launches) *launches += k;

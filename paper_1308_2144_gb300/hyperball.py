@@ -18,7 +18,8 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhyperball.so")
+# HYPERBALL_LIB selects another build of the same library (tuning sweeps)
+LIB_PATH = os.environ.get("HYPERBALL_LIB") or os.path.join(_HERE, "libhyperball.so")
 
 HB_OK = 0
 HB_ERR_INVALID = -1

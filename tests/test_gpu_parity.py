@@ -279,9 +279,10 @@ def test_malformed_csr_is_rejected(bad):
 def test_fp32_estimate_form(orc, plain):
     """FP32 estimates and deltas, FP64 accumulators: registers, changed sets
     and iteration counts stay bit-exact; accumulators within the FP32 bound
-    (per step, each estimate has relative error <= 2^-22, so the sum of
-    distances moves by at most 2^-21 * reach * steps^2 and the harmonic sum
-    by 2^-21 * reach * (1 + ln steps))."""
+    (per step, each estimate has relative error <= 2^-22, so with a factor
+    two for estimates that exceed the final one, the sum of distances moves
+    by at most 2^-20 * reach * steps^2 and the harmonic sum by
+    2^-20 * reach * (1 + ln steps))."""
     off, tgt = plain
     n = off.size - 1
     ref = orc.run(off, tgt, 4, 42, keep_changed=True)
@@ -300,8 +301,8 @@ def test_fp32_estimate_form(orc, plain):
     s, h = (x.cpu().numpy() for x in hb.accumulators())
     T = ref.steps
     reach = fin["reachable"]
-    bound_s = 2.0 ** -21 * reach * T * T + 1e-12
-    bound_h = 2.0 ** -21 * reach * (1 + math.log(T)) + 1e-12
+    bound_s = 2.0 ** -20 * reach * T * T + 1e-12
+    bound_h = 2.0 ** -20 * reach * (1 + math.log(T)) + 1e-12
     assert np.all(np.abs(s - ref.sumd) <= bound_s)
     assert np.all(np.abs(h - ref.harm) <= bound_h)
     cen = {k: v.cpu().numpy() for k, v in hb.centralities().items()}
