@@ -9,7 +9,7 @@
 
 #include "hb_internal.cuh"
 
-#include "../../include/hyperball.h"
+#include "hyperball.h"
 
 using namespace hb;
 

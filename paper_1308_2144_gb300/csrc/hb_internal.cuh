@@ -144,9 +144,20 @@ struct StepArgs {
 
 // ------------------------------------------------------------ helpers --
 
+// Byte-wise maximum of two words whose bytes are all below 128.  Register
+// values never exceed 64 - b <= 60, so in t = a + 0x80808080 - b every byte
+// is a_i + 128 - b_i, in [1, 255] (no carry crosses a byte), and its bit 7
+// is set exactly when a_i >= b_i; prmt in sign-replicate mode (selector
+// nibbles 8..B) spreads that bit over the byte, giving the select mask.
+__device__ __forceinline__ uint32_t bmax4(uint32_t a, uint32_t b) {
+    const uint32_t t = a + 0x80808080u - b;
+    uint32_t m;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(m) : "r"(t));
+    return (a & m) | (b & ~m);
+}
+
 __device__ __forceinline__ uint4 vmax16(uint4 a, uint4 b) {
-    return make_uint4(__vmaxu4(a.x, b.x), __vmaxu4(a.y, b.y), __vmaxu4(a.z, b.z),
-                      __vmaxu4(a.w, b.w));
+    return make_uint4(bmax4(a.x, b.x), bmax4(a.y, b.y), bmax4(a.z, b.z), bmax4(a.w, b.w));
 }
 
 __device__ __forceinline__ bool ne16(uint4 a, uint4 b) {
@@ -208,6 +219,20 @@ __device__ __forceinline__ void chunk_sums(uint4 c, int b, uint32_t &V, unsigned
             if (M == 0) V += 1;
             else S += 1ULL << (sh - (int)M);
         }
+    }
+}
+
+// The same with the powers looked up in a 64-entry table (pow2[M] =
+// 2^(64-b-M), pow2[0] = 0) and the zero bytes counted four at a time:
+// byte + 0x7F has bit 7 set exactly when the byte is nonzero (bytes < 128).
+__device__ __forceinline__ void chunk_sums_tab(uint4 c, const unsigned long long *pow2, uint32_t &V,
+                                               unsigned long long &S) {
+    const uint32_t w[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t x = w[k];
+        V += 4u - __popc((x + 0x7F7F7F7Fu) & 0x80808080u);
+        S += pow2[x & 0xffu] + pow2[(x >> 8) & 0xffu] + pow2[(x >> 16) & 0xffu] + pow2[x >> 24];
     }
 }
 

@@ -16,7 +16,7 @@
 //   step_end        count the iteration, record convergence
 #include "hb_internal.cuh"
 
-#include "../../include/hyperball.h"
+#include "hyperball.h"
 
 // Arcs in flight per lane when a lane holds one 16-byte chunk of a counter,
 // and the minimum resident blocks the step kernel is compiled for.
@@ -311,30 +311,47 @@ __global__ void heavy_total_kernel(const int64_t *off, int64_t n, int64_t heavy,
 
 // ------------------------------------------------------------ the step --
 
-// Gather the counters of arcs e, e+S, ... < eend into acc (this lane's
-// chunks), U arcs in flight per lane.
+// Gather the counters of arcs e, e+S, ... < eend (S = 2^logS) into acc
+// (this lane's chunks), U arcs in flight per lane; full groups of U arcs
+// run without bounds checks.
 template <int LOG2P>
 __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
                                             const uint8_t *__restrict__ cur, int64_t e,
-                                            int64_t eend, int S, int cl,
+                                            int64_t eend, int logS, int cl,
                                             uint4 (&acc)[Cfg<LOG2P>::CPL]) {
     using C = Cfg<LOG2P>;
     constexpr int U = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
-    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-    for (; e < eend; e += (int64_t)S * U) {
+    if (e >= eend) return;
+    const int cnt = (int)((eend - e + (1LL << logS) - 1) >> logS);
+    const int32_t *tp = tgt + e;
+    const uint8_t *base = cur + cl * 16;
+    int j = 0;
+    for (; j + U <= cnt; j += U) {
         int32_t w[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t ee = e + (int64_t)u * S;
-            w[u] = ee < eend ? ld_stream(tgt + ee) : -1;
-        }
+        for (int u = 0; u < U; ++u) w[u] = ld_stream(tp + ((j + u) << logS));
         uint4 g[U][C::CPL];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const uint8_t *row = cur + (int64_t)w[u] * C::P + cl * 16;
+        for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int c = 0; c < C::CPL; ++c) g[u][c] = w[u] >= 0 ? ld_counter(row + c * C::L * 16) : z;
-        }
+            for (int c = 0; c < C::CPL; ++c)
+                g[u][c] = ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
+    }
+    if (j < cnt) {
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        int32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = j + u < cnt ? ld_stream(tp + ((j + u) << logS)) : -1;
+        uint4 g[U][C::CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c)
+                g[u][c] = w[u] >= 0 ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16) : z;
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -355,7 +372,7 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
                                               int tl, int team, int logT, int32_t *clist,
                                               int32_t *biglist, bool sparse,
                                               unsigned long long *s_changed, double rdist64,
-                                              float rdist32) {
+                                              float rdist32, const unsigned long long *pow2) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     bool diff = false;
@@ -387,7 +404,7 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
     uint32_t V = 0;
     unsigned long long S = 0;
 #pragma unroll
-    for (int c = 0; c < C::CPL; ++c) chunk_sums(acc[c], a.b, V, S);
+    for (int c = 0; c < C::CPL; ++c) chunk_sums_tab(acc[c], pow2, V, S);
 #pragma unroll
     for (int o = 1; o < C::L; o <<= 1) {
         V += __shfl_xor_sync(FULL, V, o);
@@ -440,7 +457,7 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
                                            int64_t pos_end, int logS, const int32_t *list,
                                            int32_t *clist, int32_t *biglist, bool sparse,
                                            unsigned long long *s_changed, double rdist64,
-                                           float rdist32) {
+                                           float rdist32, const unsigned long long *pow2) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int logT = C::LOGL + logS;
@@ -459,12 +476,12 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P>(a.tgt, cur, e0 + slot, e1, 1 << logS, cl, acc);
+    gather_arcs<LOG2P>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
     node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
-                              sparse, s_changed, rdist64, rdist32);
+                              sparse, s_changed, rdist64, rdist32, pow2);
 }
 
 // One chunk of a heavy node, by a whole warp.  Each chunk leaves its
@@ -476,7 +493,8 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
                                            const int32_t *owner, const int64_t *cstart,
                                            const int32_t *list, int32_t *clist, int32_t *biglist,
                                            bool sparse, unsigned long long *s_changed,
-                                           double rdist64, float rdist32) {
+                                           double rdist64, float rdist32,
+                                           const unsigned long long *pow2) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int cl = lane & (C::L - 1);
@@ -493,7 +511,7 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P>(a.tgt, cur, e0 + slot, e1, C::SMAX, cl, acc);
+    gather_arcs<LOG2P>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc);
 #pragma unroll
     for (int o = C::L; o < 32; o <<= 1)
 #pragma unroll
@@ -526,7 +544,7 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
             for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
     }
     node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
-                              s_changed, rdist64, rdist32);
+                              s_changed, rdist64, rdist32, pow2);
 }
 
 template <int LOG2P, bool F32>
@@ -552,16 +570,21 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
 #pragma unroll
     for (int j = 0; j < C::NLIGHT; ++j) cnt[j] = pl->count[j + 1];
     __shared__ unsigned long long s_changed;
+    __shared__ unsigned long long s_pow2[64];
     const double rdist64 = 1.0 / (double)(t + 1);
     const float rdist32 = 1.0f / (float)(t + 1);
     if (threadIdx.x == 0) s_changed = 0;
+    if (threadIdx.x < 64) {
+        const int M = threadIdx.x, sh = 64 - a.b;
+        s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
+    }
     __syncthreads();
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = gw; it < items; it += nw) {
         if (it < hch) {
             heavy_item<LOG2P, F32>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
-                                   &s_changed, rdist64, rdist32);
+                                   &s_changed, rdist64, rdist32, s_pow2);
         } else {
             const int64_t li = it - hch;
             int j = 0;
@@ -571,7 +594,7 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
                 if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
             const int64_t pos0 = seg0 + ((li - ibj) << j);
             light_item<LOG2P, F32>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
-                                   clist, biglist, sparse, &s_changed, rdist64, rdist32);
+                                   clist, biglist, sparse, &s_changed, rdist64, rdist32, s_pow2);
         }
     }
     __syncthreads();
