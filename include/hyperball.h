@@ -182,6 +182,43 @@ const char *hb_last_error(void);
 /* Library version string. */
 const char *hb_version(void);
 
+/* ---- One iteration without device allocation -------------------------
+ * The paper has no counterpart to this call.  It exists for callers that
+ * cannot call cudaMalloc: code running inside another framework's memory
+ * pool or arena, where an allocation outside the pool breaks its
+ * accounting or is not allowed; services that freeze allocation after
+ * start-up so that no request can stall in, or fail on, the allocator; and
+ * hosts that hand the library device buffers but no allocator.
+ *
+ * hb_step_noalloc runs one iteration of Algorithm 2 at loop index t on the
+ * CSR graph (offsets: n+1 int64, targets: m int32), reading the counters
+ * `cur` (n*p bytes) and writing all of `next` (n*p bytes), exactly as
+ * hb_step does for a handle, in the caller's node order: `changed` (n
+ * bytes) receives 1 for every node whose counter changed, and for those
+ * nodes sumd[v] += (t+1)*d and harm[v] += d/(t+1) (n doubles each, updated
+ * in place) with d the change of the FP64 size estimate (Sec. 5).
+ * *n_changed (host memory, may be NULL) receives the number of changed
+ * nodes; the call returns once every output is written.  Every pointer
+ * but n_changed must be device memory; stream may be NULL.
+ *
+ * It allocates nothing: its temporary data (degree lists, work plan,
+ * partial counters of split nodes, cached estimates, counters) lives in
+ * one static device array of HB_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits.  A graph whose
+ * temporary data does not fit (about 12 bytes per node plus p bytes per
+ * 64*(32/L) arcs of nodes above the split threshold) is rejected with
+ * HB_ERR_INVALID and a message giving the size it needs.  All calls share
+ * the array and it keeps the last call's contents (everything that must
+ * start at zero is cleared by each call); calls that overlap on the GPU
+ * (two streams, or two threads) race on it and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address
+ * on that device (cudaGetSymbolAddress, with that device current); make
+ * that first call before any stream capture. */
+#define HB_NOALLOC_SCRATCH_BYTES (64u << 20)
+hb_status hb_step_noalloc(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                          int log2m, int32_t t, const uint8_t *cur, uint8_t *next, double *sumd,
+                          double *harm, uint8_t *changed, int64_t *n_changed, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

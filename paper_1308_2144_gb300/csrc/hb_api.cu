@@ -75,6 +75,11 @@ struct DevMem {
 
 }  // namespace
 
+namespace hb {
+double hll_alpha_of(int p) { return hll_alpha(p); }
+void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+}  // namespace hb
+
 struct hb_graph {
     int64_t n = 0, m = 0;
     int b = 4;

@@ -333,6 +333,11 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
                              cudaStream_t s, cudaEvent_t ev_before = nullptr,
                              cudaEvent_t ev_after = nullptr, int *launches = nullptr);
 int step_blocks_per_sm(int log2m, bool fp32);
+// The gather kernel alone (mode and t already set in the counters).
+cudaError_t launch_step_kernel(const StepArgs &a, int log2m, bool fp32, int grid, cudaStream_t s);
+// alpha_p of the estimator and the thread-local message of hb_last_error().
+double hll_alpha_of(int p);
+void set_last_error(const char *msg);
 cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_t *perm, bool fp32,
                             double *closeness, double *harmonic, double *lin, double *reachable,
                             cudaStream_t s);

@@ -742,6 +742,10 @@ int step_blocks_per_sm(int log2m, bool fp32) {
     return blocks > 0 ? blocks : 1;
 }
 
+cudaError_t launch_step_kernel(const StepArgs &a, int log2m, bool fp32, int grid, cudaStream_t s) {
+    return fp32 ? launch_step_t<true>(a, log2m, grid, s) : launch_step_t<false>(a, log2m, grid, s);
+}
+
 cudaError_t launch_lc_tables(double *lc64, float *lc32, int P, cudaStream_t s) {
     lc_tables_kernel<<<(P + 256) / 256, 256, 0, s>>>(lc64, lc32, P);
     return cudaGetLastError();

@@ -41,7 +41,7 @@ FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
            "hb_get_info", "hb_reset", "hb_save", "hb_load", "hb_destroy", "hb_last_error",
-           "hb_version"]
+           "hb_version", "hb_step_noalloc"]
 
 
 class HBError(RuntimeError):
@@ -121,6 +121,10 @@ def load():
         L.hb_last_error.argtypes = []
         L.hb_version.restype = ctypes.c_char_p
         L.hb_version.argtypes = []
+        L.hb_step_noalloc.restype = st
+        L.hb_step_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                      ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
+                                      ctypes.POINTER(ctypes.c_int64), _vp]
         _lib = L
         return L
 
@@ -238,6 +242,18 @@ def hb_destroy(h):
 
 def hb_version() -> str:
     return load().hb_version().decode()
+
+
+def hb_step_noalloc(offsets, targets, n: int, m: int, log2m: int, t: int, cur, nxt, sumd, harm,
+                    changed, stream=None) -> int:
+    """One iteration that allocates no device memory (all tensors on the
+    GPU; scratch comes from a static device array).  Returns the number of
+    changed nodes."""
+    k = ctypes.c_int64()
+    _check(load().hb_step_noalloc(_ptr(offsets), _ptr(targets), int(n), int(m), int(log2m), int(t),
+                                  _ptr(cur), _ptr(nxt), _ptr(sumd), _ptr(harm), _ptr(changed),
+                                  ctypes.byref(k), _stream_ptr(stream)))
+    return int(k.value)
 
 
 # ------------------------------------------------------------- convenience --
