@@ -159,22 +159,30 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def _all_reduce(x, world, op):
     if world <= 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(x, world):
+    import torch.distributed as dist
+    return _all_reduce(x, world, dist.ReduceOp.MAX if world > 1 else None)
 
 
 def sum_over_ranks(x, world):
-    if world <= 1:
-        return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _all_reduce(x, world, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def replica_throughput(units, ms, world):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed divided by the slowest rank's time (weak scaling)."""
+    return sum_over_ranks(units, world) / (max_over_ranks(ms, world) / 1e3)
 
 
 # ------------------------------------------------------------- the oracle --
@@ -290,8 +298,7 @@ def run_ours(args, world, rank, local):
     ms = ev0.elapsed_time(ev1)
     launches = hb.info()["launches"] - launches0
     ms_max = max_over_ranks(ms, world)
-    arcs_all = sum_over_ranks(arcs, world)
-    value = arcs_all / (ms_max / 1e3)
+    value = replica_throughput(arcs, ms, world)
 
     # roofline of the gather kernel (events recorded by the library on this stream)
     peak, peak_kind = measured_peaks()

@@ -1,0 +1,50 @@
+"""bench.py's multi-rank path (independent replicas, weak scaling) on CPU
+ranks with the gloo backend: the slowest rank's time and the sum of all
+ranks' units make the whole-job number."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    units = 1000.0 * (rank + 1)          # rank r processed 1000 (r+1) arc-updates
+    ms = 10.0 + 5.0 * rank               # the slowest rank took 15 ms
+    val = bench.replica_throughput(units, ms, world)
+    mx = bench.max_over_ranks(ms, world)
+    sm = bench.sum_over_ranks(units, world)
+    bench.barrier(world)
+    out[rank] = (val, mx, sm)
+    dist.destroy_process_group()
+
+
+def test_two_rank_replica_aggregation():
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    for r in range(world):
+        val, mx, sm = out[r]
+        assert mx == 15.0
+        assert sm == 3000.0
+        assert val == pytest.approx(3000.0 / 0.015)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.replica_throughput(500.0, 10.0, 1) == pytest.approx(50000.0)
+    assert bench.max_over_ranks(3.0, 1) == 3.0
