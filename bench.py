@@ -42,6 +42,8 @@ WORKLOADS = {
                                         "targets, transpose scanned, log2m=4"),
     "web": dict(log2m=4, seed=42, desc="R-MAT scale 28 (268,435,456 nodes), edge factor 16, dedup, "
                                       "transpose scanned, log2m=4, FP32 estimates"),
+    "web24": dict(log2m=4, seed=42, desc="R-MAT scale 24 (16,777,216 nodes), edge factor 16, dedup, "
+                                        "transpose scanned, log2m=4, FP32 estimates (profiling size)"),
 }
 
 
@@ -53,6 +55,8 @@ def make_graph(name, device):
         return graphs.plain_graph(device=device)
     if name == "web":
         return graphs.web_graph(device=device)
+    if name == "web24":
+        return graphs.web_graph(scale=24, device=device, bucket_bits=2)
     raise ValueError(name)
 
 
@@ -253,7 +257,7 @@ def run_ours(args, world, rank, local):
     build.build()
     hbl.load()
     wl = WORKLOADS[args.workload]
-    fp32 = args.fp32 or args.workload == "web"
+    fp32 = args.fp32 or args.workload.startswith("web")
     stream = torch.cuda.current_stream()
     g = make_graph(args.workload, "cuda")
     n, m, log2m = g.n, g.m, wl["log2m"]

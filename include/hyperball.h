@@ -182,6 +182,56 @@ const char *hb_last_error(void);
 /* Library version string. */
 const char *hb_version(void);
 
+/* ---- Batched form ------------------------------------------------------
+ * Many independent HyperBall problems -- graphs of uneven size, each with
+ * its own log2m and seed (the paper's repeated runs of Sec. 5 are one use:
+ * the same graph with several seeds) -- advanced together.  Every kernel
+ * of an iteration covers all graphs in one launch; the iteration is
+ * captured into a CUDA graph, and hb_batch_run repeats it on the device
+ * (conditional while node) until no graph is active, so a whole run is one
+ * graph launch.  Each graph keeps its own loop index, frontier and
+ * convergence; a graph that has converged costs nothing in later
+ * iterations.  Results are those of the same graph run alone. */
+typedef struct {
+    const int64_t *offsets;   /* n+1 CSR offsets (host or device) */
+    const int32_t *targets;   /* m CSR targets (host or device) */
+    int64_t n, m;
+    int32_t log2m;            /* 4..12 */
+    uint64_t seed;            /* node-hash seed */
+} hb_graph_desc;
+
+typedef struct hb_batch hb_batch;
+
+/* Create the batch (k in [1, 4096]); options as for hb_create (frontier
+ * PULL is taken as AUTO; max_steps caps hb_batch_run).  With a NULL stream
+ * the batch makes its own. */
+hb_status hb_batch_create(int k, const hb_graph_desc *gs, const hb_options *opt, hb_batch **out);
+
+/* One iteration of every graph that has not converged; *n_active (may be
+ * NULL) receives the number of graphs still changing afterwards. */
+hb_status hb_batch_step(hb_batch *b, int32_t *n_active);
+
+/* Iterate on the device until every graph has converged (or max_steps
+ * batch iterations ran: HB_ERR_NOT_CONVERGED).  *iterations receives the
+ * batch iterations executed since the last reset. */
+hb_status hb_batch_run(hb_batch *b, int32_t *iterations);
+
+/* Re-initialise every graph (seeds[i], or the previous seeds if NULL). */
+hb_status hb_batch_reset(hb_batch *b, const uint64_t *seeds);
+
+/* Per-graph results and counters, as the single-graph getters. */
+hb_status hb_batch_get_centralities(hb_batch *b, int i, double *closeness, double *harmonic,
+                                    double *lin, double *reachable);
+hb_status hb_batch_get_registers(hb_batch *b, int i, uint8_t *out);
+hb_status hb_batch_get_accumulators(hb_batch *b, int i, double *sumd, double *harm);
+hb_status hb_batch_get_info(hb_batch *b, int i, hb_info *info);
+
+/* Batch iterations since the last reset, graphs still active, and arcs
+ * scanned by all graphs (arc-updates). */
+hb_status hb_batch_get_totals(hb_batch *b, int32_t *iterations, int32_t *n_active, int64_t *arcs);
+
+void hb_batch_destroy(hb_batch *b);
+
 /* ---- One iteration without device allocation -------------------------
  * The paper has no counterpart to this call.  It exists for callers that
  * cannot call cudaMalloc: code running inside another framework's memory

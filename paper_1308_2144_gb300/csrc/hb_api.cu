@@ -7,9 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "hb_internal.cuh"
-
-#include "hyperball.h"
+#include "hb_handle.h"
 
 using namespace hb;
 
@@ -47,78 +45,12 @@ double hll_alpha(int p) {
     }
 }
 
-struct DevMem {
-    std::vector<void *> blocks;
-    size_t bytes = 0;
-    cudaError_t err = cudaSuccess;
-    template <class T>
-    T *alloc(size_t count) {
-        if (err != cudaSuccess) return nullptr;
-        void *p = nullptr;
-        size_t sz = count * sizeof(T);
-        if (sz == 0) sz = 16;
-        err = cudaMalloc(&p, sz);
-        if (err != cudaSuccess) { cudaGetLastError(); return nullptr; }
-        blocks.push_back(p);
-        bytes += sz;
-        return static_cast<T *>(p);
-    }
-    void release(void *p) {
-        for (size_t i = 0; i < blocks.size(); ++i)
-            if (blocks[i] == p) { cudaFree(p); blocks.erase(blocks.begin() + (long)i); return; }
-    }
-    void free_all() {
-        for (void *p : blocks) cudaFree(p);
-        blocks.clear();
-    }
-};
-
 }  // namespace
 
 namespace hb {
 double hll_alpha_of(int p) { return hll_alpha(p); }
 void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
 }  // namespace hb
-
-struct hb_graph {
-    int64_t n = 0, m = 0;
-    int b = 4;
-    Layout y{};
-    uint64_t seed = 0;
-    hb_options opt{};
-    cudaStream_t s = nullptr;
-    bool fp32 = false, relabel = true, broken = false;
-    int step_grid = 0;
-    DevMem mem;
-    int64_t *off = nullptr;
-    int32_t *tgt = nullptr;
-    int64_t *roff = nullptr;
-    int32_t *rtgt = nullptr;
-    int32_t *perm = nullptr, *inv = nullptr;
-    Counters *ctr = nullptr;
-    Counters *ctr_host = nullptr;
-    int64_t seg_count[kSegs] = {0};
-    int64_t n_pos = 0;
-    int64_t heavy_total = 0;
-    StepArgs a{};
-    // host bookkeeping
-    int32_t t = 0;
-    bool converged = false;
-    int64_t last_changed = 0, last_nodes = 0, last_arcs = 0, total_arcs = 0;
-    int32_t last_sparse = 0;
-    int launches = 0;
-    bool profile = false;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    int64_t kernel_launches = 0;
-    double kernel_ms = 0.0, kernel_bytes = 0.0;
-
-    ~hb_graph() {
-        if (ev[0]) cudaEventDestroy(ev[0]);
-        if (ev[1]) cudaEventDestroy(ev[1]);
-        if (ctr_host) cudaFreeHost(ctr_host);
-        mem.free_all();
-    }
-};
 
 namespace {
 
@@ -244,10 +176,15 @@ hb_status finish_setup(hb_graph *g) {
     e = launch_dense_plan(a, g->y, g->seg_count, const_cast<Plan *>(a.plan_dense),
                           const_cast<int32_t *>(a.owner_dense), const_cast<int64_t *>(a.cstart_dense), s);
     if (e != cudaSuccess) return cuda_fail(e, "dense plan");
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, l2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     g->step_grid = sms * step_blocks_per_sm(g->b, g->fp32);
+    // the most gathered counters (lowest ids after the degree sort) that fit
+    // in half of L2 are gathered with an evict-last hint
+    const int64_t hot = g->relabel ? ((int64_t)l2 / 2) / P : 0;
+    a.hot_nodes = (int32_t)(hot < n ? hot : n);
     return HB_OK;
 }
 
@@ -376,7 +313,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         int64_t *noff = M.alloc<int64_t>(n + 1);
         int32_t *ntgt = M.alloc<int32_t>(m);
         if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory (relabel)"); }
-        e = degree_sort(in_off, n, g->perm, g->inv, s);
+        e = degree_sort(in_off, in_tgt, n, m, g->perm, g->inv, s);
         if (e == cudaSuccess) e = relabel_csr(in_off, in_tgt, n, m, g->perm, g->inv, noff, ntgt, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { delete g; return cuda_fail(e, "relabel"); }
@@ -395,6 +332,29 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     *out = g;
     return HB_OK;
 }
+
+}  // namespace
+
+namespace hb {
+
+hb_status create_handle64(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                          int log2m, uint64_t seed, const hb_options *opt, hb_graph **out) {
+    return create_impl<int64_t>(offsets, targets, n, m, log2m, seed, opt, out);
+}
+
+hb_status sync_host_state(hb_graph *g) {
+    cudaError_t e = cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    if (e != cudaSuccess) return cuda_fail(e, "device counters");
+    g->t = g->ctr_host->steps_done;
+    g->converged = g->ctr_host->converged != 0;
+    g->last_changed = (int64_t)g->ctr_host->n_changed;
+    return HB_OK;
+}
+
+}  // namespace hb
+
+namespace {
 
 hb_status check(hb_graph *g) {
     if (!g) return fail(HB_ERR_INVALID, "handle is NULL");

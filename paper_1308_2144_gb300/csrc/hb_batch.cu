@@ -1,0 +1,606 @@
+// hb_batch.cu -- the batched form: many independent HyperBall problems
+// (graphs of uneven size, each with its own log2m, seed, iteration index
+// and frontier) advanced together.  Every kernel of an iteration covers
+// all graphs in one launch: work items of all graphs form one index space
+// (per-graph prefix sums), a warp looks its graph up by binary search and
+// runs the same per-node code as the single-graph kernels.  The iteration
+// is captured once into a CUDA graph; a run to every fixpoint is one graph
+// launch whose conditional while node repeats the iteration on the device
+// until no graph is active or the iteration cap is reached.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "hb_handle.h"
+#include "hb_step_dev.cuh"
+
+namespace hb {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kMaxBatch = 4096;
+constexpr int kMode_Idle = 2;
+
+struct BatchCtl {
+    int32_t n_active;
+    int32_t iterations;
+    int32_t max_steps;
+    int32_t k;
+    unsigned long long total_arcs;
+};
+
+struct BatchArrays {
+    const StepArgs *args;          // [k]
+    int64_t *item_prefix;          // [k+1] work items of the running iteration
+    int64_t *list_prefix;          // [k+1] previous changed lists (push marking)
+    int64_t *big_prefix;           // [k+1] previous many-predecessor lists
+    int64_t *copy_prefix;          // [k+1] copy-forward elements
+    int64_t *word_prefix;          // [k+1] must-check bitmap words to clear
+    const int64_t *tile_prefix;    // [k+1] 256-node tiles (static)
+    int64_t *graph_arcs;           // [k] arcs scanned per graph since init
+    BatchCtl *ctl;
+    int k;
+    int use_cond;
+    cudaGraphConditionalHandle cond;
+};
+
+__device__ __forceinline__ int find_graph(const int64_t *prefix, int k, int64_t i) {
+    int lo = 0, hi = k;   // prefix[lo] <= i < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int logsmax_of(int b) { return 5 - ((b - 4) < 5 ? (b - 4) : 5); }
+
+// Exclusive prefix over graphs of a per-graph value, by one block.
+template <class F>
+__device__ void graph_prefix(int k, int64_t *out, F value) {
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < k; base += blockDim.x) {
+        const int g = base + threadIdx.x;
+        const int64_t v = g < k ? value(g) : 0;
+        int64_t ex;
+        const int64_t tot = block_excl_scan(v, ex);
+        if (g < k) out[g] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = carry;
+    __syncthreads();
+}
+
+__global__ void batch_begin_kernel(BatchArrays B) {
+    for (int g = threadIdx.x; g < B.k; g += blockDim.x) {
+        const StepArgs &a = B.args[g];
+        Counters *c = a.ctr;
+        if (c->converged) {
+            c->t = c->steps_done;
+            c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
+            for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
+            c->mode = kMode_Idle;
+        } else {
+            begin_one(a);
+        }
+    }
+    __syncthreads();
+    auto push_ok = [&](int g) {
+        const StepArgs &a = B.args[g];
+        return a.ctr->mode == 1 && a.has_reverse && a.frontier != HB_FRONTIER_PULL;
+    };
+    graph_prefix(B.k, B.list_prefix, [&](int g) {
+        return push_ok(g) ? (int64_t)B.args[g].ctr->prev_list_len : 0; });
+    graph_prefix(B.k, B.big_prefix, [&](int g) {
+        return push_ok(g) ? (int64_t)B.args[g].ctr->prev_big : 0; });
+    graph_prefix(B.k, B.copy_prefix, [&](int g) {
+        const StepArgs &a = B.args[g];
+        return a.ctr->mode == 1 ? (int64_t)a.ctr->prev_list_len << (a.b - 4) : 0; });
+    graph_prefix(B.k, B.word_prefix, [&](int g) {
+        const StepArgs &a = B.args[g];
+        return a.ctr->mode == 1 ? (a.n + 31) / 32 : 0; });
+}
+
+__global__ void batch_clear_bits_kernel(BatchArrays B) {
+    const int64_t total = B.word_prefix[B.k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = find_graph(B.word_prefix, B.k, i);
+        B.args[g].mustbits[i - B.word_prefix[g]] = 0u;
+    }
+}
+
+__global__ void batch_mark_push_kernel(BatchArrays B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = B.list_prefix[B.k];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < total; i += nw) {
+        const int g = find_graph(B.list_prefix, B.k, i);
+        const StepArgs &a = B.args[g];
+        const int t = a.ctr->t;
+        const int32_t w = a.clist[(t + 1) & 1][i - B.list_prefix[g]];
+        if (a.roff[w + 1] - a.roff[w] > kBigRdeg) continue;
+        push_warp(a, w, lane);
+    }
+    // nodes with many predecessors: one block each
+    const int64_t nbig = B.big_prefix[B.k];
+    const int wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t q = blockIdx.x; q < nbig; q += gridDim.x) {
+        const int g = find_graph(B.big_prefix, B.k, q);
+        const StepArgs &a = B.args[g];
+        const int t = a.ctr->t;
+        const int32_t w = a.biglist[(t + 1) & 1][q - B.big_prefix[g]];
+        const int64_t r0 = a.roff[w], r1 = a.roff[w + 1];
+        for (int64_t j0 = r0 + 32 * wid; j0 < r1; j0 += 32 * nwarps) {
+            const int64_t j = j0 + lane;
+            mark_append(a, j < r1 ? a.rtgt[j] : -1, lane);
+        }
+    }
+}
+
+__global__ void batch_copy_forward_kernel(BatchArrays B) {
+    const int64_t total = B.copy_prefix[B.k];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int g = find_graph(B.copy_prefix, B.k, i);
+        const StepArgs &a = B.args[g];
+        copy_forward_one(a, a.ctr->t, i - B.copy_prefix[g]);
+    }
+}
+
+// One block per graph: the work plan of graphs in frontier mode.
+__global__ void batch_plan_kernel(BatchArrays B) {
+    for (int g = blockIdx.x; g < B.k; g += gridDim.x) {
+        const StepArgs &a = B.args[g];
+        if (a.ctr->mode != 1) continue;
+        PlanParams pp{};
+        const int ls = logsmax_of(a.b);
+        pp.chunk = 64LL << ls;
+        pp.nlight = ls + 1;
+        pp.dense = 0;
+        plan_block(a, pp, a.plan_sparse, a.owner_sparse, a.cstart_sparse);
+        __syncthreads();
+    }
+}
+
+__global__ void batch_items_kernel(BatchArrays B) {
+    graph_prefix(B.k, B.item_prefix, [&](int g) -> int64_t {
+        const StepArgs &a = B.args[g];
+        const int mode = a.ctr->mode;
+        if (mode == kMode_Idle) return 0;
+        return mode == 1 ? a.plan_sparse->items : a.plan_dense->items;
+    });
+}
+
+// Work item `it` of one graph (the body of the single-graph step kernel's
+// loop, with the plan read from memory).
+template <int LOG2P, bool F32>
+__device__ __forceinline__ void batch_item(const StepArgs &a, int64_t it, int t, bool sparse,
+                                           double rdist64, float rdist32,
+                                           const unsigned long long *pow2, bool prefetch,
+                                           unsigned long long *cnt) {
+    using C = Cfg<LOG2P>;
+    const Plan *pl = sparse ? a.plan_sparse : a.plan_dense;
+    const int32_t *list = sparse ? a.slist : a.dense_list;
+    const uint8_t *cur = a.regs[t & 1];
+    uint8_t *nxt = a.regs[(t + 1) & 1];
+    int32_t *clist = a.clist[t & 1];
+    int32_t *biglist = a.biglist[t & 1];
+    const int64_t hch = pl->heavy_chunks;
+    if (it < hch) {
+        heavy_item<LOG2P, F32>(a, cur, nxt, t, it, sparse ? a.owner_sparse : a.owner_dense,
+                               sparse ? a.cstart_sparse : a.cstart_dense, list, clist, biglist, sparse,
+                               cnt, rdist64, rdist32, pow2);
+        return;
+    }
+    const int64_t li = it - hch;
+    int j = 0;
+#pragma unroll
+    for (int q = 1; q < C::NLIGHT; ++q)
+        if (li >= pl->item_begin[q]) j = q;
+    const int64_t seg0 = a.seg_begin[j + 1];
+    const int64_t pos0 = seg0 + ((li - pl->item_begin[j]) << j);
+    light_item<LOG2P, F32>(a, cur, nxt, t, pos0, seg0 + pl->count[j + 1], C::LOGSMAX - j, list, clist,
+                           biglist, sparse, cnt, rdist64, rdist32, pow2, prefetch);
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(kStepThreads, 3) batch_step_kernel(BatchArrays B) {
+    extern __shared__ int64_t s_prefix[];                 // [k+1]
+    __shared__ unsigned long long s_pow2[kMaxLog2m - kMinLog2m + 1][64];
+    __shared__ unsigned long long s_cnt[kStepThreads / 32];
+    for (int i = threadIdx.x; i <= B.k; i += blockDim.x) s_prefix[i] = B.item_prefix[i];
+    for (int i = threadIdx.x; i < (kMaxLog2m - kMinLog2m + 1) * 64; i += blockDim.x) {
+        const int b = kMinLog2m + i / 64, M = i % 64, sh = 64 - b;
+        s_pow2[i / 64][M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) s_cnt[wid] = 0;
+    __syncthreads();
+    const int64_t total = s_prefix[B.k];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int cur_g = -1, t = 0;
+    bool sparse = false, prefetch = false;
+    double rd64 = 1.0;
+    float rd32 = 1.0f;
+    for (int64_t it = gw; it < total; it += nw) {
+        const int g = find_graph(s_prefix, B.k, it);
+        const StepArgs &a = B.args[g];
+        if (g != cur_g) {
+            if (cur_g >= 0 && lane == 0 && s_cnt[wid]) {
+                atomicAdd(&B.args[cur_g].ctr->n_changed, s_cnt[wid]);
+                s_cnt[wid] = 0;
+            }
+            cur_g = g;
+            const Counters *c = a.ctr;
+            t = c->t;
+            sparse = c->mode == 1;
+            prefetch = !sparse && (t == 0 || 4 * (int64_t)c->prev_changed > a.n_pos);
+            rd64 = 1.0 / (double)(t + 1);
+            rd32 = 1.0f / (float)(t + 1);
+        }
+        __syncwarp();
+        const int64_t local = it - s_prefix[g];
+        const unsigned long long *pow2 = s_pow2[a.b - kMinLog2m];
+        switch (a.b) {
+#define HB_CASE(LB) case LB: batch_item<LB, F32>(a, local, t, sparse, rd64, rd32, pow2, prefetch, &s_cnt[wid]); break;
+            HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+            HB_CASE(12)
+#undef HB_CASE
+            default: break;
+        }
+    }
+    __syncwarp();
+    if (cur_g >= 0 && lane == 0 && s_cnt[wid]) atomicAdd(&B.args[cur_g].ctr->n_changed, s_cnt[wid]);
+}
+
+// Changed-list compaction for graphs that ran a dense iteration.
+__global__ void __launch_bounds__(256) batch_compact_kernel(BatchArrays B) {
+    const int64_t total = B.tile_prefix[B.k];
+    for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int g = find_graph(B.tile_prefix, B.k, tile);
+        const StepArgs &a = B.args[g];
+        if (a.ctr->mode != 0 || a.frontier == HB_FRONTIER_OFF) continue;
+        compact_tile(a, a.ctr->t, (tile - B.tile_prefix[g]) * 256);
+    }
+}
+
+__global__ void batch_end_kernel(BatchArrays B) {
+    __shared__ int active;
+    __shared__ unsigned long long arcs;
+    if (threadIdx.x == 0) { active = 0; arcs = 0; }
+    __syncthreads();
+    for (int g = threadIdx.x; g < B.k; g += blockDim.x) {
+        const StepArgs &a = B.args[g];
+        Counters *c = a.ctr;
+        if (c->mode != kMode_Idle) {
+            end_one(a);
+            const int64_t scanned = c->mode == 1 ? (int64_t)c->arcs : a.m;
+            B.graph_arcs[g] += scanned;
+            atomicAdd(&arcs, (unsigned long long)scanned);
+        }
+        if (!c->converged) atomicAdd(&active, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        BatchCtl *ctl = B.ctl;
+        ctl->n_active = active;
+        ctl->iterations += 1;
+        ctl->total_arcs += arcs;
+        if (B.use_cond)
+            cudaGraphSetConditional(B.cond, (active > 0 && ctl->iterations < ctl->max_steps) ? 1u : 0u);
+    }
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
+
+}  // namespace
+
+}  // namespace hb
+
+using namespace hb;
+
+struct hb_batch {
+    int k = 0;
+    std::vector<hb_graph *> graphs;
+    bool fp32 = false;
+    bool own_stream = false;
+    cudaStream_t s = nullptr;
+    int step_grid = 0;
+    int aux_grid = 0;
+    DevMem mem;
+    BatchArrays B{};
+    BatchCtl *ctl_host = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    cudaGraphExec_t run_exec = nullptr;
+    cudaGraph_t step_graph = nullptr;
+    cudaGraph_t run_graph = nullptr;
+    int32_t max_steps = 1 << 20;
+
+    ~hb_batch() {
+        if (step_exec) cudaGraphExecDestroy(step_exec);
+        if (run_exec) cudaGraphExecDestroy(run_exec);
+        if (step_graph) cudaGraphDestroy(step_graph);
+        if (run_graph) cudaGraphDestroy(run_graph);
+        for (hb_graph *g : graphs) hb_destroy(g);
+        if (ctl_host) cudaFreeHost(ctl_host);
+        mem.free_all();
+        if (own_stream && s) cudaStreamDestroy(s);
+    }
+};
+
+namespace {
+
+hb_status bfail(hb_status st, const std::string &m) {
+    set_last_error(m.c_str());
+    return st;
+}
+
+// The kernels of one batched iteration, enqueued on b->s (captured).
+cudaError_t enqueue_iteration(hb_batch *b, const BatchArrays &B) {
+    cudaStream_t s = b->s;
+    batch_begin_kernel<<<1, 1024, 0, s>>>(B);
+    batch_clear_bits_kernel<<<b->aux_grid, 256, 0, s>>>(B);
+    batch_mark_push_kernel<<<b->step_grid, kStepThreads, 0, s>>>(B);
+    batch_copy_forward_kernel<<<b->aux_grid, 256, 0, s>>>(B);
+    batch_plan_kernel<<<b->k < 65535 ? b->k : 65535, 1024, 0, s>>>(B);
+    batch_items_kernel<<<1, 1024, 0, s>>>(B);
+    const size_t smem = sizeof(int64_t) * (size_t)(B.k + 1);
+    if (b->fp32) batch_step_kernel<true><<<b->step_grid, kStepThreads, smem, s>>>(B);
+    else batch_step_kernel<false><<<b->step_grid, kStepThreads, smem, s>>>(B);
+    batch_compact_kernel<<<b->aux_grid, 256, 0, s>>>(B);
+    batch_end_kernel<<<1, 1024, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+hb_status build_graphs(hb_batch *b) {
+    cudaError_t e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        BatchArrays B = b->B;
+        B.use_cond = 0;
+        e = enqueue_iteration(b, B);
+        cudaError_t e2 = cudaStreamEndCapture(b->s, &b->step_graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->step_exec, b->step_graph, 0);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch iteration graph: ") + cudaGetErrorString(e));
+
+    // run to every fixpoint: while (active && iterations < cap) { iteration }
+    e = cudaGraphCreate(&b->run_graph, 0);
+    cudaGraphConditionalHandle cond;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cond, b->run_graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&node, b->run_graph, nullptr, nullptr, 0, &cp);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(b->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            BatchArrays B = b->B;
+            B.use_cond = 1;
+            B.cond = cond;
+            e = enqueue_iteration(b, B);
+            cudaGraph_t out = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(b->s, &out);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->run_exec, b->run_graph, 0);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch loop graph: ") + cudaGetErrorString(e));
+    return HB_OK;
+}
+
+hb_status reset_ctl(hb_batch *b) {
+    BatchCtl c{};
+    c.k = b->k;
+    c.max_steps = b->max_steps;
+    cudaError_t e = cudaMemcpyAsync(b->B.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->B.graph_arcs, 0, sizeof(int64_t) * b->k, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch reset: ") + cudaGetErrorString(e));
+    return HB_OK;
+}
+
+hb_status read_ctl(hb_batch *b) {
+    cudaError_t e = cudaMemcpyAsync(b->ctl_host, b->B.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+    return HB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hb_status hb_batch_create(int k, const hb_graph_desc *gs, const hb_options *opt, hb_batch **out) {
+    set_last_error("");
+    if (!out) return bfail(HB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (k < 1 || k > kMaxBatch) return bfail(HB_ERR_INVALID, "k must lie in [1, 4096]");
+    if (!gs) return bfail(HB_ERR_INVALID, "gs is NULL");
+    hb_options o;
+    if (opt) o = *opt; else hb_default_options(&o);
+    if (o.max_steps <= 0) o.max_steps = 1 << 20;
+    if (o.frontier == HB_FRONTIER_PULL) o.frontier = HB_FRONTIER_AUTO;
+    o.flags &= ~(uint32_t)HB_PROFILE;
+    hb_batch *b = new hb_batch();
+    b->k = k;
+    b->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
+    b->max_steps = o.max_steps;
+    if (o.stream) {
+        b->s = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(HB_ERR_CUDA, "cannot create the batch stream");
+        }
+        b->own_stream = true;
+    }
+    o.stream = b->s;
+    for (int i = 0; i < k; ++i) {
+        hb_graph *g = nullptr;
+        hb_status st = create_handle64(gs[i].offsets, gs[i].targets, gs[i].n, gs[i].m, gs[i].log2m,
+                                       gs[i].seed, &o, &g);
+        if (st != HB_OK) {
+            std::string msg = std::string("graph ") + std::to_string(i) + ": " + hb_last_error();
+            delete b;
+            return bfail(st, msg);
+        }
+        b->graphs.push_back(g);
+    }
+    DevMem &M = b->mem;
+    StepArgs *args = M.alloc<StepArgs>(k);
+    int64_t *pref = M.alloc<int64_t>((size_t)6 * (k + 1));
+    int64_t *garcs = M.alloc<int64_t>(k);
+    BatchCtl *ctl = M.alloc<BatchCtl>(1);
+    if (M.err != cudaSuccess || cudaMallocHost(&b->ctl_host, sizeof(BatchCtl)) != cudaSuccess) {
+        delete b;
+        return bfail(HB_ERR_OOM, "out of memory (batch arrays)");
+    }
+    std::vector<StepArgs> hargs(k);
+    std::vector<int64_t> tiles(k + 1, 0);
+    for (int i = 0; i < k; ++i) {
+        hargs[i] = b->graphs[i]->a;
+        tiles[i + 1] = tiles[i] + (b->graphs[i]->n + 255) / 256;
+    }
+    cudaError_t e = cudaMemcpyAsync(args, hargs.data(), sizeof(StepArgs) * k, cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pref + 5 * (k + 1), tiles.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, b->s);
+    if (e != cudaSuccess) { delete b; return bfail(HB_ERR_CUDA, "batch upload"); }
+    BatchArrays &B = b->B;
+    B.args = args;
+    B.item_prefix = pref;
+    B.list_prefix = pref + (k + 1);
+    B.big_prefix = pref + 2 * (k + 1);
+    B.copy_prefix = pref + 3 * (k + 1);
+    B.word_prefix = pref + 4 * (k + 1);
+    B.tile_prefix = pref + 5 * (k + 1);
+    B.graph_arcs = garcs;
+    B.ctl = ctl;
+    B.k = k;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = sizeof(int64_t) * (size_t)(k + 1);
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(batch_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(batch_step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (b->fp32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<true>, kStepThreads, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<false>, kStepThreads, smem);
+    b->step_grid = sms * (per > 0 ? per : 1);
+    b->aux_grid = sms * 8;
+    hb_status st = reset_ctl(b);
+    if (st == HB_OK) st = build_graphs(b);
+    if (st != HB_OK) { delete b; return st; }
+    *out = b;
+    return HB_OK;
+}
+
+hb_status hb_batch_step(hb_batch *b, int32_t *n_active) {
+    if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    cudaError_t e = cudaGraphLaunch(b->step_exec, b->s);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+    hb_status st = read_ctl(b);
+    if (st != HB_OK) return st;
+    if (n_active) *n_active = b->ctl_host->n_active;
+    return HB_OK;
+}
+
+hb_status hb_batch_run(hb_batch *b, int32_t *iterations) {
+    if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    cudaError_t e = cudaGraphLaunch(b->run_exec, b->s);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
+    hb_status st = read_ctl(b);
+    if (st != HB_OK) return st;
+    if (iterations) *iterations = b->ctl_host->iterations;
+    if (b->ctl_host->n_active > 0)
+        return bfail(HB_ERR_NOT_CONVERGED, "the iteration cap was reached before every graph converged");
+    return HB_OK;
+}
+
+hb_status hb_batch_reset(hb_batch *b, const uint64_t *seeds) {
+    if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    for (int i = 0; i < b->k; ++i) {
+        hb_graph *g = b->graphs[i];
+        hb_status st = hb_reset(g, seeds ? seeds[i] : g->seed);
+        if (st != HB_OK) return st;
+    }
+    return reset_ctl(b);
+}
+
+static hb_status graph_of(hb_batch *b, int i, hb_graph **g) {
+    if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    if (i < 0 || i >= b->k) return bfail(HB_ERR_INVALID, "graph index out of range");
+    *g = b->graphs[i];
+    return sync_host_state(*g);
+}
+
+hb_status hb_batch_get_centralities(hb_batch *b, int i, double *closeness, double *harmonic,
+                                    double *lin, double *reachable) {
+    hb_graph *g;
+    hb_status st = graph_of(b, i, &g);
+    return st != HB_OK ? st : hb_get_centralities(g, closeness, harmonic, lin, reachable);
+}
+
+hb_status hb_batch_get_registers(hb_batch *b, int i, uint8_t *out) {
+    hb_graph *g;
+    hb_status st = graph_of(b, i, &g);
+    return st != HB_OK ? st : hb_get_registers(g, out);
+}
+
+hb_status hb_batch_get_accumulators(hb_batch *b, int i, double *sumd, double *harm) {
+    hb_graph *g;
+    hb_status st = graph_of(b, i, &g);
+    return st != HB_OK ? st : hb_get_accumulators(g, sumd, harm);
+}
+
+hb_status hb_batch_get_info(hb_batch *b, int i, hb_info *info) {
+    hb_graph *g;
+    hb_status st = graph_of(b, i, &g);
+    if (st != HB_OK) return st;
+    st = hb_get_info(g, info);
+    if (st != HB_OK) return st;
+    int64_t arcs = 0;
+    cudaError_t e = cudaMemcpy(&arcs, b->B.graph_arcs + i, sizeof(arcs), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, "batch info");
+    info->total_arcs = arcs;
+    return HB_OK;
+}
+
+hb_status hb_batch_get_totals(hb_batch *b, int32_t *iterations, int32_t *n_active, int64_t *arcs) {
+    if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    hb_status st = read_ctl(b);
+    if (st != HB_OK) return st;
+    if (iterations) *iterations = b->ctl_host->iterations;
+    if (n_active) *n_active = b->ctl_host->n_active;
+    if (arcs) *arcs = (int64_t)b->ctl_host->total_arcs;
+    return HB_OK;
+}
+
+void hb_batch_destroy(hb_batch *b) {
+    if (!b) return;
+    if (b->s) cudaStreamSynchronize(b->s);
+    delete b;
+}
+
+}  // extern "C"

@@ -121,14 +121,29 @@ __device__ __forceinline__ int degree_bucket(int64_t d) {
     return 119 - b;   // larger degree, smaller key
 }
 
-__global__ void part_count(const int64_t *off, int64_t n, int64_t ntiles, int64_t *counts) {
+__global__ void key_out_kernel(const int64_t *off, int64_t n, uint8_t *key) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        key[v] = (uint8_t)degree_bucket(off[v + 1] - off[v]);
+}
+
+__global__ void key_in_kernel(const unsigned long long *indeg, int64_t n, uint8_t *key) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        key[v] = (uint8_t)degree_bucket((int64_t)indeg[v]);
+}
+
+// Stable partition of the sequence src (identity if null) by key[node]:
+// per-tile bucket counts, a scan, then an order-preserving scatter.
+__global__ void part_count(const int32_t *src, const uint8_t *key, int64_t n, int64_t ntiles,
+                           int64_t *counts) {
     __shared__ int hist[kBuckets];
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) hist[k] = 0;
         __syncthreads();
         for (int i = threadIdx.x; i < kPartTile; i += blockDim.x) {
-            int64_t v = tile * kPartTile + i;
-            if (v < n) atomicAdd(&hist[degree_bucket(off[v + 1] - off[v])], 1);
+            int64_t q = tile * kPartTile + i;
+            if (q < n) atomicAdd(&hist[key[src ? src[q] : q]], 1);
         }
         __syncthreads();
         for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) counts[(int64_t)k * ntiles + tile] = hist[k];
@@ -136,8 +151,8 @@ __global__ void part_count(const int64_t *off, int64_t n, int64_t ntiles, int64_
     }
 }
 
-__global__ void part_scatter(const int64_t *off, int64_t n, int64_t ntiles, const int64_t *offs,
-                             int32_t *perm, int32_t *inv) {
+__global__ void part_scatter(const int32_t *src, const uint8_t *key, int64_t n, int64_t ntiles,
+                             const int64_t *offs, int32_t *out, int32_t *inv) {
     __shared__ int64_t base[kBuckets];
     __shared__ int wcnt[kPartThreads / 32][kBuckets];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -148,24 +163,25 @@ __global__ void part_scatter(const int64_t *off, int64_t n, int64_t ntiles, cons
             for (int k = threadIdx.x; k < (kPartThreads / 32) * kBuckets; k += blockDim.x)
                 (&wcnt[0][0])[k] = 0;
             __syncthreads();
-            int64_t v = tile * kPartTile + (int64_t)r * kPartThreads + threadIdx.x;
-            bool valid = v < n;
-            int key = valid ? degree_bucket(off[v + 1] - off[v]) : -1;
-            unsigned peers = __match_any_sync(0xffffffffu, key);
-            int rank = __popc(peers & lanemask_lt());
-            if (valid && lane == __ffs(peers) - 1) wcnt[wid][key] = __popc(peers);
+            const int64_t q = tile * kPartTile + (int64_t)r * kPartThreads + threadIdx.x;
+            const bool valid = q < n;
+            const int64_t v = valid ? (src ? (int64_t)src[q] : q) : 0;
+            const int k = valid ? (int)key[v] : -1;
+            const unsigned peers = __match_any_sync(0xffffffffu, k);
+            const int rank = __popc(peers & lanemask_lt());
+            if (valid && lane == __ffs(peers) - 1) wcnt[wid][k] = __popc(peers);
             __syncthreads();
             if (valid) {
-                int64_t pos = base[key] + rank;
-                for (int w = 0; w < wid; ++w) pos += wcnt[w][key];
-                perm[pos] = (int32_t)v;
-                inv[v] = (int32_t)pos;
+                int64_t pos = base[k] + rank;
+                for (int w = 0; w < wid; ++w) pos += wcnt[w][k];
+                out[pos] = (int32_t)v;
+                if (inv) inv[v] = (int32_t)pos;
             }
             __syncthreads();
-            for (int k = threadIdx.x; k < kBuckets; k += blockDim.x) {
-                int s = 0;
-                for (int w = 0; w < kPartThreads / 32; ++w) s += wcnt[w][k];
-                base[k] += s;
+            for (int kk = threadIdx.x; kk < kBuckets; kk += blockDim.x) {
+                int sum = 0;
+                for (int w = 0; w < kPartThreads / 32; ++w) sum += wcnt[w][kk];
+                base[kk] += sum;
             }
             __syncthreads();
         }
@@ -291,20 +307,47 @@ cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int
     return e;
 }
 
-cudaError_t degree_sort(const int64_t *off, int64_t n, int32_t *perm, int32_t *inv, cudaStream_t s) {
+// Node order for the step kernel: out-degree buckets descending (so every
+// degree class is a contiguous id range), and within a bucket in-degree
+// buckets descending (the most gathered counters share L2 lines); two
+// stable partitions, least significant key first.
+cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
+                        int32_t *inv, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    int64_t ntiles = (n + kPartTile - 1) / kPartTile;
+    const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
     int64_t *counts = nullptr;
+    unsigned long long *indeg = nullptr;
+    uint8_t *keys = nullptr;
+    int32_t *perm1 = nullptr;
     cudaError_t e = cudaMallocAsync(&counts, sizeof(int64_t) * kBuckets * ntiles * 2, s);
-    if (e != cudaSuccess) return e;
-    int g = (int)(ntiles < 152 * 8 ? ntiles : 152 * 8);
-    part_count<<<g, kPartThreads, 0, s>>>(off, n, ntiles, counts);
-    e = scan_exclusive_i64(counts, counts + kBuckets * ntiles, kBuckets * ntiles, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&indeg, sizeof(unsigned long long) * n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&keys, 2 * (size_t)n, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&perm1, sizeof(int32_t) * n, s);
     if (e == cudaSuccess) {
-        part_scatter<<<g, kPartThreads, 0, s>>>(off, n, ntiles, counts + kBuckets * ntiles, perm, inv);
-        e = cudaGetLastError();
+        cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * n, s);
+        if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, indeg);
+        key_in_kernel<<<grid_for(n, 256), 256, 0, s>>>(indeg, n, keys);
+        key_out_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, keys + n);
+        const int g = (int)(ntiles < 152 * 8 ? ntiles : 152 * 8);
+        // pass 1: by in-degree bucket
+        part_count<<<g, kPartThreads, 0, s>>>(nullptr, keys, n, ntiles, counts);
+        e = scan_exclusive_i64(counts, counts + kBuckets * ntiles, kBuckets * ntiles, s);
+        if (e == cudaSuccess)
+            part_scatter<<<g, kPartThreads, 0, s>>>(nullptr, keys, n, ntiles, counts + kBuckets * ntiles,
+                                                     perm1, nullptr);
+        // pass 2 (stable): by out-degree bucket
+        if (e == cudaSuccess) part_count<<<g, kPartThreads, 0, s>>>(perm1, keys + n, n, ntiles, counts);
+        if (e == cudaSuccess) e = scan_exclusive_i64(counts, counts + kBuckets * ntiles, kBuckets * ntiles, s);
+        if (e == cudaSuccess) {
+            part_scatter<<<g, kPartThreads, 0, s>>>(perm1, keys + n, n, ntiles, counts + kBuckets * ntiles,
+                                                     perm, inv);
+            e = cudaGetLastError();
+        }
     }
     cudaFreeAsync(counts, s);
+    cudaFreeAsync(indeg, s);
+    cudaFreeAsync(keys, s);
+    cudaFreeAsync(perm1, s);
     return e;
 }
 

@@ -1,0 +1,91 @@
+// hb_handle.h -- the hb_graph handle (internal: shared by the C-ABI
+// implementation and the batched / served forms).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "hb_internal.cuh"
+#include "hyperball.h"
+
+namespace hb {
+
+// Device allocations owned by a handle, freed together.
+struct DevMem {
+    std::vector<void *> blocks;
+    size_t bytes = 0;
+    cudaError_t err = cudaSuccess;
+    template <class T>
+    T *alloc(size_t count) {
+        if (err != cudaSuccess) return nullptr;
+        void *p = nullptr;
+        size_t sz = count * sizeof(T);
+        if (sz == 0) sz = 16;
+        err = cudaMalloc(&p, sz);
+        if (err != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        blocks.push_back(p);
+        bytes += sz;
+        return static_cast<T *>(p);
+    }
+    void release(void *p) {
+        for (size_t i = 0; i < blocks.size(); ++i)
+            if (blocks[i] == p) { cudaFree(p); blocks.erase(blocks.begin() + (long)i); return; }
+    }
+    void free_all() {
+        for (void *p : blocks) cudaFree(p);
+        blocks.clear();
+    }
+};
+
+
+// Host-side services of hb_api.cu used by the other translation units.
+hb_status create_handle64(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                          int log2m, uint64_t seed, const hb_options *opt, hb_graph **out);
+// Bring the handle's host bookkeeping (t, convergence) up to date with its
+// device counters after kernels launched outside hb_step.
+hb_status sync_host_state(hb_graph *g);
+
+}  // namespace hb
+
+using namespace hb;
+
+struct hb_graph {
+    int64_t n = 0, m = 0;
+    int b = 4;
+    Layout y{};
+    uint64_t seed = 0;
+    hb_options opt{};
+    cudaStream_t s = nullptr;
+    bool fp32 = false, relabel = true, broken = false;
+    int step_grid = 0;
+    DevMem mem;
+    int64_t *off = nullptr;
+    int32_t *tgt = nullptr;
+    int64_t *roff = nullptr;
+    int32_t *rtgt = nullptr;
+    int32_t *perm = nullptr, *inv = nullptr;
+    Counters *ctr = nullptr;
+    Counters *ctr_host = nullptr;
+    int64_t seg_count[kSegs] = {0};
+    int64_t n_pos = 0;
+    int64_t heavy_total = 0;
+    StepArgs a{};
+    // host bookkeeping
+    int32_t t = 0;
+    bool converged = false;
+    int64_t last_changed = 0, last_nodes = 0, last_arcs = 0, total_arcs = 0;
+    int32_t last_sparse = 0;
+    int launches = 0;
+    bool profile = false;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int64_t kernel_launches = 0;
+    double kernel_ms = 0.0, kernel_bytes = 0.0;
+
+    ~hb_graph() {
+        if (ev[0]) cudaEventDestroy(ev[0]);
+        if (ev[1]) cudaEventDestroy(ev[1]);
+        if (ctr_host) cudaFreeHost(ctr_host);
+        mem.free_all();
+    }
+};
+

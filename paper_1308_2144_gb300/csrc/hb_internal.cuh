@@ -139,6 +139,7 @@ struct StepArgs {
     int32_t b;
     int32_t frontier;             // HB_FRONTIER_* policy
     int32_t has_reverse;          // roff/rtgt present
+    int32_t hot_nodes;            // counters of nodes below this id are kept in L2
     double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
 };
 
@@ -175,6 +176,29 @@ __device__ __forceinline__ uint4 shfl_xor16(uint4 a, int o) {
 // Counter loads: the read buffer does not change during a step.
 __device__ __forceinline__ uint4 ld_counter(const uint8_t *p) {
     return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// Counter loads with an L2 eviction policy (from createpolicy): counters of
+// the most gathered nodes (low ids after the degree sort) are kept with
+// evict_last, the rest use evict_first so they do not displace them.
+__device__ __forceinline__ uint4 ld_counter_policy(const uint8_t *p, uint64_t pol) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p), "l"(pol));
+    return r;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
 }
 
 // Targets are streamed once per step.
@@ -312,7 +336,8 @@ cudaError_t validate_csr(const int64_t *off, const int32_t *tgt, int64_t n, int6
 cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaStream_t s);
 cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                           int64_t *toff, int32_t *ttgt, cudaStream_t s);
-cudaError_t degree_sort(const int64_t *off, int64_t n, int32_t *perm, int32_t *inv, cudaStream_t s);
+cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
+                        int32_t *inv, cudaStream_t s);
 cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                         const int32_t *perm, const int32_t *inv, int64_t *noff, int32_t *ntgt,
                         cudaStream_t s);

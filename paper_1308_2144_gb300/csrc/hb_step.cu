@@ -14,24 +14,13 @@
 //   step_kernel     gather + register-wise max (union), changed test,
 //                   estimator and accumulators for changed nodes
 //   step_end        count the iteration, record convergence
-#include "hb_internal.cuh"
-
-#include "hyperball.h"
-
-// Arcs in flight per lane when a lane holds one 16-byte chunk of a counter,
-// and the minimum resident blocks the step kernel is compiled for.
-#ifndef HB_UNROLL
-#define HB_UNROLL 8
-#endif
-#ifndef HB_MIN_BLOCKS
-#define HB_MIN_BLOCKS 6
-#endif
+#include "hb_step_dev.cuh"
 
 namespace hb {
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
+using namespace dev;
 
 // ---------------------------------------------------------- estimator --
 
@@ -95,31 +84,9 @@ __global__ void init_nodes_kernel(StepArgs a, const int32_t *perm, uint64_t seed
 
 // -------------------------------------------------------- step control --
 
-__global__ void step_begin_kernel(StepArgs a) {
-    Counters *c = a.ctr;
-    const int t = c->steps_done;
-    c->t = t;
-    c->prev_changed = c->n_changed;
-    c->prev_list_len = c->list_len;
-    c->prev_push_arcs = c->push_arcs;
-    c->prev_big = c->n_big;
-    c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
-    for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
-    int sparse = 0;
-    if (t > 0) {
-        if (a.frontier == HB_FRONTIER_PULL) sparse = 1;
-        else if (a.frontier == HB_FRONTIER_PUSH) sparse = a.has_reverse;
-        else if (a.frontier == HB_FRONTIER_AUTO)
-            sparse = a.has_reverse && (double)c->prev_push_arcs <= a.sparse_frac * (double)a.m;
-    }
-    c->mode = sparse;
-}
+__global__ void step_begin_kernel(StepArgs a) { begin_one(a); }
 
-__global__ void step_end_kernel(StepArgs a) {
-    Counters *c = a.ctr;
-    c->steps_done = c->t + 1;
-    if (c->n_changed == 0) c->converged = 1;
-}
+__global__ void step_end_kernel(StepArgs a) { end_one(a); }
 
 __global__ void clear_bits_kernel(StepArgs a, int64_t words) {
     if (a.ctr->mode != 1) return;
@@ -129,40 +96,6 @@ __global__ void clear_bits_kernel(StepArgs a, int64_t words) {
 }
 
 // ----------------------------------------------------- frontier marking --
-
-__device__ __forceinline__ int segment_of(const StepArgs &a, int64_t d) {
-#pragma unroll
-    for (int s = 0; s < kSegs; ++s)
-        if (d >= a.seg_lo[s] && d <= a.seg_hi[s]) return s;
-    return -1;
-}
-
-// Called by all 32 lanes; u < 0 for lanes with nothing to mark.  Sets the
-// must-check bit of u and, if it was clear, appends u to its degree
-// segment of the sparse list.
-__device__ __forceinline__ void mark_append(const StepArgs &a, int32_t u, int lane) {
-    int key = -1;
-    int64_t d = 0;
-    if (u >= 0) {
-        unsigned bit = 1u << (u & 31);
-        unsigned old = atomicOr(&a.mustbits[u >> 5], bit);
-        if (!(old & bit)) {
-            d = a.off[u + 1] - a.off[u];
-            key = segment_of(a, d);
-        }
-    }
-    unsigned peers = __match_any_sync(FULL, key);
-    int leader = __ffs(peers) - 1;
-    unsigned long long base = 0;
-    if (key >= 0 && lane == leader)
-        base = atomicAdd(&a.ctr->fill[key], (unsigned long long)__popc(peers));
-    base = __shfl_sync(FULL, base, leader);
-    if (key >= 0) a.slist[a.seg_begin[key] + (int64_t)base + __popc(peers & lanemask_lt())] = u;
-    unsigned long long dd = key >= 0 ? (unsigned long long)d : 0ULL;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) dd += __shfl_xor_sync(FULL, dd, o);
-    if (lane == 0 && dd) atomicAdd(&a.ctr->arcs, dd);
-}
 
 // Push: every node changed in the last iteration marks its predecessors.
 __global__ void mark_push_kernel(StepArgs a) {
@@ -177,12 +110,8 @@ __global__ void mark_push_kernel(StepArgs a) {
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = gw; i < np; i += nw) {
         const int32_t w = prev[i];
-        const int64_t r0 = a.roff[w], r1 = a.roff[w + 1];
-        if (r1 - r0 > kBigRdeg) continue;
-        for (int64_t j0 = r0; j0 < r1; j0 += 32) {
-            int64_t j = j0 + lane;
-            mark_append(a, j < r1 ? a.rtgt[j] : -1, lane);
-        }
+        if (a.roff[w + 1] - a.roff[w] > kBigRdeg) continue;
+        push_warp(a, w, lane);
     }
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t wbase = gw * 32;
@@ -221,79 +150,19 @@ __global__ void copy_forward_kernel(StepArgs a) {
     const Counters *c = a.ctr;
     if (c->mode != 1) return;
     const int t = c->t;
-    const int32_t *prev = a.clist[(t + 1) & 1];
-    const uint8_t *cur = a.regs[t & 1];
-    uint8_t *nxt = a.regs[(t + 1) & 1];
-    const int CH = (1 << a.b) >> 4;
-    const int logCH = a.b - 4;
-    const int64_t total = (int64_t)c->prev_list_len << logCH;
+    const int64_t total = (int64_t)c->prev_list_len << (a.b - 4);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = k >> logCH;
-        const int ch = (int)(k & (CH - 1));
-        const int32_t w = prev[i];
-        if (ch == 0) a.changed[w] = 0;
-        if (!((a.mustbits[w >> 5] >> (w & 31)) & 1u)) {
-            const int64_t o = ((int64_t)w << logCH) + ch;
-            reinterpret_cast<uint4 *>(nxt)[o] = reinterpret_cast<const uint4 *>(cur)[o];
-        }
-    }
+         k += (int64_t)gridDim.x * blockDim.x)
+        copy_forward_one(a, t, k);
 }
 
 // -------------------------------------------------------------- planning --
-
-struct PlanParams {
-    int64_t count[kSegs];   // dense: segment sizes
-    int64_t chunk;
-    int32_t nlight;
-    int32_t dense;
-};
 
 // One block.  Items: first the chunks of heavy nodes (chunk starts by a
 // block scan, then the chunk -> node map), then each light class packs
 // 2^j nodes per warp item.
 __global__ void plan_kernel(StepArgs a, PlanParams pp, Plan *plan, int32_t *owner, int64_t *cstart) {
-    if (!pp.dense && a.ctr->mode != 1) return;
-    __shared__ int64_t carry;
-    int64_t cnt[kSegs];
-    for (int s = 0; s < kSegs; ++s) cnt[s] = pp.dense ? pp.count[s] : (int64_t)a.ctr->fill[s];
-    const int32_t *list = pp.dense ? a.dense_list : a.slist;
-    const int64_t h = cnt[0];
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < h; base += blockDim.x) {
-        const int64_t i = base + threadIdx.x;
-        int64_t c = 0;
-        if (i < h) {
-            const int64_t pos = a.seg_begin[0] + i;
-            const int64_t v = list ? list[pos] : pos;
-            const int64_t d = a.off[v + 1] - a.off[v];
-            c = (d + pp.chunk - 1) / pp.chunk;
-        }
-        int64_t ex;
-        const int64_t tot = block_excl_scan(c, ex);
-        if (i < h) cstart[i] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) cstart[h] = carry;
-    __syncthreads();
-    for (int64_t i = threadIdx.x; i < h; i += blockDim.x)
-        for (int64_t q = cstart[i]; q < cstart[i + 1]; ++q) owner[q] = (int32_t)i;
-    if (threadIdx.x == 0) {
-        int64_t run = 0, nodes = 0;
-        for (int s = 0; s < kSegs; ++s) { plan->count[s] = cnt[s]; nodes += cnt[s]; }
-        for (int j = 0; j < kSegs - 1; ++j) {
-            plan->item_begin[j] = run;
-            if (j < pp.nlight) run += (cnt[j + 1] + (1LL << j) - 1) >> j;
-        }
-        plan->item_begin[kSegs - 1] = run;
-        plan->heavy_chunks = carry;
-        plan->items = carry + run;
-        plan->nodes = nodes;
-        plan->arcs = pp.dense ? a.m : (int64_t)a.ctr->arcs;
-    }
+    plan_block(a, pp, plan, owner, cstart);
 }
 
 __global__ void heavy_total_kernel(const int64_t *off, int64_t n, int64_t heavy, int64_t chunk,
@@ -310,242 +179,6 @@ __global__ void heavy_total_kernel(const int64_t *off, int64_t n, int64_t heavy,
 }
 
 // ------------------------------------------------------------ the step --
-
-// Gather the counters of arcs e, e+S, ... < eend (S = 2^logS) into acc
-// (this lane's chunks), U arcs in flight per lane; full groups of U arcs
-// run without bounds checks.
-template <int LOG2P>
-__device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
-                                            const uint8_t *__restrict__ cur, int64_t e,
-                                            int64_t eend, int logS, int cl,
-                                            uint4 (&acc)[Cfg<LOG2P>::CPL]) {
-    using C = Cfg<LOG2P>;
-    constexpr int U = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
-    if (e >= eend) return;
-    const int cnt = (int)((eend - e + (1LL << logS) - 1) >> logS);
-    const int32_t *tp = tgt + e;
-    const uint8_t *base = cur + cl * 16;
-    int j = 0;
-    for (; j + U <= cnt; j += U) {
-        int32_t w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) w[u] = ld_stream(tp + ((j + u) << logS));
-        uint4 g[U][C::CPL];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c)
-                g[u][c] = ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16);
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
-    }
-    if (j < cnt) {
-        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-        int32_t w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) w[u] = j + u < cnt ? ld_stream(tp + ((j + u) << logS)) : -1;
-        uint4 g[U][C::CPL];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c)
-                g[u][c] = w[u] >= 0 ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16) : z;
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
-    }
-}
-
-// Per-node tail, called by all 32 lanes.  acc holds the union of the
-// successors' counters (this lane's chunks; every slot of the team holds
-// the same).  Folds in the node's own counter, writes it to the write
-// buffer, sets the changed flag, and for changed nodes evaluates size()
-// and updates the accumulators (Sec. 5), appending the node to the changed
-// list.
-template <int LOG2P, bool F32>
-__device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *__restrict__ cur,
-                                              uint8_t *__restrict__ nxt, int t, int64_t v,
-                                              bool active, uint4 (&acc)[Cfg<LOG2P>::CPL], int cl,
-                                              int tl, int team, int logT, int32_t *clist,
-                                              int32_t *biglist, bool sparse,
-                                              unsigned long long *s_changed, double rdist64,
-                                              float rdist32, const unsigned long long *pow2) {
-    using C = Cfg<LOG2P>;
-    const int lane = threadIdx.x & 31;
-    bool diff = false;
-    if (active) {
-        const uint8_t *own = cur + v * C::P + cl * 16;
-#pragma unroll
-        for (int c = 0; c < C::CPL; ++c) {
-            const uint4 o = ld_counter(own + c * C::L * 16);
-            const uint4 nv = vmax16(acc[c], o);
-            diff |= ne16(nv, o);
-            acc[c] = nv;
-        }
-    }
-    const unsigned bal = __ballot_sync(FULL, diff);
-    const unsigned tmask = logT == 5 ? FULL : (((1u << (1 << logT)) - 1u) << (team << logT));
-    const bool ch = (bal & tmask) != 0u;
-    if (active && tl < C::L) {
-        uint8_t *dst = nxt + v * C::P + cl * 16;
-#pragma unroll
-        for (int c = 0; c < C::CPL; ++c) *reinterpret_cast<uint4 *>(dst + c * C::L * 16) = acc[c];
-    }
-    const bool leader = active && tl == 0;
-    if (leader) a.changed[v] = ch ? 1 : 0;
-    const unsigned lb = __ballot_sync(FULL, leader && ch);
-    if (lb == 0u) return;
-
-    // size() of the new counter: zero count and fixed-point sum, reduced
-    // over the chunk lanes of the team.
-    uint32_t V = 0;
-    unsigned long long S = 0;
-#pragma unroll
-    for (int c = 0; c < C::CPL; ++c) chunk_sums_tab(acc[c], pow2, V, S);
-#pragma unroll
-    for (int o = 1; o < C::L; o <<= 1) {
-        V += __shfl_xor_sync(FULL, V, o);
-        S += __shfl_xor_sync(FULL, S, o);
-    }
-    if (leader && ch) {
-        // Sec. 5: the new layer sits at distance t+1
-        if (F32) {
-            float *ec = static_cast<float *>(a.ecache);
-            const float E = estimate32(V, S, C::P, a.b, a.c32, a.thr_x, a.lc32);
-            const float d = __fsub_rn(E, ec[v]);
-            ec[v] = E;
-            a.sumd[v] = __fma_rn((double)(t + 1), (double)d, a.sumd[v]);   // exact product
-            a.harm[v] = __dadd_rn(a.harm[v], (double)__fmul_rn(d, rdist32));
-        } else {
-            double *ec = static_cast<double *>(a.ecache);
-            const double E = estimate64(V, S, C::P, a.b, a.c64, a.thr_x, a.lc64);
-            const double d = __dsub_rn(E, ec[v]);
-            ec[v] = E;
-            a.sumd[v] = __fma_rn((double)(t + 1), d, a.sumd[v]);
-            a.harm[v] = __fma_rn(d, rdist64, a.harm[v]);
-        }
-    }
-    if (lane == 0) atomicAdd(s_changed, (unsigned long long)__popc(lb));
-    if (!sparse) return;   // dense iterations: the changed list is compacted afterwards
-    // frontier iterations change few nodes: append them right away
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&a.ctr->list_len, (unsigned long long)__popc(lb));
-    base = __shfl_sync(FULL, base, 0);
-    if (leader && ch) clist[base + __popc(lb & lanemask_lt())] = (int32_t)v;
-    if (a.has_reverse) {
-        const int64_t rd = (leader && ch) ? a.roff[v + 1] - a.roff[v] : 0;
-        unsigned long long s = (unsigned long long)rd;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-        if (lane == 0 && s) atomicAdd(&a.ctr->push_arcs, s);
-        const unsigned bb = __ballot_sync(FULL, rd > kBigRdeg);
-        if (bb) {
-            unsigned long long bbase = 0;
-            if (lane == 0) bbase = atomicAdd(&a.ctr->n_big, (unsigned long long)__popc(bb));
-            bbase = __shfl_sync(FULL, bbase, 0);
-            if (rd > kBigRdeg) biglist[bbase + __popc(bb & lanemask_lt())] = (int32_t)v;
-        }
-    }
-}
-
-template <int LOG2P, bool F32>
-__device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__restrict__ cur,
-                                           uint8_t *__restrict__ nxt, int t, int64_t pos0,
-                                           int64_t pos_end, int logS, const int32_t *list,
-                                           int32_t *clist, int32_t *biglist, bool sparse,
-                                           unsigned long long *s_changed, double rdist64,
-                                           float rdist32, const unsigned long long *pow2) {
-    using C = Cfg<LOG2P>;
-    const int lane = threadIdx.x & 31;
-    const int logT = C::LOGL + logS;
-    const int team = lane >> logT;
-    const int tl = lane & ((1 << logT) - 1);
-    const int cl = tl & (C::L - 1);
-    const int slot = tl >> C::LOGL;
-    const int64_t pos = pos0 + team;
-    const bool active = pos < pos_end;
-    int64_t v = 0, e0 = 0, e1 = 0;
-    if (active) {
-        v = list ? (int64_t)list[pos] : pos;
-        e0 = a.off[v];
-        e1 = a.off[v + 1];
-    }
-    uint4 acc[C::CPL];
-#pragma unroll
-    for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
-    for (int o = C::L; o < (1 << logT); o <<= 1)
-#pragma unroll
-        for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
-    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
-                              sparse, s_changed, rdist64, rdist32, pow2);
-}
-
-// One chunk of a heavy node, by a whole warp.  Each chunk leaves its
-// partial union in scratch; the last chunk to arrive combines them and
-// finishes the node.
-template <int LOG2P, bool F32>
-__device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__restrict__ cur,
-                                           uint8_t *__restrict__ nxt, int t, int64_t it,
-                                           const int32_t *owner, const int64_t *cstart,
-                                           const int32_t *list, int32_t *clist, int32_t *biglist,
-                                           bool sparse, unsigned long long *s_changed,
-                                           double rdist64, float rdist32,
-                                           const unsigned long long *pow2) {
-    using C = Cfg<LOG2P>;
-    const int lane = threadIdx.x & 31;
-    const int cl = lane & (C::L - 1);
-    const int slot = lane >> C::LOGL;
-    const int32_t hp = owner[it];
-    const int64_t c0 = cstart[hp];
-    const int64_t nch = cstart[hp + 1] - c0;
-    const int64_t k = it - c0;
-    const int64_t pos = a.seg_begin[0] + hp;
-    const int64_t v = list ? (int64_t)list[pos] : pos;
-    const int64_t a1 = a.off[v + 1];
-    const int64_t e0 = a.off[v] + k * C::CHUNK;
-    const int64_t e1 = e0 + C::CHUNK < a1 ? e0 + C::CHUNK : a1;
-    uint4 acc[C::CPL];
-#pragma unroll
-    for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc);
-#pragma unroll
-    for (int o = C::L; o < 32; o <<= 1)
-#pragma unroll
-        for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
-    if (nch > 1) {
-        if (slot == 0) {
-            uint8_t *dst = a.partial + it * C::P + cl * 16;
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c) __stcg(reinterpret_cast<uint4 *>(dst + c * C::L * 16), acc[c]);
-        }
-        __threadfence();
-        __syncwarp();
-        unsigned last = 0;
-        if (lane == 0) last = atomicAdd(&a.arrive[hp], 1u) == (unsigned)(nch - 1) ? 1u : 0u;
-        last = __shfl_sync(FULL, last, 0);
-        if (!last) return;
-        if (lane == 0) a.arrive[hp] = 0u;
-        __threadfence();
-#pragma unroll
-        for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-        for (int64_t q = slot; q < nch; q += C::SMAX) {
-            const uint8_t *src = a.partial + (c0 + q) * C::P + cl * 16;
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c)
-                acc[c] = vmax16(acc[c], __ldcg(reinterpret_cast<const uint4 *>(src + c * C::L * 16)));
-        }
-#pragma unroll
-        for (int o = C::L; o < 32; o <<= 1)
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
-    }
-    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
-                              s_changed, rdist64, rdist32, pow2);
-}
 
 template <int LOG2P, bool F32>
 __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MIN_BLOCKS)
@@ -573,6 +206,8 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
     __shared__ unsigned long long s_pow2[64];
     const double rdist64 = 1.0 / (double)(t + 1);
     const float rdist32 = 1.0f / (float)(t + 1);
+    // most nodes change in the first iterations: fetch their accumulators early
+    const bool prefetch = !sparse && (t == 0 || 4 * (int64_t)ctr->prev_changed > a.n_pos);
     if (threadIdx.x == 0) s_changed = 0;
     if (threadIdx.x < 64) {
         const int M = threadIdx.x, sh = 64 - a.b;
@@ -594,7 +229,8 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
                 if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
             const int64_t pos0 = seg0 + ((li - ibj) << j);
             light_item<LOG2P, F32>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
-                                   clist, biglist, sparse, &s_changed, rdist64, rdist32, s_pow2);
+                                   clist, biglist, sparse, &s_changed, rdist64, rdist32, s_pow2,
+                                   prefetch);
         }
     }
     __syncthreads();
@@ -602,45 +238,11 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
 }
 
 // After a dense iteration (frontier kept): list the changed nodes, their
-// predecessor count and the ones with many predecessors.  One global atomic
-// per block; the list order does not matter.
+// predecessor count and the ones with many predecessors.
 __global__ void __launch_bounds__(256) compact_changed_kernel(StepArgs a) {
-    const Counters *c = a.ctr;
-    if (c->mode != 0) return;
-    const int t = c->t;
-    int32_t *clist = a.clist[t & 1];
-    int32_t *biglist = a.biglist[t & 1];
-    __shared__ unsigned wcnt[8], wbig[8];
-    __shared__ unsigned long long sbase, bbase, spush;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = base + threadIdx.x;
-        const bool ch = v < a.n && a.changed[v];
-        int64_t rd = 0;
-        if (ch && a.has_reverse) rd = a.roff[v + 1] - a.roff[v];
-        const bool big = rd > kBigRdeg;
-        const unsigned bc = __ballot_sync(FULL, ch), bb = __ballot_sync(FULL, big);
-        unsigned long long ps = (unsigned long long)rd;
-#pragma unroll
-        for (int o = 16; o; o >>= 1) ps += __shfl_xor_sync(FULL, ps, o);
-        if (threadIdx.x == 0) spush = 0;
-        if (lane == 0) { wcnt[wid] = __popc(bc); wbig[wid] = __popc(bb); }
-        __syncthreads();
-        if (lane == 0 && ps) atomicAdd(&spush, ps);
-        if (threadIdx.x == 0) {
-            unsigned tot = 0, totb = 0;
-            for (int w = 0; w < 8; ++w) { tot += wcnt[w]; totb += wbig[w]; }
-            sbase = tot ? atomicAdd(&a.ctr->list_len, (unsigned long long)tot) : 0;
-            bbase = totb ? atomicAdd(&a.ctr->n_big, (unsigned long long)totb) : 0;
-        }
-        __syncthreads();
-        unsigned off = 0, offb = 0;
-        for (int w = 0; w < wid; ++w) { off += wcnt[w]; offb += wbig[w]; }
-        if (ch) clist[sbase + off + __popc(bc & lanemask_lt())] = (int32_t)v;
-        if (big) biglist[bbase + offb + __popc(bb & lanemask_lt())] = (int32_t)v;
-        if (threadIdx.x == 0 && spush) atomicAdd(&a.ctr->push_arcs, spush);
-        __syncthreads();
-    }
+    if (a.ctr->mode != 0) return;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += (int64_t)gridDim.x * blockDim.x)
+        compact_tile(a, a.ctr->t, base);
 }
 
 // --------------------------------------------------------------- outputs --

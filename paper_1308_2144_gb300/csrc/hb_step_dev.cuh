@@ -1,0 +1,481 @@
+// hb_step_dev.cuh -- device-side pieces of one HyperBall iteration shared by
+// the single-graph kernels (hb_step.cu) and the batched kernels (hb_batch.cu):
+// frontier marking, the gather + register-wise max of a node's successors,
+// and the per-node tail (own counter, changed flag, estimator, accumulators).
+#pragma once
+
+#include "hb_internal.cuh"
+#include "hyperball.h"
+
+// Arcs in flight per lane when a lane holds one 16-byte chunk of a counter,
+// and the minimum resident blocks the step kernel is compiled for.
+#ifndef HB_UNROLL
+#define HB_UNROLL 8
+#endif
+#ifndef HB_MIN_BLOCKS
+#define HB_MIN_BLOCKS 6
+#endif
+// L2 eviction hints on counter gathers, and streaming stores for data the
+// next iteration reads only after it has left L2.
+#ifndef HB_CACHE_HINTS
+#define HB_CACHE_HINTS 0
+#endif
+#ifndef HB_STREAM_STORES
+#define HB_STREAM_STORES 1
+#endif
+
+namespace hb {
+namespace dev {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int segment_of(const StepArgs &a, int64_t d) {
+#pragma unroll
+    for (int s = 0; s < kSegs; ++s)
+        if (d >= a.seg_lo[s] && d <= a.seg_hi[s]) return s;
+    return -1;
+}
+
+// Called by all 32 lanes; u < 0 for lanes with nothing to mark.  Sets the
+// must-check bit of u and, if it was clear, appends u to its degree
+// segment of the sparse list.
+__device__ __forceinline__ void mark_append(const StepArgs &a, int32_t u, int lane) {
+    int key = -1;
+    int64_t d = 0;
+    if (u >= 0) {
+        unsigned bit = 1u << (u & 31);
+        unsigned old = atomicOr(&a.mustbits[u >> 5], bit);
+        if (!(old & bit)) {
+            d = a.off[u + 1] - a.off[u];
+            key = segment_of(a, d);
+        }
+    }
+    unsigned peers = __match_any_sync(FULL, key);
+    int leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (key >= 0 && lane == leader)
+        base = atomicAdd(&a.ctr->fill[key], (unsigned long long)__popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    if (key >= 0) a.slist[a.seg_begin[key] + (int64_t)base + __popc(peers & lanemask_lt())] = u;
+    unsigned long long dd = key >= 0 ? (unsigned long long)d : 0ULL;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) dd += __shfl_xor_sync(FULL, dd, o);
+    if (lane == 0 && dd) atomicAdd(&a.ctr->arcs, dd);
+}
+
+// Gather the counters of arcs e, e+S, ... < eend (S = 2^logS) into acc
+// (this lane's chunks), U arcs in flight per lane; full groups of U arcs
+// run without bounds checks.
+template <int LOG2P, int UMAX>
+__device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
+                                            const uint8_t *__restrict__ cur, int64_t e,
+                                            int64_t eend, int logS, int cl,
+                                            uint4 (&acc)[Cfg<LOG2P>::CPL], uint32_t hot) {
+    using C = Cfg<LOG2P>;
+    constexpr int U0 = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
+    constexpr int U = U0 < UMAX ? U0 : UMAX;
+    if (e >= eend) return;
+    const int cnt = (int)((eend - e + (1LL << logS) - 1) >> logS);
+    const int32_t *tp = tgt + e;
+    const uint8_t *base = cur + cl * 16;
+#if HB_CACHE_HINTS
+    const uint64_t pol_last = policy_evict_last(), pol_first = policy_evict_first();
+#define HB_GATHER(addr, w) ld_counter_policy((addr), (uint32_t)(w) < hot ? pol_last : pol_first)
+#else
+#define HB_GATHER(addr, w) ld_counter(addr)
+#endif
+    int j = 0;
+    for (; j + U <= cnt; j += U) {
+        int32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = ld_stream(tp + ((j + u) << logS));
+        uint4 g[U][C::CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c)
+                g[u][c] = HB_GATHER(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, w[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
+    }
+    if (j < cnt) {
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        int32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = j + u < cnt ? ld_stream(tp + ((j + u) << logS)) : -1;
+        uint4 g[U][C::CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c)
+                g[u][c] = w[u] >= 0 ? HB_GATHER(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, w[u]) : z;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
+    }
+#undef HB_GATHER
+}
+
+// Pull the node's accumulators and cached estimate into L2 while its
+// successors are gathered (used when most nodes are expected to change).
+__device__ __forceinline__ void prefetch_accumulators(const StepArgs &a, int64_t v, bool f32) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.sumd + v));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.harm + v));
+    if (f32) asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<float *>(a.ecache) + v));
+    else asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<double *>(a.ecache) + v));
+}
+
+// Per-node tail, called by all 32 lanes.  acc holds the union of the
+// successors' counters (this lane's chunks; every slot of the team holds
+// the same).  Folds in the node's own counter, writes it to the write
+// buffer, sets the changed flag, and for changed nodes evaluates size()
+// and updates the accumulators (Sec. 5), appending the node to the changed
+// list.
+template <int LOG2P, bool F32>
+__device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *__restrict__ cur,
+                                              uint8_t *__restrict__ nxt, int t, int64_t v,
+                                              bool active, uint4 (&acc)[Cfg<LOG2P>::CPL], int cl,
+                                              int tl, int team, int logT, int32_t *clist,
+                                              int32_t *biglist, bool sparse,
+                                              unsigned long long *s_changed, double rdist64,
+                                              float rdist32, const unsigned long long *pow2) {
+    using C = Cfg<LOG2P>;
+    const int lane = threadIdx.x & 31;
+    bool diff = false;
+    if (active) {
+        const uint8_t *own = cur + v * C::P + cl * 16;
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) {
+            const uint4 o = ld_counter(own + c * C::L * 16);
+            const uint4 nv = vmax16(acc[c], o);
+            diff |= ne16(nv, o);
+            acc[c] = nv;
+        }
+    }
+    const unsigned bal = __ballot_sync(FULL, diff);
+    const unsigned tmask = logT == 5 ? FULL : (((1u << (1 << logT)) - 1u) << (team << logT));
+    const bool ch = (bal & tmask) != 0u;
+    if (active && tl < C::L) {
+        uint8_t *dst = nxt + v * C::P + cl * 16;
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) {
+#if HB_STREAM_STORES
+            __stcs(reinterpret_cast<uint4 *>(dst + c * C::L * 16), acc[c]);
+#else
+            *reinterpret_cast<uint4 *>(dst + c * C::L * 16) = acc[c];
+#endif
+        }
+    }
+    const bool leader = active && tl == 0;
+    if (leader) a.changed[v] = ch ? 1 : 0;
+    const unsigned lb = __ballot_sync(FULL, leader && ch);
+    if (lb == 0u) return;
+
+    // size() of the new counter: zero count and fixed-point sum, reduced
+    // over the chunk lanes of the team.
+    uint32_t V = 0;
+    unsigned long long S = 0;
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c) chunk_sums_tab(acc[c], pow2, V, S);
+#pragma unroll
+    for (int o = 1; o < C::L; o <<= 1) {
+        V += __shfl_xor_sync(FULL, V, o);
+        S += __shfl_xor_sync(FULL, S, o);
+    }
+    if (leader && ch) {
+        // Sec. 5: the new layer sits at distance t+1
+        if (F32) {
+            float *ec = static_cast<float *>(a.ecache);
+            const float E = estimate32(V, S, C::P, a.b, a.c32, a.thr_x, a.lc32);
+            const float d = __fsub_rn(E, ec[v]);
+            ec[v] = E;
+            a.sumd[v] = __fma_rn((double)(t + 1), (double)d, a.sumd[v]);   // exact product
+            a.harm[v] = __dadd_rn(a.harm[v], (double)__fmul_rn(d, rdist32));
+        } else {
+            double *ec = static_cast<double *>(a.ecache);
+            const double E = estimate64(V, S, C::P, a.b, a.c64, a.thr_x, a.lc64);
+            const double d = __dsub_rn(E, ec[v]);
+            ec[v] = E;
+            a.sumd[v] = __fma_rn((double)(t + 1), d, a.sumd[v]);
+            a.harm[v] = __fma_rn(d, rdist64, a.harm[v]);
+        }
+    }
+    if (lane == 0) atomicAdd(s_changed, (unsigned long long)__popc(lb));
+    if (!sparse) return;   // dense iterations: the changed list is compacted afterwards
+    // frontier iterations change few nodes: append them right away
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctr->list_len, (unsigned long long)__popc(lb));
+    base = __shfl_sync(FULL, base, 0);
+    if (leader && ch) clist[base + __popc(lb & lanemask_lt())] = (int32_t)v;
+    if (a.has_reverse) {
+        const int64_t rd = (leader && ch) ? a.roff[v + 1] - a.roff[v] : 0;
+        unsigned long long s = (unsigned long long)rd;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0 && s) atomicAdd(&a.ctr->push_arcs, s);
+        const unsigned bb = __ballot_sync(FULL, rd > kBigRdeg);
+        if (bb) {
+            unsigned long long bbase = 0;
+            if (lane == 0) bbase = atomicAdd(&a.ctr->n_big, (unsigned long long)__popc(bb));
+            bbase = __shfl_sync(FULL, bbase, 0);
+            if (rd > kBigRdeg) biglist[bbase + __popc(bb & lanemask_lt())] = (int32_t)v;
+        }
+    }
+}
+
+template <int LOG2P, bool F32>
+__device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__restrict__ cur,
+                                           uint8_t *__restrict__ nxt, int t, int64_t pos0,
+                                           int64_t pos_end, int logS, const int32_t *list,
+                                           int32_t *clist, int32_t *biglist, bool sparse,
+                                           unsigned long long *s_changed, double rdist64,
+                                           float rdist32, const unsigned long long *pow2,
+                                           bool prefetch) {
+    using C = Cfg<LOG2P>;
+    const int lane = threadIdx.x & 31;
+    const int logT = C::LOGL + logS;
+    const int team = lane >> logT;
+    const int tl = lane & ((1 << logT) - 1);
+    const int cl = tl & (C::L - 1);
+    const int slot = tl >> C::LOGL;
+    const int64_t pos = pos0 + team;
+    const bool active = pos < pos_end;
+    int64_t v = 0, e0 = 0, e1 = 0;
+    if (active) {
+        v = list ? (int64_t)list[pos] : pos;
+        e0 = a.off[v];
+        e1 = a.off[v + 1];
+        if (prefetch && tl == 0) prefetch_accumulators(a, v, F32);
+    }
+    uint4 acc[C::CPL];
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
+    if (logS == C::LOGSMAX)
+        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
+    else
+        gather_arcs<LOG2P, kArcsPerSlot>(a.tgt, cur, e0 + slot, e1, logS, cl, acc,
+                                         (uint32_t)a.hot_nodes);
+    for (int o = C::L; o < (1 << logT); o <<= 1)
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
+    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
+                              sparse, s_changed, rdist64, rdist32, pow2);
+}
+
+// One chunk of a heavy node, by a whole warp.  Each chunk leaves its
+// partial union in scratch; the last chunk to arrive combines them and
+// finishes the node.
+template <int LOG2P, bool F32>
+__device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__restrict__ cur,
+                                           uint8_t *__restrict__ nxt, int t, int64_t it,
+                                           const int32_t *owner, const int64_t *cstart,
+                                           const int32_t *list, int32_t *clist, int32_t *biglist,
+                                           bool sparse, unsigned long long *s_changed,
+                                           double rdist64, float rdist32,
+                                           const unsigned long long *pow2) {
+    using C = Cfg<LOG2P>;
+    const int lane = threadIdx.x & 31;
+    const int cl = lane & (C::L - 1);
+    const int slot = lane >> C::LOGL;
+    const int32_t hp = owner[it];
+    const int64_t c0 = cstart[hp];
+    const int64_t nch = cstart[hp + 1] - c0;
+    const int64_t k = it - c0;
+    const int64_t pos = a.seg_begin[0] + hp;
+    const int64_t v = list ? (int64_t)list[pos] : pos;
+    const int64_t a1 = a.off[v + 1];
+    const int64_t e0 = a.off[v] + k * C::CHUNK;
+    const int64_t e1 = e0 + C::CHUNK < a1 ? e0 + C::CHUNK : a1;
+    uint4 acc[C::CPL];
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
+    gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, (uint32_t)a.hot_nodes);
+#pragma unroll
+    for (int o = C::L; o < 32; o <<= 1)
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
+    if (nch > 1) {
+        if (slot == 0) {
+            uint8_t *dst = a.partial + it * C::P + cl * 16;
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c) __stcg(reinterpret_cast<uint4 *>(dst + c * C::L * 16), acc[c]);
+        }
+        __threadfence();
+        __syncwarp();
+        unsigned last = 0;
+        if (lane == 0) last = atomicAdd(&a.arrive[hp], 1u) == (unsigned)(nch - 1) ? 1u : 0u;
+        last = __shfl_sync(FULL, last, 0);
+        if (!last) return;
+        if (lane == 0) a.arrive[hp] = 0u;
+        __threadfence();
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
+        for (int64_t q = slot; q < nch; q += C::SMAX) {
+            const uint8_t *src = a.partial + (c0 + q) * C::P + cl * 16;
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c)
+                acc[c] = vmax16(acc[c], __ldcg(reinterpret_cast<const uint4 *>(src + c * C::L * 16)));
+        }
+#pragma unroll
+        for (int o = C::L; o < 32; o <<= 1)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
+    }
+    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
+                              s_changed, rdist64, rdist32, pow2);
+}
+
+// Start of an iteration for one graph: shift this iteration's counters
+// into the "previous" slots and choose dense or sparse (frontier) mode.
+__device__ __forceinline__ void begin_one(const StepArgs &a) {
+    Counters *c = a.ctr;
+    const int t = c->steps_done;
+    c->t = t;
+    c->prev_changed = c->n_changed;
+    c->prev_list_len = c->list_len;
+    c->prev_push_arcs = c->push_arcs;
+    c->prev_big = c->n_big;
+    c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
+    for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
+    int sparse = 0;
+    if (t > 0) {
+        if (a.frontier == HB_FRONTIER_PULL) sparse = 1;
+        else if (a.frontier == HB_FRONTIER_PUSH) sparse = a.has_reverse;
+        else if (a.frontier == HB_FRONTIER_AUTO)
+            sparse = a.has_reverse && (double)c->prev_push_arcs <= a.sparse_frac * (double)a.m;
+    }
+    c->mode = sparse;
+}
+
+// End of an iteration: count it and record convergence (Sec. 4.2: stop
+// after the first iteration that changes no counter).
+__device__ __forceinline__ void end_one(const StepArgs &a) {
+    Counters *c = a.ctr;
+    c->steps_done = c->t + 1;
+    if (c->n_changed == 0) c->converged = 1;
+}
+
+// Push marking by one warp: the predecessors of changed node w.
+__device__ __forceinline__ void push_warp(const StepArgs &a, int32_t w, int lane) {
+    const int64_t r0 = a.roff[w], r1 = a.roff[w + 1];
+    for (int64_t j0 = r0; j0 < r1; j0 += 32) {
+        const int64_t j = j0 + lane;
+        mark_append(a, j < r1 ? a.rtgt[j] : -1, lane);
+    }
+}
+
+// Copy-forward element k (node index k / CH of the previous changed list,
+// chunk k % CH): clears the node's changed flag and, unless the node is
+// recomputed in this iteration, copies that chunk of its counter into the
+// write buffer.
+__device__ __forceinline__ void copy_forward_one(const StepArgs &a, int t, int64_t k) {
+    const int32_t *prev = a.clist[(t + 1) & 1];
+    const uint8_t *cur = a.regs[t & 1];
+    uint8_t *nxt = a.regs[(t + 1) & 1];
+    const int logCH = a.b - 4;
+    const int64_t i = k >> logCH;
+    const int ch = (int)(k & ((1 << logCH) - 1));
+    const int32_t w = prev[i];
+    if (ch == 0) a.changed[w] = 0;
+    if (!((a.mustbits[w >> 5] >> (w & 31)) & 1u)) {
+        const int64_t o = ((int64_t)w << logCH) + ch;
+        reinterpret_cast<uint4 *>(nxt)[o] = reinterpret_cast<const uint4 *>(cur)[o];
+    }
+}
+
+struct PlanParams {
+    int64_t count[kSegs];   // dense: segment sizes
+    int64_t chunk;
+    int32_t nlight;
+    int32_t dense;
+};
+
+// Work plan of one graph, by one whole block.  Items: first the chunks of
+// heavy nodes (chunk starts by a block scan, then the chunk -> node map),
+// then each light class packs 2^j nodes per warp item.
+__device__ __forceinline__ void plan_block(const StepArgs &a, const PlanParams &pp, Plan *plan,
+                                           int32_t *owner, int64_t *cstart) {
+    if (!pp.dense && a.ctr->mode != 1) return;
+    __shared__ int64_t carry;
+    int64_t cnt[kSegs];
+    for (int s = 0; s < kSegs; ++s) cnt[s] = pp.dense ? pp.count[s] : (int64_t)a.ctr->fill[s];
+    const int32_t *list = pp.dense ? a.dense_list : a.slist;
+    const int64_t h = cnt[0];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < h; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int64_t c = 0;
+        if (i < h) {
+            const int64_t pos = a.seg_begin[0] + i;
+            const int64_t v = list ? list[pos] : pos;
+            const int64_t d = a.off[v + 1] - a.off[v];
+            c = (d + pp.chunk - 1) / pp.chunk;
+        }
+        int64_t ex;
+        const int64_t tot = block_excl_scan(c, ex);
+        if (i < h) cstart[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cstart[h] = carry;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < h; i += blockDim.x)
+        for (int64_t q = cstart[i]; q < cstart[i + 1]; ++q) owner[q] = (int32_t)i;
+    if (threadIdx.x == 0) {
+        int64_t run = 0, nodes = 0;
+        for (int s = 0; s < kSegs; ++s) { plan->count[s] = cnt[s]; nodes += cnt[s]; }
+        for (int j = 0; j < kSegs - 1; ++j) {
+            plan->item_begin[j] = run;
+            if (j < pp.nlight) run += (cnt[j + 1] + (1LL << j) - 1) >> j;
+        }
+        plan->item_begin[kSegs - 1] = run;
+        plan->heavy_chunks = carry;
+        plan->items = carry + run;
+        plan->nodes = nodes;
+        plan->arcs = pp.dense ? a.m : (int64_t)a.ctr->arcs;
+    }
+}
+
+// Changed-list compaction of the 256 nodes from `base`, by one block of 256
+// threads: one global atomic per block; the list order does not matter.
+__device__ __forceinline__ void compact_tile(const StepArgs &a, int t, int64_t base) {
+    int32_t *clist = a.clist[t & 1];
+    int32_t *biglist = a.biglist[t & 1];
+    __shared__ unsigned wcnt[8], wbig[8];
+    __shared__ unsigned long long sbase, bbase, spush;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t v = base + threadIdx.x;
+    const bool ch = v < a.n && a.changed[v];
+    int64_t rd = 0;
+    if (ch && a.has_reverse) rd = a.roff[v + 1] - a.roff[v];
+    const bool big = rd > kBigRdeg;
+    const unsigned bc = __ballot_sync(FULL, ch), bb = __ballot_sync(FULL, big);
+    unsigned long long ps = (unsigned long long)rd;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ps += __shfl_xor_sync(FULL, ps, o);
+    if (threadIdx.x == 0) spush = 0;
+    if (lane == 0) { wcnt[wid] = __popc(bc); wbig[wid] = __popc(bb); }
+    __syncthreads();
+    if (lane == 0 && ps) atomicAdd(&spush, ps);
+    if (threadIdx.x == 0) {
+        unsigned tot = 0, totb = 0;
+        for (int w = 0; w < 8; ++w) { tot += wcnt[w]; totb += wbig[w]; }
+        sbase = tot ? atomicAdd(&a.ctr->list_len, (unsigned long long)tot) : 0;
+        bbase = totb ? atomicAdd(&a.ctr->n_big, (unsigned long long)totb) : 0;
+    }
+    __syncthreads();
+    unsigned off = 0, offb = 0;
+    for (int w = 0; w < wid; ++w) { off += wcnt[w]; offb += wbig[w]; }
+    if (ch) clist[sbase + off + __popc(bc & lanemask_lt())] = (int32_t)v;
+    if (big) biglist[bbase + offb + __popc(bb & lanemask_lt())] = (int32_t)v;
+    if (threadIdx.x == 0 && spush) atomicAdd(&a.ctr->push_arcs, spush);
+    __syncthreads();
+}
+
+}  // namespace dev
+}  // namespace hb

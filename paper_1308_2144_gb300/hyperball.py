@@ -41,7 +41,10 @@ FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
            "hb_get_info", "hb_reset", "hb_save", "hb_load", "hb_destroy", "hb_last_error",
-           "hb_version", "hb_step_noalloc"]
+           "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
+           "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
+           "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
+           "hb_batch_destroy"]
 
 
 class HBError(RuntimeError):
@@ -70,6 +73,11 @@ class Info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("offsets", ctypes.c_void_p), ("targets", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("log2m", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 _lib = None
@@ -121,6 +129,28 @@ def load():
         L.hb_last_error.argtypes = []
         L.hb_version.restype = ctypes.c_char_p
         L.hb_version.argtypes = []
+        L.hb_batch_create.restype = st
+        L.hb_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(GraphDesc), ctypes.POINTER(Options),
+                                      ctypes.POINTER(_vp)]
+        L.hb_batch_step.restype = st
+        L.hb_batch_step.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+        L.hb_batch_run.restype = st
+        L.hb_batch_run.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+        L.hb_batch_reset.restype = st
+        L.hb_batch_reset.argtypes = [_vp, _vp]
+        L.hb_batch_get_centralities.restype = st
+        L.hb_batch_get_centralities.argtypes = [_vp, ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.hb_batch_get_registers.restype = st
+        L.hb_batch_get_registers.argtypes = [_vp, ctypes.c_int, _vp]
+        L.hb_batch_get_accumulators.restype = st
+        L.hb_batch_get_accumulators.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+        L.hb_batch_get_info.restype = st
+        L.hb_batch_get_info.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(Info)]
+        L.hb_batch_get_totals.restype = st
+        L.hb_batch_get_totals.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int64)]
+        L.hb_batch_destroy.restype = None
+        L.hb_batch_destroy.argtypes = [_vp]
         L.hb_step_noalloc.restype = st
         L.hb_step_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                       ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
@@ -254,6 +284,84 @@ def hb_step_noalloc(offsets, targets, n: int, m: int, log2m: int, t: int, cur, n
                                   _ptr(cur), _ptr(nxt), _ptr(sumd), _ptr(harm), _ptr(changed),
                                   ctypes.byref(k), _stream_ptr(stream)))
     return int(k.value)
+
+
+class HyperBallBatch:
+    """Many graphs advanced together (the batched form).  ``graphs`` is a
+    list of (offsets, targets, n, log2m, seed) with tensors kept alive by
+    this object."""
+
+    def __init__(self, graphs, **opts):
+        self._keep = []
+        descs = (GraphDesc * len(graphs))()
+        self.sizes = []
+        for i, (off, tgt, n, log2m, seed) in enumerate(graphs):
+            self._keep += [off, tgt]
+            descs[i] = GraphDesc(_ptr(off).value, _ptr(tgt).value if tgt.numel() else None, int(n),
+                                 int(tgt.shape[0]), int(log2m), int(seed) & (2**64 - 1))
+            self.sizes.append((int(n), 1 << int(log2m)))
+        self.k = len(graphs)
+        self.options = make_options(**opts)
+        self._h = _vp()
+        _check(load().hb_batch_create(self.k, descs, ctypes.byref(self.options), ctypes.byref(self._h)))
+
+    def step(self) -> int:
+        a = ctypes.c_int32()
+        _check(load().hb_batch_step(self._h, ctypes.byref(a)))
+        return int(a.value)
+
+    def run(self) -> int:
+        it = ctypes.c_int32()
+        _check(load().hb_batch_run(self._h, ctypes.byref(it)))
+        return int(it.value)
+
+    def reset(self, seeds=None):
+        arr = None
+        if seeds is not None:
+            arr = (ctypes.c_uint64 * self.k)(*[int(x) & (2**64 - 1) for x in seeds])
+        _check(load().hb_batch_reset(self._h, arr))
+
+    def totals(self):
+        it, act, arcs = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(load().hb_batch_get_totals(self._h, ctypes.byref(it), ctypes.byref(act), ctypes.byref(arcs)))
+        return int(it.value), int(act.value), int(arcs.value)
+
+    def info(self, i) -> dict:
+        info = Info()
+        _check(load().hb_batch_get_info(self._h, i, ctypes.byref(info)))
+        return info.as_dict()
+
+    def registers(self, i, device="cuda"):
+        n, p = self.sizes[i]
+        out = torch.empty((n, p), dtype=torch.uint8, device=device)
+        _check(load().hb_batch_get_registers(self._h, i, _ptr(out)))
+        return out
+
+    def accumulators(self, i, device="cuda"):
+        n, _ = self.sizes[i]
+        s = torch.empty(n, dtype=torch.float64, device=device)
+        h = torch.empty(n, dtype=torch.float64, device=device)
+        _check(load().hb_batch_get_accumulators(self._h, i, _ptr(s), _ptr(h)))
+        return s, h
+
+    def centralities(self, i, device="cuda") -> dict:
+        n, _ = self.sizes[i]
+        out = {k: torch.empty(n, dtype=torch.float64, device=device)
+               for k in ("closeness", "harmonic", "lin", "reachable")}
+        _check(load().hb_batch_get_centralities(self._h, i, _ptr(out["closeness"]), _ptr(out["harmonic"]),
+                                                _ptr(out["lin"]), _ptr(out["reachable"])))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------- convenience --
