@@ -232,6 +232,60 @@ hb_status hb_batch_get_totals(hb_batch *b, int32_t *iterations, int32_t *n_activ
 
 void hb_batch_destroy(hb_batch *b);
 
+/* ---- Serving form ------------------------------------------------------
+ * A request loop for centrality jobs (graph from a device-resident pool,
+ * log2m, seed) with continuous batching: a server thread keeps up to
+ * `slots` requests on the device at once, their counters resident between
+ * iterations, and advances all of them in the same batched launches.
+ * Between iterations it admits queued requests (FIFO) into free slots
+ * while the device has run_bytes + reserve_bytes free, and finalises
+ * requests whose counters stopped changing: results are copied to host
+ * memory and the request's device memory is freed.  A request's result is
+ * the same as the same (graph, log2m, seed) run alone. */
+#define HB_REQ_QUEUED  0
+#define HB_REQ_RUNNING 1
+#define HB_REQ_DONE    2
+#define HB_REQ_FAILED  3
+
+typedef struct {
+    int32_t slots;            /* requests on the device at once, 1..4096 (1 = FIFO one at a time) */
+    uint32_t flags;           /* HB_FP32_ESTIMATE or 0 */
+    int32_t max_steps;        /* per-request iteration cap */
+    int64_t reserve_bytes;    /* device memory left free when admitting */
+} hb_server_options;
+
+typedef struct {
+    int32_t state;            /* HB_REQ_* */
+    int32_t steps;            /* iterations to the fixpoint */
+    int64_t arcs;             /* arc-updates of the request */
+    double submit_s, admit_s, done_s;   /* server clock (seconds since creation) */
+} hb_request_info;
+
+typedef struct hb_server hb_server;
+
+void hb_server_default_options(hb_server_options *opt);   /* 32 slots, 4 GiB reserve */
+hb_status hb_server_create(const hb_server_options *opt, hb_server **out);
+/* Add a graph to the pool (CSR copied to the device once) and prepare it
+ * for each log2m listed (relabelling, reverse CSR, plans shared by all its
+ * requests).  *graph_id receives its id. */
+hb_status hb_server_add_graph(hb_server *s, const int64_t *offsets, const int32_t *targets, int64_t n,
+                              int64_t m, const int32_t *log2ms, int n_log2m, int32_t *graph_id);
+/* Queue a request; returns at once with its id. */
+hb_status hb_server_submit(hb_server *s, int32_t graph_id, int32_t log2m, uint64_t seed,
+                           int64_t *request_id);
+/* Wait until the request is done (timeout_s < 0: no limit; HB_ERR_TIMEOUT
+ * if it ran out).  info may be NULL. */
+hb_status hb_server_wait(hb_server *s, int64_t request_id, double timeout_s, hb_request_info *info);
+/* Copy a finished request's centralities (n doubles each, host memory, any
+ * may be NULL) and forget the request. */
+hb_status hb_server_take(hb_server *s, int64_t request_id, double *closeness, double *harmonic,
+                         double *lin, double *reachable);
+/* Completed requests, batched iterations, arc-updates, seconds with work on
+ * the device, and the server clock. */
+hb_status hb_server_stats(hb_server *s, int64_t *completed, int64_t *iterations, int64_t *arcs,
+                          double *busy_s, double *clock_s);
+void hb_server_destroy(hb_server *s);
+
 /* ---- One iteration without device allocation -------------------------
  * The paper has no counterpart to this call.  It exists for callers that
  * cannot call cudaMalloc: code running inside another framework's memory

@@ -75,9 +75,12 @@ cudaError_t to_caller(void *dst, const void *src, size_t bytes, cudaStream_t s) 
                                                                : cudaMemcpyDeviceToHost, s);
 }
 
-// Everything after the scanned CSR (g->off, g->tgt, owned) is in place:
-// segments, reverse CSR, state buffers, plans.  Does not initialise.
-hb_status finish_setup(hb_graph *g) {
+// Shared set-up of a graph for one log2m, once the scanned CSR (g->off,
+// g->tgt) is in place: degree segments, heavy chunks, reverse CSR,
+// estimator tables, the dense plan and the launch shape.  Everything here
+// is read-only during iterations, so several runs (different seeds) can
+// share it.
+hb_status setup_shared(hb_graph *g) {
     cudaStream_t s = g->s;
     const int64_t n = g->n, m = g->m;
     const int P = 1 << g->b;
@@ -106,39 +109,16 @@ hb_status finish_setup(hb_graph *g) {
     a.roff = g->roff;
     a.rtgt = g->rtgt;
     a.has_reverse = want_reverse ? 1 : 0;
-    a.regs[0] = M.alloc<uint8_t>((size_t)n * P);
-    a.regs[1] = M.alloc<uint8_t>((size_t)n * P);
-    a.sumd = M.alloc<double>(n);
-    a.harm = M.alloc<double>(n);
-    a.ecache = g->fp32 ? (void *)M.alloc<float>(n) : (void *)M.alloc<double>(n);
-    a.changed = M.alloc<uint8_t>(n);
-    a.mustbits = M.alloc<uint32_t>((n + 31) / 32 + 1);
-    a.clist[0] = M.alloc<int32_t>(n);
-    a.clist[1] = M.alloc<int32_t>(n);
-    const int64_t big_cap = (m / kBigRdeg + 1) < n ? (m / kBigRdeg + 1) : (n > 0 ? n : 1);
-    a.biglist[0] = M.alloc<int32_t>(big_cap);
-    a.biglist[1] = M.alloc<int32_t>(big_cap);
-    a.slist = M.alloc<int32_t>(g->n_pos);
-    Plan *plans = M.alloc<Plan>(2);
-    a.plan_dense = plans;
-    a.plan_sparse = plans + 1;
+    a.plan_dense = M.alloc<Plan>(1);
     a.owner_dense = M.alloc<int32_t>(g->heavy_total);
-    a.owner_sparse = M.alloc<int32_t>(g->heavy_total);
     a.cstart_dense = M.alloc<int64_t>(g->seg_count[0] + 1);
-    a.cstart_sparse = M.alloc<int64_t>(g->seg_count[0] + 1);
-    a.partial = M.alloc<uint8_t>((size_t)g->heavy_total * P);
-    a.arrive = M.alloc<uint32_t>(g->seg_count[0] + 1);
-    g->ctr = M.alloc<Counters>(1);
-    a.ctr = g->ctr;
     double *lc64 = M.alloc<double>(P + 1);
     float *lc32 = M.alloc<float>(P + 1);
     a.lc64 = lc64;
     a.lc32 = lc32;
     int32_t *dense_list = nullptr;
     if (!g->relabel) dense_list = M.alloc<int32_t>(g->n_pos);
-    if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (HyperBall state)");
-    if (cudaMallocHost(&g->ctr_host, sizeof(Counters)) != cudaSuccess)
-        return fail(HB_ERR_OOM, "out of pinned host memory");
+    if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (HyperBall tables)");
 
     const double alpha = hll_alpha(P);
     a.c64 = std::ldexp(alpha * (double)P * (double)P, 64 - g->b);
@@ -157,8 +137,6 @@ hb_status finish_setup(hb_graph *g) {
     a.b = g->b;
     a.frontier = g->opt.frontier;
     a.sparse_frac = 0.25;
-    cudaMemsetAsync(a.arrive, 0, sizeof(uint32_t) * (g->seg_count[0] + 1), s);
-    cudaMemsetAsync(a.changed, 0, (size_t)(n > 0 ? n : 1), s);
     if (dense_list) {
         int64_t *sb_dev = M.alloc<int64_t>(kSegs);
         unsigned long long *fill = M.alloc<unsigned long long>(kSegs);
@@ -181,11 +159,124 @@ hb_status finish_setup(hb_graph *g) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     g->step_grid = sms * step_blocks_per_sm(g->b, g->fp32);
-    // the most gathered counters (lowest ids after the degree sort) that fit
-    // in half of L2 are gathered with an evict-last hint
+    // counters of the most gathered nodes (lowest ids after the degree sort)
+    // that fit in half of L2, for the optional eviction hints
     const int64_t hot = g->relabel ? ((int64_t)l2 / 2) / P : 0;
     a.hot_nodes = (int32_t)(hot < n ? hot : n);
     return HB_OK;
+}
+
+hb_status init_state(hb_graph *g, uint64_t seed);
+
+}  // namespace
+
+namespace hb {
+
+// Bytes of the per-run state of a graph (counters, accumulators, flags,
+// lists, frontier plan, heavy-chunk scratch), carved from one allocation.
+size_t run_bytes(const hb_graph *g) {
+    const int64_t n = g->n, m = g->m, P = (int64_t)1 << g->b;
+    const int64_t big_cap = (m / kBigRdeg + 1) < n ? (m / kBigRdeg + 1) : (n > 0 ? n : 1);
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t b = 0;
+    b += 2 * up((size_t)n * P);
+    b += 2 * up(sizeof(double) * n);
+    b += up((g->fp32 ? sizeof(float) : sizeof(double)) * n);
+    b += up((size_t)n);
+    b += up(sizeof(uint32_t) * ((n + 31) / 32 + 1));
+    b += 2 * up(sizeof(int32_t) * n) + 2 * up(sizeof(int32_t) * big_cap);
+    b += up(sizeof(int32_t) * g->n_pos);
+    b += up(sizeof(Plan)) + up(sizeof(int32_t) * g->heavy_total) + up(sizeof(int64_t) * (g->seg_count[0] + 1));
+    b += up((size_t)g->heavy_total * P) + up(sizeof(uint32_t) * (g->seg_count[0] + 1));
+    b += up(sizeof(Counters));
+    return b;
+}
+
+// Per-run state of a graph whose shared set-up (g->a's shared fields) is
+// done: one device allocation, carved.
+hb_status setup_run(hb_graph *g) {
+    const int64_t n = g->n, m = g->m, P = (int64_t)1 << g->b;
+    const int64_t big_cap = (m / kBigRdeg + 1) < n ? (m / kBigRdeg + 1) : (n > 0 ? n : 1);
+    const size_t total = run_bytes(g);
+    uint8_t *base = g->mem.alloc<uint8_t>(total);
+    if (!base) return fail(HB_ERR_OOM, "out of device memory (HyperBall state: " + std::to_string(total) + " bytes)");
+    size_t off = 0;
+    auto take = [&](size_t bytes) { uint8_t *p = base + off; off += (bytes + 255) & ~(size_t)255; return p; };
+    StepArgs &a = g->a;
+    a.regs[0] = take((size_t)n * P);
+    a.regs[1] = take((size_t)n * P);
+    a.sumd = reinterpret_cast<double *>(take(sizeof(double) * n));
+    a.harm = reinterpret_cast<double *>(take(sizeof(double) * n));
+    a.ecache = take((g->fp32 ? sizeof(float) : sizeof(double)) * n);
+    a.changed = take((size_t)n);
+    a.mustbits = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * ((n + 31) / 32 + 1)));
+    a.clist[0] = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * n));
+    a.clist[1] = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * n));
+    a.biglist[0] = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * big_cap));
+    a.biglist[1] = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * big_cap));
+    a.slist = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * g->n_pos));
+    a.plan_sparse = reinterpret_cast<Plan *>(take(sizeof(Plan)));
+    a.owner_sparse = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * g->heavy_total));
+    a.cstart_sparse = reinterpret_cast<int64_t *>(take(sizeof(int64_t) * (g->seg_count[0] + 1)));
+    a.partial = take((size_t)g->heavy_total * P);
+    a.arrive = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * (g->seg_count[0] + 1)));
+    g->ctr = reinterpret_cast<Counters *>(take(sizeof(Counters)));
+    a.ctr = g->ctr;
+    if (!g->ctr_host && cudaMallocHost(&g->ctr_host, sizeof(Counters)) != cudaSuccess)
+        return fail(HB_ERR_OOM, "out of pinned host memory");
+    cudaError_t e = cudaMemsetAsync(a.arrive, 0, sizeof(uint32_t) * (g->seg_count[0] + 1), g->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.changed, 0, (size_t)(n > 0 ? n : 1), g->s);
+    if (e != cudaSuccess) return cuda_fail(e, "run state");
+    return HB_OK;
+}
+
+void drop_run_state(hb_graph *g) {
+    if (g->a.regs[0]) g->mem.release(g->a.regs[0]);   // the carved per-run block starts there
+    StepArgs &a = g->a;
+    a.regs[0] = a.regs[1] = nullptr;
+    a.sumd = a.harm = nullptr;
+    a.ecache = nullptr;
+    a.changed = nullptr;
+    a.mustbits = nullptr;
+    a.clist[0] = a.clist[1] = a.biglist[0] = a.biglist[1] = a.slist = nullptr;
+    a.plan_sparse = nullptr;
+    a.owner_sparse = nullptr;
+    a.cstart_sparse = nullptr;
+    a.partial = nullptr;
+    a.arrive = nullptr;
+    a.ctr = g->ctr = nullptr;
+}
+
+// A new run on the shared set-up of `tmpl` (same graph and log2m): the
+// instance borrows the template's read-only arrays, owns only its per-run
+// state, and starts from the counters of `seed`.
+hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_graph **out) {
+    hb_graph *g = new hb_graph();
+    g->n = tmpl->n; g->m = tmpl->m; g->b = tmpl->b; g->y = tmpl->y;
+    g->opt = tmpl->opt;
+    g->s = s;
+    g->fp32 = tmpl->fp32; g->relabel = tmpl->relabel;
+    g->step_grid = tmpl->step_grid;
+    g->off = tmpl->off; g->tgt = tmpl->tgt; g->roff = tmpl->roff; g->rtgt = tmpl->rtgt;
+    g->perm = tmpl->perm; g->inv = tmpl->inv;
+    for (int k = 0; k < kSegs; ++k) g->seg_count[k] = tmpl->seg_count[k];
+    g->n_pos = tmpl->n_pos;
+    g->heavy_total = tmpl->heavy_total;
+    g->a = tmpl->a;
+    hb_status st = setup_run(g);
+    if (st == HB_OK) st = init_state(g, seed);
+    if (st != HB_OK) { delete g; return st; }
+    *out = g;
+    return HB_OK;
+}
+
+}  // namespace hb
+
+namespace {
+
+hb_status finish_setup(hb_graph *g) {
+    hb_status st = setup_shared(g);
+    return st == HB_OK ? setup_run(g) : st;
 }
 
 hb_status init_state(hb_graph *g, uint64_t seed) {

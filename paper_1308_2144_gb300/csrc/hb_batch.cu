@@ -8,6 +8,7 @@
 // launch whose conditional while node repeats the iteration on the device
 // until no graph is active or the iteration cap is reached.
 #include <algorithm>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -40,6 +41,7 @@ struct BatchArrays {
     int64_t *word_prefix;          // [k+1] must-check bitmap words to clear
     const int64_t *tile_prefix;    // [k+1] 256-node tiles (static)
     int64_t *graph_arcs;           // [k] arcs scanned per graph since init
+    int32_t *done;                 // [k] 1 once the graph has converged
     BatchCtl *ctl;
     int k;
     int use_cond;
@@ -288,6 +290,7 @@ __global__ void batch_end_kernel(BatchArrays B) {
             atomicAdd(&arcs, (unsigned long long)scanned);
         }
         if (!c->converged) atomicAdd(&active, 1);
+        B.done[g] = c->converged ? 1 : 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -427,6 +430,51 @@ hb_status read_ctl(hb_batch *b) {
     return HB_OK;
 }
 
+// Device arrays, launch shape and captured graphs of a batch of k slots.
+hb_status batch_setup(hb_batch *b, const std::vector<StepArgs> &hargs, const std::vector<int64_t> &tiles) {
+    const int k = b->k;
+    DevMem &M = b->mem;
+    StepArgs *args = M.alloc<StepArgs>(k);
+    int64_t *pref = M.alloc<int64_t>((size_t)6 * (k + 1));
+    int64_t *garcs = M.alloc<int64_t>(k);
+    int32_t *done = M.alloc<int32_t>(k);
+    BatchCtl *ctl = M.alloc<BatchCtl>(1);
+    if (M.err != cudaSuccess || (!b->ctl_host && cudaMallocHost(&b->ctl_host, sizeof(BatchCtl)) != cudaSuccess))
+        return bfail(HB_ERR_OOM, "out of memory (batch arrays)");
+    cudaError_t e = cudaMemcpyAsync(args, hargs.data(), sizeof(StepArgs) * k, cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(pref + 5 * (k + 1), tiles.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(done, 0, sizeof(int32_t) * k, b->s);
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, "batch upload");
+    BatchArrays &B = b->B;
+    B.args = args;
+    B.item_prefix = pref;
+    B.list_prefix = pref + (k + 1);
+    B.big_prefix = pref + 2 * (k + 1);
+    B.copy_prefix = pref + 3 * (k + 1);
+    B.word_prefix = pref + 4 * (k + 1);
+    B.tile_prefix = pref + 5 * (k + 1);
+    B.graph_arcs = garcs;
+    B.done = done;
+    B.ctl = ctl;
+    B.k = k;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = sizeof(int64_t) * (size_t)(k + 1);
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(batch_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(batch_step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (b->fp32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<true>, kStepThreads, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<false>, kStepThreads, smem);
+    b->step_grid = sms * (per > 0 ? per : 1);
+    b->aux_grid = sms * 8;
+    hb_status st = reset_ctl(b);
+    if (st == HB_OK) st = build_graphs(b);
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -467,50 +515,13 @@ hb_status hb_batch_create(int k, const hb_graph_desc *gs, const hb_options *opt,
         }
         b->graphs.push_back(g);
     }
-    DevMem &M = b->mem;
-    StepArgs *args = M.alloc<StepArgs>(k);
-    int64_t *pref = M.alloc<int64_t>((size_t)6 * (k + 1));
-    int64_t *garcs = M.alloc<int64_t>(k);
-    BatchCtl *ctl = M.alloc<BatchCtl>(1);
-    if (M.err != cudaSuccess || cudaMallocHost(&b->ctl_host, sizeof(BatchCtl)) != cudaSuccess) {
-        delete b;
-        return bfail(HB_ERR_OOM, "out of memory (batch arrays)");
-    }
     std::vector<StepArgs> hargs(k);
     std::vector<int64_t> tiles(k + 1, 0);
     for (int i = 0; i < k; ++i) {
         hargs[i] = b->graphs[i]->a;
         tiles[i + 1] = tiles[i] + (b->graphs[i]->n + 255) / 256;
     }
-    cudaError_t e = cudaMemcpyAsync(args, hargs.data(), sizeof(StepArgs) * k, cudaMemcpyHostToDevice, b->s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(pref + 5 * (k + 1), tiles.data(), sizeof(int64_t) * (k + 1), cudaMemcpyHostToDevice, b->s);
-    if (e != cudaSuccess) { delete b; return bfail(HB_ERR_CUDA, "batch upload"); }
-    BatchArrays &B = b->B;
-    B.args = args;
-    B.item_prefix = pref;
-    B.list_prefix = pref + (k + 1);
-    B.big_prefix = pref + 2 * (k + 1);
-    B.copy_prefix = pref + 3 * (k + 1);
-    B.word_prefix = pref + 4 * (k + 1);
-    B.tile_prefix = pref + 5 * (k + 1);
-    B.graph_arcs = garcs;
-    B.ctl = ctl;
-    B.k = k;
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = sizeof(int64_t) * (size_t)(k + 1);
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(batch_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(batch_step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    }
-    if (b->fp32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<true>, kStepThreads, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<false>, kStepThreads, smem);
-    b->step_grid = sms * (per > 0 ? per : 1);
-    b->aux_grid = sms * 8;
-    hb_status st = reset_ctl(b);
-    if (st == HB_OK) st = build_graphs(b);
+    hb_status st = batch_setup(b, hargs, tiles);
     if (st != HB_OK) { delete b; return st; }
     *out = b;
     return HB_OK;
@@ -602,5 +613,389 @@ void hb_batch_destroy(hb_batch *b) {
     if (b->s) cudaStreamSynchronize(b->s);
     delete b;
 }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ serving --
+// A request loop over the batched kernels: a fixed number of slots, each
+// holding one running request (graph from the server's pool, log2m, seed)
+// with its counters resident on the device.  Between iterations, queued
+// requests are admitted into free slots while device memory allows, and
+// requests whose counters stopped changing are finalised, copied to the
+// host and their memory freed; all running requests advance in the same
+// launches (continuous batching).
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+namespace {
+
+struct ServeReq {
+    int graph = 0, log2m = 4;
+    uint64_t seed = 0;
+    int state = HB_REQ_QUEUED;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    hb_graph *inst = nullptr;
+    int slot = -1;
+    int32_t steps = 0;
+    int64_t arcs = 0;
+    hb_status err = HB_OK;
+    std::vector<double> out[4];
+};
+
+struct PoolGraph {
+    int64_t *off = nullptr;
+    int32_t *tgt = nullptr;
+    int64_t n = 0, m = 0;
+    std::map<int, hb_graph *> tmpl;   // per log2m: relabelled CSR, reverse CSR, plans
+};
+
+}  // namespace
+
+struct hb_server {
+    hb_server_options opt{};
+    hb_batch *batch = nullptr;
+    DevMem mem;
+    Counters *null_ctr = nullptr;
+    std::vector<StepArgs> slot_args;
+    std::vector<int64_t> slot_req;
+    std::vector<int64_t> tiles;
+    std::vector<PoolGraph> pool;
+    std::map<int64_t, ServeReq> reqs;
+    std::deque<int64_t> queue;
+    int64_t next_id = 1;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::thread th;
+    bool stop = false;
+    std::chrono::steady_clock::time_point t0;
+    int64_t iterations = 0, total_arcs = 0, completed = 0;
+    double busy_s = 0;
+    std::string fatal;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    ~hb_server() {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        if (th.joinable()) th.join();
+        for (auto &kv : reqs)
+            if (kv.second.inst) hb_destroy(kv.second.inst);
+        for (auto &pg : pool)
+            for (auto &kv : pg.tmpl) hb_destroy(kv.second);
+        delete batch;
+        mem.free_all();
+    }
+};
+
+namespace {
+
+StepArgs null_slot(hb_server *S, int slot) {
+    StepArgs a{};
+    a.ctr = S->null_ctr + slot;
+    a.b = 4;
+    a.frontier = HB_FRONTIER_OFF;
+    return a;
+}
+
+// Put the slot's arguments (and the node tiles of every slot) on the device.
+cudaError_t publish_slots(hb_server *S) {
+    hb_batch *b = S->batch;
+    const int k = b->k;
+    S->tiles.assign(k + 1, 0);
+    for (int i = 0; i < k; ++i) S->tiles[i + 1] = S->tiles[i] + (S->slot_args[i].n + 255) / 256;
+    cudaError_t e = cudaMemcpyAsync(const_cast<StepArgs *>(b->B.args), S->slot_args.data(),
+                                    sizeof(StepArgs) * k, cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<int64_t *>(b->B.tile_prefix), S->tiles.data(), sizeof(int64_t) * (k + 1),
+                            cudaMemcpyHostToDevice, b->s);
+    return e;
+}
+
+void serve_loop(hb_server *S) {
+    hb_batch *b = S->batch;
+    const int k = b->k;
+    std::vector<int32_t> done(k);
+    std::vector<int64_t> garcs(k);
+    std::vector<ServeReq *> running_req(k, nullptr);
+    std::vector<char> fresh(k, 0);
+    for (;;) {
+        bool changed = false;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            // admission: FIFO, into free slots, while device memory allows
+            for (int slot = 0; slot < k && !S->queue.empty(); ++slot) {
+                if (S->slot_req[slot] >= 0) continue;
+                const int64_t id = S->queue.front();
+                ServeReq &r = S->reqs[id];
+                hb_graph *tmpl = S->pool[r.graph].tmpl[r.log2m];
+                size_t free_b = 0, total_b = 0;
+                cudaMemGetInfo(&free_b, &total_b);
+                if ((int64_t)free_b < (int64_t)run_bytes(tmpl) + S->opt.reserve_bytes) break;
+                S->queue.pop_front();
+                lk.unlock();
+                hb_graph *inst = nullptr;
+                hb_status st = make_instance(tmpl, r.seed, b->s, &inst);
+                lk.lock();
+                if (st != HB_OK) {
+                    r.state = HB_REQ_FAILED;
+                    r.err = st;
+                    r.t_done = S->now();
+                    S->done_cv.notify_all();
+                    --slot;
+                    continue;
+                }
+                r.inst = inst;
+                r.slot = slot;
+                r.state = HB_REQ_RUNNING;
+                r.t_admit = S->now();
+                S->slot_req[slot] = id;
+                S->slot_args[slot] = inst->a;
+                running_req[slot] = &r;
+                fresh[slot] = 1;
+                changed = true;
+            }
+            bool running = false;
+            for (int slot = 0; slot < k; ++slot) running |= S->slot_req[slot] >= 0;
+            if (!running) {
+                if (S->stop) return;
+                S->cv.wait(lk);
+                continue;
+            }
+        }
+        const double t_start = S->now();
+        cudaError_t e = cudaSuccess;
+        if (changed) {
+            e = publish_slots(S);
+            for (int slot = 0; slot < k && e == cudaSuccess; ++slot)
+                if (fresh[slot]) {
+                    e = cudaMemsetAsync(b->B.graph_arcs + slot, 0, sizeof(int64_t), b->s);
+                    fresh[slot] = 0;
+                }
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->step_exec, b->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(done.data(), b->B.done, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, b->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(garcs.data(), b->B.graph_arcs, sizeof(int64_t) * k, cudaMemcpyDeviceToHost, b->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+        if (e != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->fatal = cudaGetErrorString(e);
+            for (auto &kv : S->reqs)
+                if (kv.second.state == HB_REQ_RUNNING || kv.second.state == HB_REQ_QUEUED) {
+                    kv.second.state = HB_REQ_FAILED;
+                    kv.second.err = HB_ERR_CUDA;
+                }
+            S->done_cv.notify_all();
+            return;
+        }
+        ++S->iterations;
+        bool freed = false;
+        for (int slot = 0; slot < k; ++slot) {
+            if (!running_req[slot]) continue;
+            ServeReq &r = *running_req[slot];
+            r.steps += 1;
+            const bool capped = r.steps >= S->opt.max_steps;
+            if (!done[slot] && !capped) continue;
+            hb_graph *inst = r.inst;
+            hb_status st = sync_host_state(inst);
+            for (int q = 0; q < 4 && st == HB_OK; ++q) r.out[q].resize((size_t)inst->n);
+            if (st == HB_OK)
+                st = hb_get_centralities(inst, r.out[0].data(), r.out[1].data(), r.out[2].data(), r.out[3].data());
+            r.steps = inst->t;
+            r.arcs = garcs[slot];
+            hb_destroy(inst);
+            std::lock_guard<std::mutex> lk(S->mu);
+            r.inst = nullptr;
+            r.slot = -1;
+            r.err = st != HB_OK ? st : (done[slot] ? HB_OK : HB_ERR_NOT_CONVERGED);
+            r.state = r.err == HB_OK ? HB_REQ_DONE : HB_REQ_FAILED;
+            r.t_done = S->now();
+            S->total_arcs += r.arcs;
+            S->completed += 1;
+            S->slot_req[slot] = -1;
+            S->slot_args[slot] = null_slot(S, slot);
+            running_req[slot] = nullptr;
+            freed = true;
+            S->done_cv.notify_all();
+        }
+        if (freed) publish_slots(S);
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->busy_s += S->now() - t_start;
+    }
+}
+
+hb_status sfail(hb_status st, const std::string &m) {
+    set_last_error(m.c_str());
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hb_server_default_options(hb_server_options *o) {
+    if (!o) return;
+    o->slots = 32;
+    o->flags = 0;
+    o->max_steps = 1 << 16;
+    o->reserve_bytes = (int64_t)4 << 30;
+}
+
+hb_status hb_server_create(const hb_server_options *opt, hb_server **out) {
+    set_last_error("");
+    if (!out) return sfail(HB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    hb_server_options o;
+    if (opt) o = *opt; else hb_server_default_options(&o);
+    if (o.slots < 1 || o.slots > kMaxBatch) return sfail(HB_ERR_INVALID, "slots must lie in [1, 4096]");
+    if (o.max_steps <= 0) o.max_steps = 1 << 16;
+    if (o.reserve_bytes < 0) o.reserve_bytes = 0;
+    cudaFree(nullptr);
+    hb_server *S = new hb_server();
+    S->opt = o;
+    S->t0 = std::chrono::steady_clock::now();
+    hb_batch *b = new hb_batch();
+    S->batch = b;
+    b->k = o.slots;
+    b->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
+    b->max_steps = 1 << 30;
+    if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess) {
+        delete S;
+        return sfail(HB_ERR_CUDA, "cannot create the server stream");
+    }
+    b->own_stream = true;
+    S->null_ctr = S->mem.alloc<Counters>(o.slots);
+    if (!S->null_ctr) { delete S; return sfail(HB_ERR_OOM, "out of device memory"); }
+    std::vector<Counters> nc(o.slots);
+    for (auto &c : nc) { std::memset(&c, 0, sizeof(c)); c.converged = 1; }
+    if (cudaMemcpy(S->null_ctr, nc.data(), sizeof(Counters) * o.slots, cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete S;
+        return sfail(HB_ERR_CUDA, "server set-up");
+    }
+    S->slot_args.resize(o.slots);
+    S->slot_req.assign(o.slots, -1);
+    for (int i = 0; i < o.slots; ++i) S->slot_args[i] = null_slot(S, i);
+    std::vector<int64_t> tiles(o.slots + 1, 0);
+    hb_status st = batch_setup(b, S->slot_args, tiles);
+    if (st != HB_OK) { delete S; return st; }
+    S->th = std::thread(serve_loop, S);
+    *out = S;
+    return HB_OK;
+}
+
+hb_status hb_server_add_graph(hb_server *S, const int64_t *offsets, const int32_t *targets, int64_t n,
+                              int64_t m, const int32_t *log2ms, int n_log2m, int32_t *graph_id) {
+    if (!S || !graph_id || !log2ms || n_log2m < 1) return sfail(HB_ERR_INVALID, "NULL argument");
+    hb_options o;
+    hb_default_options(&o);
+    o.flags = (S->opt.flags & HB_FP32_ESTIMATE) | HB_BORROW_DEVICE_PTRS;
+    o.stream = nullptr;
+    PoolGraph pg;
+    pg.n = n;
+    pg.m = m;
+    // the pool keeps its own device copy of the CSR
+    pg.off = S->mem.alloc<int64_t>(n + 1);
+    pg.tgt = S->mem.alloc<int32_t>(m);
+    if (S->mem.err != cudaSuccess) return sfail(HB_ERR_OOM, "out of device memory (pool graph)");
+    cudaError_t e = cudaMemcpy(pg.off, offsets, sizeof(int64_t) * (n + 1), cudaMemcpyDefault);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpy(pg.tgt, targets, sizeof(int32_t) * m, cudaMemcpyDefault);
+    if (e != cudaSuccess) return sfail(HB_ERR_CUDA, std::string("pool upload: ") + cudaGetErrorString(e));
+    for (int i = 0; i < n_log2m; ++i) {
+        hb_graph *t = nullptr;
+        hb_status st = create_handle64(pg.off, pg.tgt, n, m, log2ms[i], 0, &o, &t);
+        if (st != HB_OK) {
+            for (auto &kv : pg.tmpl) hb_destroy(kv.second);
+            return st;
+        }
+        drop_run_state(t);
+        pg.tmpl[log2ms[i]] = t;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->pool.push_back(std::move(pg));
+    *graph_id = (int32_t)S->pool.size() - 1;
+    return HB_OK;
+}
+
+hb_status hb_server_submit(hb_server *S, int32_t graph_id, int32_t log2m, uint64_t seed, int64_t *request_id) {
+    if (!S || !request_id) return sfail(HB_ERR_INVALID, "NULL argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (!S->fatal.empty()) return sfail(HB_ERR_STATE, "server stopped after a CUDA error: " + S->fatal);
+    if (graph_id < 0 || graph_id >= (int32_t)S->pool.size()) return sfail(HB_ERR_INVALID, "unknown graph id");
+    if (!S->pool[graph_id].tmpl.count(log2m))
+        return sfail(HB_ERR_INVALID, "log2m not prepared for this graph (hb_server_add_graph)");
+    const int64_t id = S->next_id++;
+    ServeReq &r = S->reqs[id];
+    r.graph = graph_id;
+    r.log2m = log2m;
+    r.seed = seed;
+    r.t_submit = S->now();
+    S->queue.push_back(id);
+    *request_id = id;
+    S->cv.notify_all();
+    return HB_OK;
+}
+
+hb_status hb_server_wait(hb_server *S, int64_t request_id, double timeout_s, hb_request_info *info) {
+    if (!S) return sfail(HB_ERR_INVALID, "server is NULL");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) return sfail(HB_ERR_INVALID, "unknown request");
+    ServeReq &r = it->second;
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (r.state == HB_REQ_QUEUED || r.state == HB_REQ_RUNNING) {
+        if (timeout_s >= 0 && S->done_cv.wait_until(lk, deadline) == std::cv_status::timeout &&
+            (r.state == HB_REQ_QUEUED || r.state == HB_REQ_RUNNING))
+            break;
+        if (timeout_s < 0) S->done_cv.wait(lk);
+    }
+    if (info) {
+        info->state = r.state;
+        info->steps = r.steps;
+        info->arcs = r.arcs;
+        info->submit_s = r.t_submit;
+        info->admit_s = r.t_admit;
+        info->done_s = r.t_done;
+    }
+    if (r.state == HB_REQ_QUEUED || r.state == HB_REQ_RUNNING) return sfail(HB_ERR_TIMEOUT, "request not finished");
+    if (r.state == HB_REQ_FAILED) return sfail(r.err, "request failed");
+    return HB_OK;
+}
+
+hb_status hb_server_take(hb_server *S, int64_t request_id, double *closeness, double *harmonic, double *lin,
+                         double *reachable) {
+    if (!S) return sfail(HB_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) return sfail(HB_ERR_INVALID, "unknown request");
+    ServeReq &r = it->second;
+    if (r.state != HB_REQ_DONE) return sfail(HB_ERR_STATE, "request not done");
+    double *dst[4] = {closeness, harmonic, lin, reachable};
+    for (int q = 0; q < 4; ++q)
+        if (dst[q] && !r.out[q].empty()) std::memcpy(dst[q], r.out[q].data(), sizeof(double) * r.out[q].size());
+    S->reqs.erase(it);
+    return HB_OK;
+}
+
+hb_status hb_server_stats(hb_server *S, int64_t *completed, int64_t *iterations, int64_t *arcs,
+                          double *busy_s, double *clock_s) {
+    if (!S) return sfail(HB_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (completed) *completed = S->completed;
+    if (iterations) *iterations = S->iterations;
+    if (arcs) *arcs = S->total_arcs;
+    if (busy_s) *busy_s = S->busy_s;
+    if (clock_s) *clock_s = S->now();
+    return HB_OK;
+}
+
+void hb_server_destroy(hb_server *S) { delete S; }
 
 }  // extern "C"

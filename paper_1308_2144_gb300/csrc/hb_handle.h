@@ -44,6 +44,13 @@ hb_status create_handle64(const int64_t *offsets, const int32_t *targets, int64_
 // Bring the handle's host bookkeeping (t, convergence) up to date with its
 // device counters after kernels launched outside hb_step.
 hb_status sync_host_state(hb_graph *g);
+// Per-run state: its size, its allocation, and a new run (instance) that
+// borrows the read-only set-up of a template handle.
+size_t run_bytes(const hb_graph *g);
+hb_status setup_run(hb_graph *g);
+hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_graph **out);
+// Free the per-run state of a handle that serves only as a template.
+void drop_run_state(hb_graph *g);
 
 }  // namespace hb
 

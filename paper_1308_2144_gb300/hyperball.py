@@ -37,6 +37,8 @@ HB_PROFILE = 0x10
 
 FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
 
+HB_REQ_QUEUED, HB_REQ_RUNNING, HB_REQ_DONE, HB_REQ_FAILED = 0, 1, 2, 3
+
 # every symbol include/hyperball.h declares
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
@@ -44,7 +46,9 @@ EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
            "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
-           "hb_batch_destroy"]
+           "hb_batch_destroy", "hb_server_default_options", "hb_server_create",
+           "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_take",
+           "hb_server_stats", "hb_server_destroy"]
 
 
 class HBError(RuntimeError):
@@ -70,6 +74,19 @@ class Info(ctypes.Structure):
                 ("converged", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_double), ("kernel_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("flags", ctypes.c_uint32), ("max_steps", ctypes.c_int32),
+                ("reserve_bytes", ctypes.c_int64)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("steps", ctypes.c_int32), ("arcs", ctypes.c_int64),
+                ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -151,6 +168,27 @@ def load():
                                           ctypes.POINTER(ctypes.c_int64)]
         L.hb_batch_destroy.restype = None
         L.hb_batch_destroy.argtypes = [_vp]
+        L.hb_server_default_options.restype = None
+        L.hb_server_default_options.argtypes = [ctypes.POINTER(ServerOptions)]
+        L.hb_server_create.restype = st
+        L.hb_server_create.argtypes = [ctypes.POINTER(ServerOptions), ctypes.POINTER(_vp)]
+        L.hb_server_add_graph.restype = st
+        L.hb_server_add_graph.argtypes = [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int32)]
+        L.hb_server_submit.restype = st
+        L.hb_server_submit.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                       ctypes.POINTER(ctypes.c_int64)]
+        L.hb_server_wait.restype = st
+        L.hb_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(RequestInfo)]
+        L.hb_server_take.restype = st
+        L.hb_server_take.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
+        L.hb_server_stats.restype = st
+        L.hb_server_stats.argtypes = [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.hb_server_destroy.restype = None
+        L.hb_server_destroy.argtypes = [_vp]
         L.hb_step_noalloc.restype = st
         L.hb_step_noalloc.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                       ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
@@ -355,6 +393,65 @@ class HyperBallBatch:
     def close(self):
         if getattr(self, "_h", None):
             load().hb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HyperBallServer:
+    """The serving form: a request loop with continuous batching over a
+    pool of device-resident graphs (see hb_server_* in hyperball.h)."""
+
+    def __init__(self, slots=32, fp32=False, max_steps=1 << 16, reserve_bytes=4 << 30):
+        L = load()
+        o = ServerOptions()
+        L.hb_server_default_options(ctypes.byref(o))
+        o.slots, o.flags, o.max_steps, o.reserve_bytes = int(slots), HB_FP32_ESTIMATE if fp32 else 0, \
+            int(max_steps), int(reserve_bytes)
+        self._h = _vp()
+        _check(L.hb_server_create(ctypes.byref(o), ctypes.byref(self._h)))
+        self.sizes = []
+
+    def add_graph(self, offsets, targets, n, log2ms=(4,)) -> int:
+        arr = (ctypes.c_int32 * len(log2ms))(*[int(x) for x in log2ms])
+        gid = ctypes.c_int32()
+        _check(load().hb_server_add_graph(self._h, _ptr(offsets), _ptr(targets) if targets.shape[0] else None,
+                                          int(n), int(targets.shape[0]), arr, len(log2ms), ctypes.byref(gid)))
+        self.sizes.append(int(n))
+        return int(gid.value)
+
+    def submit(self, graph_id, log2m, seed) -> int:
+        rid = ctypes.c_int64()
+        _check(load().hb_server_submit(self._h, int(graph_id), int(log2m), int(seed) & (2**64 - 1),
+                                       ctypes.byref(rid)))
+        return int(rid.value)
+
+    def wait(self, request_id, timeout=-1.0) -> dict:
+        info = RequestInfo()
+        _check(load().hb_server_wait(self._h, int(request_id), float(timeout), ctypes.byref(info)))
+        return info.as_dict()
+
+    def take(self, request_id, n) -> dict:
+        out = {k: np.empty(n, dtype=np.float64) for k in ("closeness", "harmonic", "lin", "reachable")}
+        _check(load().hb_server_take(self._h, int(request_id), _ptr(out["closeness"]), _ptr(out["harmonic"]),
+                                     _ptr(out["lin"]), _ptr(out["reachable"])))
+        return out
+
+    def stats(self) -> dict:
+        c, it, a = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        busy, clock = ctypes.c_double(), ctypes.c_double()
+        _check(load().hb_server_stats(self._h, ctypes.byref(c), ctypes.byref(it), ctypes.byref(a),
+                                      ctypes.byref(busy), ctypes.byref(clock)))
+        return {"completed": c.value, "iterations": it.value, "arcs": a.value, "busy_s": busy.value,
+                "clock_s": clock.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hb_server_destroy(self._h)
             self._h = None
 
     def __del__(self):
