@@ -127,7 +127,6 @@ def recorded_traffic(workload):
     """DRAM traffic per gather-kernel launch from the committed ncu summary,
     valid only while the kernel source is the one that was profiled."""
     path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}_traffic.txt")
-    src = os.path.join(ROOT, "paper_1308_2144_gb300", "csrc", "hb_step.cu")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -135,13 +134,20 @@ def recorded_traffic(workload):
         if "=" in ln and not ln.startswith("#"):
             k, v = ln.split("=", 1)
             vals[k.strip()] = v.strip()
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if vals.get("source_sha256") != digest:
+    if vals.get("source_sha256") != kernel_source_digest():
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+def kernel_source_digest():
+    """sha256 over the sources the gather kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in ("hb_step.cu", "hb_step_dev.cuh", "hb_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1308_2144_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
 
 
 def dist_setup():

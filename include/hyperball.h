@@ -167,6 +167,17 @@ hb_status hb_get_info(hb_graph *g, hb_info *info);
 /* Re-initialise counters, accumulators and t (same graph, new seed). */
 hb_status hb_reset(hb_graph *g, uint64_t seed);
 
+/* Autotuner: choose how many lanes each light degree class of the gather
+ * kernel gets (the class sizing: about *arcs_per_slot arcs per lane slot;
+ * candidates 1, 2, 4, 8, 16) by timing the first two iterations with each
+ * candidate, then re-initialise the counters with the handle's seed.
+ * Results never depend on the choice.  *arcs_per_slot (may be NULL)
+ * receives the choice. */
+hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
+
+/* Set the class sizing directly (1, 2, 4, 8 or 16) and re-initialise. */
+hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot);
+
 /* Checkpoint: write t, counters, last frontier and accumulators (and the
  * graph) to a file; hb_load rebuilds a handle that continues exactly
  * where the saved one stopped. */
@@ -225,6 +236,10 @@ hb_status hb_batch_get_centralities(hb_batch *b, int i, double *closeness, doubl
 hb_status hb_batch_get_registers(hb_batch *b, int i, uint8_t *out);
 hb_status hb_batch_get_accumulators(hb_batch *b, int i, double *sumd, double *harm);
 hb_status hb_batch_get_info(hb_batch *b, int i, hb_info *info);
+
+/* Autotuner of the batch: as hb_tune, timing whole batched iterations;
+ * every graph is re-initialised afterwards. */
+hb_status hb_batch_tune(hb_batch *b, int32_t *arcs_per_slot);
 
 /* Batch iterations since the last reset, graphs still active, and arcs
  * scanned by all graphs (arc-updates). */

@@ -135,6 +135,7 @@ hb_status setup_shared(hb_graph *g) {
         a.seg_hi[k] = g->y.hi[k];
     }
     a.b = g->b;
+    a.aps = g->y.aps;
     a.frontier = g->opt.frontier;
     a.sparse_frac = 0.25;
     if (dense_list) {
@@ -247,11 +248,55 @@ void drop_run_state(hb_graph *g) {
     a.ctr = g->ctr = nullptr;
 }
 
+// Re-size the light degree classes (arcs per slot), keeping every read-only
+// array that does not depend on it: segments, the dense list of an
+// unrelabelled graph and the dense plan are rebuilt.
+hb_status retune(hb_graph *g, int aps) {
+    cudaStream_t s = g->s;
+    const int64_t n = g->n;
+    g->y = make_layout(g->b, aps);
+    cudaError_t e = count_degree_segments(g->off, n, g->y, g->seg_count, s);
+    if (e != cudaSuccess) return cuda_fail(e, "degree segments");
+    int64_t seg_begin[kSegs], run = 0;
+    for (int k = 0; k < kSegs; ++k) { seg_begin[k] = run; run += g->seg_count[k]; }
+    StepArgs &a = g->a;
+    for (int k = 0; k < kSegs; ++k) {
+        a.seg_begin[k] = seg_begin[k];
+        a.seg_lo[k] = g->y.lo[k];
+        a.seg_hi[k] = g->y.hi[k];
+    }
+    a.aps = aps;
+    if (a.dense_list) {
+        int64_t *sb_dev = nullptr;
+        unsigned long long *fill = nullptr;
+        e = cudaMallocAsync(&sb_dev, sizeof(seg_begin), s);
+        if (e == cudaSuccess) e = cudaMallocAsync(&fill, sizeof(unsigned long long) * kSegs, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sb_dev, seg_begin, sizeof(seg_begin), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = build_dense_list(g->off, n, g->y, sb_dev, const_cast<int32_t *>(a.dense_list), fill, s);
+        cudaFreeAsync(sb_dev, s);
+        cudaFreeAsync(fill, s);
+        if (e != cudaSuccess) return cuda_fail(e, "dense list");
+    }
+    e = launch_dense_plan(a, g->y, g->seg_count, const_cast<Plan *>(a.plan_dense),
+                          const_cast<int32_t *>(a.owner_dense), const_cast<int64_t *>(a.cstart_dense), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "dense plan");
+    return HB_OK;
+}
+
 // A new run on the shared set-up of `tmpl` (same graph and log2m): the
 // instance borrows the template's read-only arrays, owns only its per-run
 // state, and starts from the counters of `seed`.
-hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_graph **out) {
+hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_graph **out,
+                        cudaMemPool_t pool, Counters *ctr_host) {
     hb_graph *g = new hb_graph();
+    g->mem.pool = pool;
+    g->mem.stream = s;
+    if (ctr_host) {
+        g->ctr_host = ctr_host;
+        g->own_ctr_host = false;
+    }
     g->n = tmpl->n; g->m = tmpl->m; g->b = tmpl->b; g->y = tmpl->y;
     g->opt = tmpl->opt;
     g->s = s;
@@ -628,6 +673,49 @@ hb_status hb_get_info(hb_graph *g, hb_info *info) {
     info->kernel_ms = g->kernel_ms;
     info->kernel_bytes = g->kernel_bytes;
     return HB_OK;
+}
+
+hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    bool ok = false;
+    for (int c : kTuneAps) ok |= c == arcs_per_slot;
+    if (!ok) return fail(HB_ERR_INVALID, "arcs_per_slot must be 1, 2, 4, 8 or 16");
+    st = retune(g, arcs_per_slot);
+    return st == HB_OK ? init_state(g, g->seed) : st;
+}
+
+hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    const uint64_t seed = g->seed;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(HB_ERR_CUDA, "tuning events");
+    int best = g->y.aps;
+    float best_ms = 1e30f;
+    for (int aps : kTuneAps) {
+        st = retune(g, aps);
+        if (st == HB_OK) st = init_state(g, seed);
+        if (st != HB_OK) break;
+        // time the first two iterations (every node recomputed and changing)
+        cudaEventRecord(e0, g->s);
+        for (int i = 0; i < 2 && st == HB_OK; ++i) st = hb_step(g, nullptr);
+        cudaEventRecord(e1, g->s);
+        float ms = 0.f;
+        if (st == HB_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = aps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HB_OK) return st;
+    st = retune(g, best);
+    if (st == HB_OK) st = init_state(g, seed);
+    if (st == HB_OK && arcs_per_slot) *arcs_per_slot = best;
+    return st;
 }
 
 hb_status hb_reset(hb_graph *g, uint64_t seed) {

@@ -34,7 +34,7 @@ struct BatchCtl {
 
 struct BatchArrays {
     const StepArgs *args;          // [k]
-    int64_t *item_prefix;          // [k+1] work items of the running iteration
+    int64_t *item_prefix;          // [9][k+1] work items of the running iteration, per log2m
     int64_t *list_prefix;          // [k+1] previous changed lists (push marking)
     int64_t *big_prefix;           // [k+1] previous many-predecessor lists
     int64_t *copy_prefix;          // [k+1] copy-forward elements
@@ -45,6 +45,7 @@ struct BatchArrays {
     BatchCtl *ctl;
     int k;
     int use_cond;
+    unsigned log2m_mask;           // bit b-4 set: some graph has log2m b
     cudaGraphConditionalHandle cond;
 };
 
@@ -172,13 +173,17 @@ __global__ void batch_plan_kernel(BatchArrays B) {
     }
 }
 
+// Work-item prefixes, one per log2m present: graphs of other log2m count 0.
 __global__ void batch_items_kernel(BatchArrays B) {
-    graph_prefix(B.k, B.item_prefix, [&](int g) -> int64_t {
-        const StepArgs &a = B.args[g];
-        const int mode = a.ctr->mode;
-        if (mode == kMode_Idle) return 0;
-        return mode == 1 ? a.plan_sparse->items : a.plan_dense->items;
-    });
+    for (int lb = kMinLog2m; lb <= kMaxLog2m; ++lb) {
+        if (!((B.log2m_mask >> (lb - kMinLog2m)) & 1u)) continue;
+        graph_prefix(B.k, B.item_prefix + (size_t)(lb - kMinLog2m) * (B.k + 1), [&](int g) -> int64_t {
+            const StepArgs &a = B.args[g];
+            const int mode = a.ctr->mode;
+            if (mode == kMode_Idle || a.b != lb) return 0;
+            return mode == 1 ? a.plan_sparse->items : a.plan_dense->items;
+        });
+    }
 }
 
 // Work item `it` of one graph (the body of the single-graph step kernel's
@@ -213,15 +218,20 @@ __device__ __forceinline__ void batch_item(const StepArgs &a, int64_t it, int t,
                            biglist, sparse, cnt, rdist64, rdist32, pow2, prefetch);
 }
 
-template <bool F32>
-__global__ void __launch_bounds__(kStepThreads, 3) batch_step_kernel(BatchArrays B) {
+// The gather kernel over the items of every graph with log2m = LOG2P (one
+// instantiation per log2m keeps its register budget that of the
+// single-graph kernel).
+template <int LOG2P, bool F32>
+__global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : 4)
+    batch_step_kernel(BatchArrays B) {
     extern __shared__ int64_t s_prefix[];                 // [k+1]
-    __shared__ unsigned long long s_pow2[kMaxLog2m - kMinLog2m + 1][64];
+    __shared__ unsigned long long s_pow2[64];
     __shared__ unsigned long long s_cnt[kStepThreads / 32];
-    for (int i = threadIdx.x; i <= B.k; i += blockDim.x) s_prefix[i] = B.item_prefix[i];
-    for (int i = threadIdx.x; i < (kMaxLog2m - kMinLog2m + 1) * 64; i += blockDim.x) {
-        const int b = kMinLog2m + i / 64, M = i % 64, sh = 64 - b;
-        s_pow2[i / 64][M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
+    const int64_t *prefix = B.item_prefix + (size_t)(LOG2P - kMinLog2m) * (B.k + 1);
+    for (int i = threadIdx.x; i <= B.k; i += blockDim.x) s_prefix[i] = prefix[i];
+    if (threadIdx.x < 64) {
+        const int M = threadIdx.x, sh = 64 - LOG2P;
+        s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) s_cnt[wid] = 0;
@@ -250,18 +260,30 @@ __global__ void __launch_bounds__(kStepThreads, 3) batch_step_kernel(BatchArrays
             rd32 = 1.0f / (float)(t + 1);
         }
         __syncwarp();
-        const int64_t local = it - s_prefix[g];
-        const unsigned long long *pow2 = s_pow2[a.b - kMinLog2m];
-        switch (a.b) {
-#define HB_CASE(LB) case LB: batch_item<LB, F32>(a, local, t, sparse, rd64, rd32, pow2, prefetch, &s_cnt[wid]); break;
-            HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
-            HB_CASE(12)
-#undef HB_CASE
-            default: break;
-        }
+        batch_item<LOG2P, F32>(a, it - s_prefix[g], t, sparse, rd64, rd32, s_pow2, prefetch, &s_cnt[wid]);
     }
     __syncwarp();
     if (cur_g >= 0 && lane == 0 && s_cnt[wid]) atomicAdd(&B.args[cur_g].ctr->n_changed, s_cnt[wid]);
+}
+
+template <bool F32>
+const void *batch_step_ptr(int lb) {
+    switch (lb) {
+#define HB_CASE(LB) case LB: return reinterpret_cast<const void *>(&batch_step_kernel<LB, F32>);
+        HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11) HB_CASE(12)
+#undef HB_CASE
+        default: return nullptr;
+    }
+}
+
+template <bool F32>
+void launch_batch_step(int lb, int grid, size_t smem, cudaStream_t s, const BatchArrays &B) {
+    switch (lb) {
+#define HB_CASE(LB) case LB: batch_step_kernel<LB, F32><<<grid, kStepThreads, smem, s>>>(B); break;
+        HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11) HB_CASE(12)
+#undef HB_CASE
+        default: break;
+    }
 }
 
 // Changed-list compaction for graphs that ran a dense iteration.
@@ -332,8 +354,17 @@ struct hb_batch {
     cudaGraph_t step_graph = nullptr;
     cudaGraph_t run_graph = nullptr;
     int32_t max_steps = 1 << 20;
+    unsigned log2m_mask = 0;
+    int lb_grid[kMaxLog2m + 1] = {0};
+    cudaStream_t side[kMaxLog2m + 1] = {nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join[kMaxLog2m + 1] = {nullptr};
 
     ~hb_batch() {
+        for (int i = 0; i <= kMaxLog2m; ++i) {
+            if (side[i]) cudaStreamDestroy(side[i]);
+            if (ev_join[i]) cudaEventDestroy(ev_join[i]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
         if (step_exec) cudaGraphExecDestroy(step_exec);
         if (run_exec) cudaGraphExecDestroy(run_exec);
         if (step_graph) cudaGraphDestroy(step_graph);
@@ -362,8 +393,16 @@ cudaError_t enqueue_iteration(hb_batch *b, const BatchArrays &B) {
     batch_plan_kernel<<<b->k < 65535 ? b->k : 65535, 1024, 0, s>>>(B);
     batch_items_kernel<<<1, 1024, 0, s>>>(B);
     const size_t smem = sizeof(int64_t) * (size_t)(B.k + 1);
-    if (b->fp32) batch_step_kernel<true><<<b->step_grid, kStepThreads, smem, s>>>(B);
-    else batch_step_kernel<false><<<b->step_grid, kStepThreads, smem, s>>>(B);
+    // one gather kernel per log2m present, as parallel branches
+    cudaEventRecord(b->ev_fork, s);
+    for (int lb = kMinLog2m; lb <= kMaxLog2m; ++lb) {
+        if (!((b->log2m_mask >> (lb - kMinLog2m)) & 1u)) continue;
+        cudaStreamWaitEvent(b->side[lb], b->ev_fork, 0);
+        if (b->fp32) launch_batch_step<true>(lb, b->lb_grid[lb], smem, b->side[lb], B);
+        else launch_batch_step<false>(lb, b->lb_grid[lb], smem, b->side[lb], B);
+        cudaEventRecord(b->ev_join[lb], b->side[lb]);
+        cudaStreamWaitEvent(s, b->ev_join[lb], 0);
+    }
     batch_compact_kernel<<<b->aux_grid, 256, 0, s>>>(B);
     batch_end_kernel<<<1, 1024, 0, s>>>(B);
     return cudaGetLastError();
@@ -435,7 +474,7 @@ hb_status batch_setup(hb_batch *b, const std::vector<StepArgs> &hargs, const std
     const int k = b->k;
     DevMem &M = b->mem;
     StepArgs *args = M.alloc<StepArgs>(k);
-    int64_t *pref = M.alloc<int64_t>((size_t)6 * (k + 1));
+    int64_t *pref = M.alloc<int64_t>((size_t)14 * (k + 1));
     int64_t *garcs = M.alloc<int64_t>(k);
     int32_t *done = M.alloc<int32_t>(k);
     BatchCtl *ctl = M.alloc<BatchCtl>(1);
@@ -448,27 +487,35 @@ hb_status batch_setup(hb_batch *b, const std::vector<StepArgs> &hargs, const std
     if (e != cudaSuccess) return bfail(HB_ERR_CUDA, "batch upload");
     BatchArrays &B = b->B;
     B.args = args;
-    B.item_prefix = pref;
+    B.item_prefix = pref + 6 * (k + 1);   // 9 arrays, one per log2m
     B.list_prefix = pref + (k + 1);
     B.big_prefix = pref + 2 * (k + 1);
     B.copy_prefix = pref + 3 * (k + 1);
     B.word_prefix = pref + 4 * (k + 1);
     B.tile_prefix = pref + 5 * (k + 1);
+    B.log2m_mask = b->log2m_mask;
     B.graph_arcs = garcs;
     B.done = done;
     B.ctl = ctl;
     B.k = k;
-    int dev = 0, sms = 0, per = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t smem = sizeof(int64_t) * (size_t)(k + 1);
-    if (smem > 48 * 1024) {
-        cudaFuncSetAttribute(batch_step_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(batch_step_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return bfail(HB_ERR_CUDA, "batch events");
+    for (int lb = kMinLog2m; lb <= kMaxLog2m; ++lb) {
+        if (!((b->log2m_mask >> (lb - kMinLog2m)) & 1u)) continue;
+        const void *fn = b->fp32 ? batch_step_ptr<true>(lb) : batch_step_ptr<false>(lb);
+        if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kStepThreads, smem);
+        b->lb_grid[lb] = sms * (per > 0 ? per : 1);
+        if (cudaStreamCreateWithFlags(&b->side[lb], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[lb], cudaEventDisableTiming) != cudaSuccess)
+            return bfail(HB_ERR_CUDA, "batch streams");
     }
-    if (b->fp32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<true>, kStepThreads, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_step_kernel<false>, kStepThreads, smem);
-    b->step_grid = sms * (per > 0 ? per : 1);
+    b->step_grid = sms * 6;
     b->aux_grid = sms * 8;
     hb_status st = reset_ctl(b);
     if (st == HB_OK) st = build_graphs(b);
@@ -520,6 +567,7 @@ hb_status hb_batch_create(int k, const hb_graph_desc *gs, const hb_options *opt,
     for (int i = 0; i < k; ++i) {
         hargs[i] = b->graphs[i]->a;
         tiles[i + 1] = tiles[i] + (b->graphs[i]->n + 255) / 256;
+        b->log2m_mask |= 1u << (b->graphs[i]->b - kMinLog2m);
     }
     hb_status st = batch_setup(b, hargs, tiles);
     if (st != HB_OK) { delete b; return st; }
@@ -598,6 +646,48 @@ hb_status hb_batch_get_info(hb_batch *b, int i, hb_info *info) {
     return HB_OK;
 }
 
+hb_status hb_batch_tune(hb_batch *b, int32_t *arcs_per_slot) {
+    if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(HB_ERR_CUDA, "tuning events");
+    auto apply = [&](int aps) -> hb_status {
+        std::vector<StepArgs> hargs(b->k);
+        for (int i = 0; i < b->k; ++i) {
+            hb_graph *g = b->graphs[i];
+            hb_status st = retune(g, aps);
+            if (st == HB_OK) st = hb_reset(g, g->seed);
+            if (st != HB_OK) return st;
+            hargs[i] = g->a;
+        }
+        cudaError_t e = cudaMemcpyAsync(const_cast<StepArgs *>(b->B.args), hargs.data(), sizeof(StepArgs) * b->k,
+                                        cudaMemcpyHostToDevice, b->s);
+        if (e != cudaSuccess) return bfail(HB_ERR_CUDA, "batch tune upload");
+        return reset_ctl(b);
+    };
+    int best = kArcsPerSlot;
+    float best_ms = 1e30f;
+    hb_status st = HB_OK;
+    for (int aps : kTuneAps) {
+        st = apply(aps);
+        if (st != HB_OK) break;
+        cudaEventRecord(e0, b->s);
+        for (int i = 0; i < 2; ++i) cudaGraphLaunch(b->step_exec, b->s);
+        cudaEventRecord(e1, b->s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            ms < best_ms) {
+            best_ms = ms;
+            best = aps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == HB_OK) st = apply(best);
+    if (st == HB_OK && arcs_per_slot) *arcs_per_slot = best;
+    return st;
+}
+
 hb_status hb_batch_get_totals(hb_batch *b, int32_t *iterations, int32_t *n_active, int64_t *arcs) {
     if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
     hb_status st = read_ctl(b);
@@ -644,7 +734,8 @@ struct ServeReq {
     int32_t steps = 0;
     int64_t arcs = 0;
     hb_status err = HB_OK;
-    std::vector<double> out[4];
+    int64_t n = 0;
+    double *dres = nullptr;   // device: closeness, harmonic, lin, reachable (n each)
 };
 
 struct PoolGraph {
@@ -660,11 +751,14 @@ struct hb_server {
     hb_server_options opt{};
     hb_batch *batch = nullptr;
     DevMem mem;
+    cudaMemPool_t pool = nullptr;       // per-request state and results, stream-ordered
+    Counters *ctr_host = nullptr;       // pinned counter block shared by the server's instances
+    cudaStream_t copy_stream = nullptr; // result copies to the client
     Counters *null_ctr = nullptr;
     std::vector<StepArgs> slot_args;
     std::vector<int64_t> slot_req;
     std::vector<int64_t> tiles;
-    std::vector<PoolGraph> pool;
+    std::vector<PoolGraph> graphs;
     std::map<int64_t, ServeReq> reqs;
     std::deque<int64_t> queue;
     int64_t next_id = 1;
@@ -687,12 +781,19 @@ struct hb_server {
         }
         cv.notify_all();
         if (th.joinable()) th.join();
-        for (auto &kv : reqs)
+        cudaStream_t s = batch ? batch->s : nullptr;
+        for (auto &kv : reqs) {
             if (kv.second.inst) hb_destroy(kv.second.inst);
-        for (auto &pg : pool)
+            if (kv.second.dres) cudaFreeAsync(kv.second.dres, s);
+        }
+        for (auto &pg : graphs)
             for (auto &kv : pg.tmpl) hb_destroy(kv.second);
+        if (s) cudaStreamSynchronize(s);
+        if (copy_stream) { cudaStreamSynchronize(copy_stream); cudaStreamDestroy(copy_stream); }
         delete batch;
         mem.free_all();
+        if (pool) cudaMemPoolDestroy(pool);
+        if (ctr_host) cudaFreeHost(ctr_host);
     }
 };
 
@@ -736,14 +837,20 @@ void serve_loop(hb_server *S) {
                 if (S->slot_req[slot] >= 0) continue;
                 const int64_t id = S->queue.front();
                 ServeReq &r = S->reqs[id];
-                hb_graph *tmpl = S->pool[r.graph].tmpl[r.log2m];
-                size_t free_b = 0, total_b = 0;
+                hb_graph *tmpl = S->graphs[r.graph].tmpl[r.log2m];
+                // admission by device memory: free memory plus what the
+                // server's pool holds but does not use
+                size_t free_b = 0, total_b = 0, reserved = 0, used = 0;
                 cudaMemGetInfo(&free_b, &total_b);
-                if ((int64_t)free_b < (int64_t)run_bytes(tmpl) + S->opt.reserve_bytes) break;
+                cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+                cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrUsedMemCurrent, &used);
+                const int64_t avail = (int64_t)free_b + (int64_t)(reserved - used);
+                const int64_t need = (int64_t)run_bytes(tmpl) + 32 * tmpl->n + 4096;
+                if (avail < need + S->opt.reserve_bytes) break;
                 S->queue.pop_front();
                 lk.unlock();
                 hb_graph *inst = nullptr;
-                hb_status st = make_instance(tmpl, r.seed, b->s, &inst);
+                hb_status st = make_instance(tmpl, r.seed, b->s, &inst, S->pool, S->ctr_host);
                 lk.lock();
                 if (st != HB_OK) {
                     r.state = HB_REQ_FAILED;
@@ -806,12 +913,25 @@ void serve_loop(hb_server *S) {
             if (!done[slot] && !capped) continue;
             hb_graph *inst = r.inst;
             hb_status st = sync_host_state(inst);
-            for (int q = 0; q < 4 && st == HB_OK; ++q) r.out[q].resize((size_t)inst->n);
+            // results stay on the device until the client takes them; the
+            // counters and the rest of the run state are freed now
+            double *dres = nullptr;
+            if (st == HB_OK && cudaMallocFromPoolAsync(reinterpret_cast<void **>(&dres),
+                                                       sizeof(double) * 4 * (size_t)(inst->n > 0 ? inst->n : 1),
+                                                       S->pool, b->s) != cudaSuccess) {
+                cudaGetLastError();
+                dres = nullptr;
+                st = HB_ERR_OOM;
+            }
+            const size_t nn = (size_t)inst->n;
             if (st == HB_OK)
-                st = hb_get_centralities(inst, r.out[0].data(), r.out[1].data(), r.out[2].data(), r.out[3].data());
+                st = hb_get_centralities(inst, dres, dres + nn, dres + 2 * nn, dres + 3 * nn);
             r.steps = inst->t;
             r.arcs = garcs[slot];
+            r.n = inst->n;
             hb_destroy(inst);
+            if (st != HB_OK && dres) { cudaFreeAsync(dres, b->s); dres = nullptr; }
+            r.dres = dres;
             std::lock_guard<std::mutex> lk(S->mu);
             r.inst = nullptr;
             r.slot = -1;
@@ -867,11 +987,26 @@ hb_status hb_server_create(const hb_server_options *opt, hb_server **out) {
     b->k = o.slots;
     b->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
     b->max_steps = 1 << 30;
+    b->log2m_mask = (1u << (kMaxLog2m - kMinLog2m + 1)) - 1;   // requests may use any log2m
     if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess) {
         delete S;
         return sfail(HB_ERR_CUDA, "cannot create the server stream");
     }
     b->own_stream = true;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    uint64_t keep = UINT64_MAX;
+    if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaMallocHost(&S->ctr_host, sizeof(Counters)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete S;
+        return sfail(HB_ERR_CUDA, "server memory pool or streams");
+    }
     S->null_ctr = S->mem.alloc<Counters>(o.slots);
     if (!S->null_ctr) { delete S; return sfail(HB_ERR_OOM, "out of device memory"); }
     std::vector<Counters> nc(o.slots);
@@ -919,8 +1054,8 @@ hb_status hb_server_add_graph(hb_server *S, const int64_t *offsets, const int32_
         pg.tmpl[log2ms[i]] = t;
     }
     std::lock_guard<std::mutex> lk(S->mu);
-    S->pool.push_back(std::move(pg));
-    *graph_id = (int32_t)S->pool.size() - 1;
+    S->graphs.push_back(std::move(pg));
+    *graph_id = (int32_t)S->graphs.size() - 1;
     return HB_OK;
 }
 
@@ -928,8 +1063,8 @@ hb_status hb_server_submit(hb_server *S, int32_t graph_id, int32_t log2m, uint64
     if (!S || !request_id) return sfail(HB_ERR_INVALID, "NULL argument");
     std::lock_guard<std::mutex> lk(S->mu);
     if (!S->fatal.empty()) return sfail(HB_ERR_STATE, "server stopped after a CUDA error: " + S->fatal);
-    if (graph_id < 0 || graph_id >= (int32_t)S->pool.size()) return sfail(HB_ERR_INVALID, "unknown graph id");
-    if (!S->pool[graph_id].tmpl.count(log2m))
+    if (graph_id < 0 || graph_id >= (int32_t)S->graphs.size()) return sfail(HB_ERR_INVALID, "unknown graph id");
+    if (!S->graphs[graph_id].tmpl.count(log2m))
         return sfail(HB_ERR_INVALID, "log2m not prepared for this graph (hb_server_add_graph)");
     const int64_t id = S->next_id++;
     ServeReq &r = S->reqs[id];
@@ -972,15 +1107,27 @@ hb_status hb_server_wait(hb_server *S, int64_t request_id, double timeout_s, hb_
 hb_status hb_server_take(hb_server *S, int64_t request_id, double *closeness, double *harmonic, double *lin,
                          double *reachable) {
     if (!S) return sfail(HB_ERR_INVALID, "server is NULL");
-    std::lock_guard<std::mutex> lk(S->mu);
-    auto it = S->reqs.find(request_id);
-    if (it == S->reqs.end()) return sfail(HB_ERR_INVALID, "unknown request");
-    ServeReq &r = it->second;
-    if (r.state != HB_REQ_DONE) return sfail(HB_ERR_STATE, "request not done");
+    double *dres = nullptr;
+    int64_t n = 0;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(request_id);
+        if (it == S->reqs.end()) return sfail(HB_ERR_INVALID, "unknown request");
+        ServeReq &r = it->second;
+        if (r.state != HB_REQ_DONE) return sfail(HB_ERR_STATE, "request not done");
+        dres = r.dres;
+        n = r.n;
+        S->reqs.erase(it);
+    }
+    // copied outside the lock, so the server loop keeps running meanwhile
     double *dst[4] = {closeness, harmonic, lin, reachable};
-    for (int q = 0; q < 4; ++q)
-        if (dst[q] && !r.out[q].empty()) std::memcpy(dst[q], r.out[q].data(), sizeof(double) * r.out[q].size());
-    S->reqs.erase(it);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q)
+        if (dst[q] && n > 0)
+            e = cudaMemcpyAsync(dst[q], dres + (size_t)q * n, sizeof(double) * n, cudaMemcpyDefault, S->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->copy_stream);
+    cudaFreeAsync(dres, S->copy_stream);
+    if (e != cudaSuccess) return sfail(HB_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
     return HB_OK;
 }
 

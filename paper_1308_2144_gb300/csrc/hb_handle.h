@@ -15,28 +15,35 @@ struct DevMem {
     std::vector<void *> blocks;
     size_t bytes = 0;
     cudaError_t err = cudaSuccess;
+    // With a pool, allocations are stream-ordered on `stream` from that pool
+    // (no device-wide synchronisation on free).
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t stream = nullptr;
     template <class T>
     T *alloc(size_t count) {
         if (err != cudaSuccess) return nullptr;
         void *p = nullptr;
         size_t sz = count * sizeof(T);
         if (sz == 0) sz = 16;
-        err = cudaMalloc(&p, sz);
+        err = pool ? cudaMallocFromPoolAsync(&p, sz, pool, stream) : cudaMalloc(&p, sz);
         if (err != cudaSuccess) { cudaGetLastError(); return nullptr; }
         blocks.push_back(p);
         bytes += sz;
         return static_cast<T *>(p);
     }
+    void free_one(void *p) {
+        if (pool) cudaFreeAsync(p, stream);
+        else cudaFree(p);
+    }
     void release(void *p) {
         for (size_t i = 0; i < blocks.size(); ++i)
-            if (blocks[i] == p) { cudaFree(p); blocks.erase(blocks.begin() + (long)i); return; }
+            if (blocks[i] == p) { free_one(p); blocks.erase(blocks.begin() + (long)i); return; }
     }
     void free_all() {
-        for (void *p : blocks) cudaFree(p);
+        for (void *p : blocks) free_one(p);
         blocks.clear();
     }
 };
-
 
 // Host-side services of hb_api.cu used by the other translation units.
 hb_status create_handle64(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
@@ -48,9 +55,17 @@ hb_status sync_host_state(hb_graph *g);
 // borrows the read-only set-up of a template handle.
 size_t run_bytes(const hb_graph *g);
 hb_status setup_run(hb_graph *g);
-hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_graph **out);
+// The instance's run state comes from `pool` (stream-ordered on s) when
+// given, and it reads its counters through `ctr_host` (pinned, owned by the
+// caller) when given.
+hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_graph **out,
+                        cudaMemPool_t pool = nullptr, Counters *ctr_host = nullptr);
 // Free the per-run state of a handle that serves only as a template.
 void drop_run_state(hb_graph *g);
+// Re-size the light degree classes of a handle (autotuner).
+hb_status retune(hb_graph *g, int aps);
+// Candidate class sizings the autotuners try.
+constexpr int kTuneAps[] = {1, 2, 4, 8, 16};
 
 }  // namespace hb
 
@@ -88,10 +103,12 @@ struct hb_graph {
     int64_t kernel_launches = 0;
     double kernel_ms = 0.0, kernel_bytes = 0.0;
 
+    bool own_ctr_host = true;
+
     ~hb_graph() {
         if (ev[0]) cudaEventDestroy(ev[0]);
         if (ev[1]) cudaEventDestroy(ev[1]);
-        if (ctr_host) cudaFreeHost(ctr_host);
+        if (ctr_host && own_ctr_host) cudaFreeHost(ctr_host);
         mem.free_all();
     }
 };

@@ -11,7 +11,7 @@ constexpr int kWarp = 32;
 constexpr int kMaxLog2m = 12;
 constexpr int kMinLog2m = 4;
 constexpr int kSegs = 7;          // segment 0: heavy nodes; 1..6: light classes
-constexpr int kArcsPerSlot = 4;   // class sizing: about this many arcs per lane slot
+constexpr int kArcsPerSlot = 4;   // default class sizing: about this many arcs per lane slot
 constexpr int kStepThreads = 256;
 constexpr int kBigRdeg = 1024;    // changed nodes with more predecessors are pushed grid-wide
 
@@ -35,15 +35,19 @@ struct Cfg {
 
 // Host-side copy of the same numbers for a runtime log2m.
 struct Layout {
-    int log2m, P, logL, L, logSmax, nlight;
+    int log2m, P, logL, L, logSmax, nlight, aps;
     int64_t chunk, heavy;
     // degree bounds of segment s: nodes with lo[s] <= deg <= hi[s]
     int64_t lo[kSegs], hi[kSegs];
 };
 
-inline Layout make_layout(int log2m) {
+// aps (arcs per slot, a power of two from 1 to 16) sizes the light degree
+// classes: a node of degree d gets the smallest team whose slots each take
+// at most aps arcs.  The autotuner picks it per graph.
+inline Layout make_layout(int log2m, int aps = kArcsPerSlot) {
     Layout y{};
     y.log2m = log2m;
+    y.aps = aps;
     y.P = 1 << log2m;
     y.logL = (log2m - 4) < 5 ? (log2m - 4) : 5;
     y.L = 1 << y.logL;
@@ -55,8 +59,8 @@ inline Layout make_layout(int log2m) {
     y.hi[0] = INT64_MAX;
     for (int j = 0; j < y.nlight; ++j) {
         int64_t s = 1LL << (y.logSmax - j);
-        y.hi[j + 1] = (j == 0) ? y.heavy : kArcsPerSlot * s;
-        y.lo[j + 1] = (j == y.nlight - 1) ? 1 : kArcsPerSlot * s / 2 + 1;
+        y.hi[j + 1] = (j == 0) ? y.heavy : aps * s;
+        y.lo[j + 1] = (j == y.nlight - 1) ? 1 : aps * s / 2 + 1;
     }
     for (int s = y.nlight + 1; s < kSegs; ++s) { y.lo[s] = 1; y.hi[s] = 0; }
     return y;
@@ -140,6 +144,7 @@ struct StepArgs {
     int32_t frontier;             // HB_FRONTIER_* policy
     int32_t has_reverse;          // roff/rtgt present
     int32_t hot_nodes;            // counters of nodes below this id are kept in L2
+    int32_t aps;                  // class sizing (arcs per slot) of the layout
     double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
 };
 

@@ -211,6 +211,7 @@ extern "C" hb_status hb_step_noalloc(const int64_t *offsets, const int32_t *targ
     a.m = m;
     for (int k = 0; k < kSegs; ++k) { a.seg_begin[k] = seg_begin[k]; a.seg_lo[k] = y.lo[k]; a.seg_hi[k] = y.hi[k]; }
     a.b = log2m;
+    a.aps = y.aps;
     a.frontier = HB_FRONTIER_OFF;
     a.has_reverse = 0;
 

@@ -255,9 +255,12 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
     if (logS == C::LOGSMAX)
         gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
+    else if (a.aps <= 2)
+        gather_arcs<LOG2P, 2>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
+    else if (a.aps <= 4)
+        gather_arcs<LOG2P, 4>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
     else
-        gather_arcs<LOG2P, kArcsPerSlot>(a.tgt, cur, e0 + slot, e1, logS, cl, acc,
-                                         (uint32_t)a.hot_nodes);
+        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));

@@ -46,7 +46,7 @@ EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
            "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
-           "hb_batch_destroy", "hb_server_default_options", "hb_server_create",
+           "hb_batch_destroy", "hb_tune", "hb_set_class_sizing", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
            "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_take",
            "hb_server_stats", "hb_server_destroy"]
 
@@ -136,6 +136,12 @@ def load():
         L.hb_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
         L.hb_reset.restype = st
         L.hb_reset.argtypes = [_vp, ctypes.c_uint64]
+        L.hb_set_class_sizing.restype = st
+        L.hb_set_class_sizing.argtypes = [_vp, ctypes.c_int32]
+        L.hb_tune.restype = st
+        L.hb_tune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+        L.hb_batch_tune.restype = st
+        L.hb_batch_tune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
         L.hb_save.restype = st
         L.hb_save.argtypes = [_vp, ctypes.c_char_p]
         L.hb_load.restype = st
@@ -292,6 +298,13 @@ def hb_reset(h, seed: int):
     _check(load().hb_reset(h, int(seed) & (2**64 - 1)))
 
 
+def hb_tune(h) -> int:
+    """Autotune the degree-class sizing; returns the chosen arcs per slot."""
+    a = ctypes.c_int32()
+    _check(load().hb_tune(h, ctypes.byref(a)))
+    return int(a.value)
+
+
 def hb_save(h, path: str):
     _check(load().hb_save(h, path.encode()))
 
@@ -352,6 +365,11 @@ class HyperBallBatch:
         it = ctypes.c_int32()
         _check(load().hb_batch_run(self._h, ctypes.byref(it)))
         return int(it.value)
+
+    def tune(self) -> int:
+        a = ctypes.c_int32()
+        _check(load().hb_batch_tune(self._h, ctypes.byref(a)))
+        return int(a.value)
 
     def reset(self, seeds=None):
         arr = None
@@ -435,8 +453,12 @@ class HyperBallServer:
         _check(load().hb_server_wait(self._h, int(request_id), float(timeout), ctypes.byref(info)))
         return info.as_dict()
 
-    def take(self, request_id, n) -> dict:
-        out = {k: np.empty(n, dtype=np.float64) for k in ("closeness", "harmonic", "lin", "reachable")}
+    def take(self, request_id, n, out=None) -> dict:
+        """Copy a finished request's centralities into `out` (a dict of
+        float64 buffers of n entries: numpy, or torch on the host (pinned is
+        fastest) or the GPU), allocated here if None."""
+        if out is None:
+            out = {k: np.empty(n, dtype=np.float64) for k in ("closeness", "harmonic", "lin", "reachable")}
         _check(load().hb_server_take(self._h, int(request_id), _ptr(out["closeness"]), _ptr(out["harmonic"]),
                                      _ptr(out["lin"]), _ptr(out["reachable"])))
         return out
@@ -495,6 +517,12 @@ class HyperBall:
 
     def reset(self, seed: int):
         hb_reset(self._h, seed)
+
+    def tune(self) -> int:
+        return hb_tune(self._h)
+
+    def set_class_sizing(self, arcs_per_slot: int):
+        _check(load().hb_set_class_sizing(self._h, int(arcs_per_slot)))
 
     def _out(self, shape, dtype, device):
         return torch.empty(shape, dtype=dtype, device=device)

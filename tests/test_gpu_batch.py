@@ -122,3 +122,19 @@ def test_batch_rejects_bad_arguments():
     g = graphs.plain_graph(n=50, seed=1)
     with pytest.raises(hbl.HBError):
         hbl.HyperBallBatch([(g.offsets.cuda(), g.targets.cuda(), g.n, 3, 1)])
+
+
+def test_batch_autotuner_keeps_results():
+    mix = _mix(count=8, seed=9)
+    batch = hbl.HyperBallBatch(_descs(mix))
+    aps = batch.tune()
+    assert aps in (1, 2, 4, 8, 16)
+    batch.run()
+    for i, (g, b, s) in enumerate(mix):
+        solo = hbl.HyperBall(g.offsets.cuda(), g.targets.cuda(), log2m=b, seed=s, n=g.n)
+        solo.run()
+        assert torch.equal(batch.registers(i), solo.registers())
+        for x, y in zip(batch.accumulators(i), solo.accumulators()):
+            assert torch.equal(x, y)
+        solo.close()
+    batch.close()

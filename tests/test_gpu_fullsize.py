@@ -1,0 +1,205 @@
+"""Parity at the measured sizes, in the launch configuration bench.py
+times (frontier AUTO, degree relabelling, FP64 estimates, default grid).
+
+* encyclopedia-like graph (4,206,785 nodes, 97.7M arcs after dedup,
+  log2m 6): the oracle runs the whole computation on the host cores;
+  every iteration's changed set, the final registers and the iteration
+  count must be bit-exact, accumulators and centralities within 1e-9.
+* web-like graph (R-MAT scale 28, 4.26G arcs, log2m 4, FP32 estimates):
+  too large for a full oracle run, so (a) a 1M-node induced subgraph is
+  checked completely, and (b) on the full graph the counters after the
+  first two iterations are checked on sampled nodes against unions the
+  oracle's initial counters define, plus monotonicity on the sample.
+  Set HB_SKIP_WEB=1 to skip (b) on machines without ~120 GB of device
+  memory.
+
+Precision form (A8): the FP32-estimate run is compared with the FP64 run
+and the oracle; the error of each centrality (max, p99, median relative)
+is printed and held under the bound of test_gpu_parity.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1308_2144_gb300 import graphs
+from paper_1308_2144_gb300 import hyperball as hbl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1308_2144_gb300 import build
+    build.build()
+    hbl.load()
+
+
+def close(a, b, rtol=1e-9):
+    np.testing.assert_allclose(np.asarray(a), np.asarray(b), rtol=rtol, atol=0)
+
+
+def _rel_report(name, got, ref):
+    mask = ref != 0
+    rel = np.abs(got[mask] - ref[mask]) / np.abs(ref[mask])
+    exact0 = bool(np.all(got[~mask] == 0)) if (~mask).any() else True
+    return {"centrality": name, "max": float(rel.max()) if rel.size else 0.0,
+            "p99": float(np.quantile(rel, 0.99)) if rel.size else 0.0,
+            "median": float(np.median(rel)) if rel.size else 0.0, "zeros_exact": exact0}
+
+
+@pytest.fixture(scope="module")
+def enwiki():
+    g = graphs.enwiki_graph(device="cuda")
+    torch.cuda.synchronize()
+    return g
+
+
+def test_enwiki_full_size_every_iteration(orc, enwiki):
+    g = enwiki
+    off, tgt = g.numpy()
+    b, seed = 6, 42
+    ref = orc.run(off, tgt, b, seed, keep_changed=True)
+    hb = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n)   # bench.py's options
+    t = 0
+    while True:
+        k = hb.step()
+        ch, _ = hb.frontier(device="cpu")
+        assert np.array_equal(ch.numpy(), ref.changed_hist[t]), t
+        t += 1
+        if k == 0:
+            break
+    assert t == ref.steps
+    assert np.array_equal(hb.registers(device="cpu").numpy(), ref.regs)
+    s, h = hb.accumulators(device="cpu")
+    close(s.numpy(), ref.sumd)
+    close(h.numpy(), ref.harm)
+    fin = orc.finalize(b, ref.regs, ref.sumd, ref.harm)
+    cen = {k_: v.numpy() for k_, v in hb.centralities(device="cpu").items()}
+    for key in fin:
+        close(cen[key], fin[key])
+    hb.close()
+
+
+def test_enwiki_precision_form_report(orc, enwiki):
+    """FP32 estimates vs FP64 (GPU) and vs the oracle, per centrality."""
+    g = enwiki
+    off, tgt = g.numpy()
+    b, seed = 6, 42
+    ref = orc.run(off, tgt, b, seed)
+    fin = orc.finalize(b, ref.regs, ref.sumd, ref.harm)
+    h64 = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n)
+    h32 = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n, fp32=True)
+    assert h64.run() == h32.run() == ref.steps
+    assert torch.equal(h64.registers(), h32.registers())
+    c64 = {k: v.cpu().numpy() for k, v in h64.centralities().items()}
+    c32 = {k: v.cpu().numpy() for k, v in h32.centralities().items()}
+    rep = []
+    for key in ("closeness", "harmonic", "lin", "reachable"):
+        r1 = _rel_report(key, c32[key], c64[key])
+        r1["against"] = "gpu-fp64"
+        r2 = _rel_report(key, c32[key], fin[key])
+        r2["against"] = "oracle-fp64"
+        rep += [r1, r2]
+    print("\nPRECISION_REPORT enwiki " + json.dumps(rep))
+    T = ref.steps
+    reach = fin["reachable"]
+    s32, h32_ = (x.cpu().numpy() for x in h32.accumulators())
+    assert np.all(np.abs(s32 - ref.sumd) <= 2.0 ** -20 * reach * T * T + 1e-12)
+    assert np.all(np.abs(h32_ - ref.harm) <= 2.0 ** -20 * reach * (1 + math.log(T)) + 1e-12)
+    h64.close()
+    h32.close()
+
+
+@pytest.fixture(scope="module")
+def web():
+    if os.environ.get("HB_SKIP_WEB"):
+        pytest.skip("HB_SKIP_WEB set")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 120 * 2**30:
+        pytest.skip("needs ~120 GB of free device memory")
+    g = graphs.web_graph(device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return g
+
+
+def test_web_induced_subgraph_full_parity(orc, web):
+    """A seeded 1M-node induced subgraph of the web-like graph, checked
+    completely in both precision forms."""
+    g = web
+    sample = graphs.permutation(g.n, 77, 9, device="cuda")[:1_000_000]
+    sub = graphs.induced_subgraph(g, torch.sort(sample).values)
+    off, tgt = sub.numpy()
+    b, seed = 4, 42
+    ref = orc.run(off, tgt, b, seed)
+    fin = orc.finalize(b, ref.regs, ref.sumd, ref.harm)
+    for fp32 in (False, True):
+        hb = hbl.HyperBall(sub.offsets, sub.targets, log2m=b, seed=seed, n=sub.n, fp32=fp32)
+        assert hb.run() == ref.steps
+        assert np.array_equal(hb.registers(device="cpu").numpy(), ref.regs)
+        s, h = (x.numpy() for x in hb.accumulators(device="cpu"))
+        cen = {k: v.numpy() for k, v in hb.centralities(device="cpu").items()}
+        if not fp32:
+            close(s, ref.sumd)
+            close(h, ref.harm)
+            for key in fin:
+                close(cen[key], fin[key])
+        else:
+            T = ref.steps
+            reach = fin["reachable"]
+            assert np.all(np.abs(s - ref.sumd) <= 2.0 ** -20 * reach * T * T + 1e-12)
+            assert np.all(np.abs(h - ref.harm) <= 2.0 ** -20 * reach * (1 + math.log(T)) + 1e-12)
+            rep = [_rel_report(k, cen[k], fin[k]) for k in ("closeness", "harmonic", "lin", "reachable")]
+            print("\nPRECISION_REPORT web-1M-subgraph vs oracle " + json.dumps(rep))
+        hb.close()
+
+
+def test_web_full_size_sampled(orc, web):
+    """Full web-like graph, bench launch configuration (FP32 estimates):
+    after iteration 1 and 2 the counters of sampled nodes equal the union
+    the definition gives (c_1[v] = c_0[v] max c_0[w] over successors;
+    c_2[v] = c_1[v] max c_1[w]), and registers only grow."""
+    g = web
+    b, seed = 4, 42
+    hb = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n, fp32=True)
+    c0 = orc.init(g.n, b, seed)
+    rng = np.random.default_rng(123)
+    off = g.offsets.cpu().numpy()
+    tgt = g.targets.cpu().numpy()
+    deg = off[1:] - off[:-1]
+    pick = rng.choice(np.flatnonzero((deg > 0) & (deg < 2000)), size=3000, replace=False)
+    # nodes whose successors' successors are needed for the second check
+    pick2 = pick[deg[pick] < 100][:50]
+    succ2 = np.unique(np.concatenate([tgt[off[v]:off[v + 1]] for v in pick2]))
+    reg0 = hb.registers(device="cpu").numpy()
+    assert np.array_equal(reg0[pick], c0[pick])
+    assert hb.step() > 0
+    reg1 = hb.registers(device="cpu").numpy()
+    for v in pick:
+        w = tgt[off[v]:off[v + 1]]
+        expect = np.maximum(c0[v], c0[w].max(axis=0))
+        assert np.array_equal(reg1[v], expect), v
+    # c_1 of the successors of pick2, by the same definition from c_0
+    c1_needed = {}
+    for u in np.union1d(succ2, pick2):
+        w = tgt[off[u]:off[u + 1]]
+        c1_needed[u] = np.maximum(c0[u], c0[w].max(axis=0)) if w.size else c0[u].copy()
+        assert np.array_equal(reg1[u], c1_needed[u])
+    assert hb.step() > 0
+    reg2 = hb.registers(device="cpu").numpy()
+    for v in pick2:
+        w = tgt[off[v]:off[v + 1]]
+        expect = np.maximum(c1_needed[v], np.max([c1_needed[x] for x in w], axis=0))
+        assert np.array_equal(reg2[v], expect), v
+    assert np.all(reg2[pick] >= reg1[pick]) and np.all(reg1[pick] >= reg0[pick])
+    del reg0, reg1, reg2, c0
+    steps = hb.run()
+    info = hb.info()
+    assert info["converged"] == 1 and 5 <= steps <= 64
+    hb.close()

@@ -309,3 +309,30 @@ def test_fp32_estimate_form(orc, plain):
     rel = np.abs(cen["reachable"] - reach) / reach
     assert rel.max() < 2e-7
     hb.close()
+
+
+# -------------------------------------------------------------- autotuner --
+
+@pytest.mark.parametrize("b", [4, 6, 9])
+@pytest.mark.parametrize("relabel", [True, False])
+def test_every_class_sizing_gives_the_same_result(orc, b, relabel):
+    """The autotuner's choice changes only how lanes are grouped, never the
+    result: every candidate class sizing, and the tuned one, match the
+    oracle."""
+    off, tgt = _degree_boundary_graph(b, seed=11)
+    ref = orc.run(off, tgt, b, 3)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=b, seed=3, n=off.size - 1, relabel=relabel)
+    for aps in (1, 2, 4, 8, 16, None):
+        if aps is None:
+            assert hb.tune() in (1, 2, 4, 8, 16)
+        else:
+            hb.set_class_sizing(aps)
+        assert hb.run() == ref.steps
+        assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+        s, h = hb.accumulators(device="cpu")
+        close(s.numpy(), ref.sumd)
+        close(h.numpy(), ref.harm)
+        hb.reset(3)
+    with pytest.raises(hbl.HBError):
+        hb.set_class_sizing(3)
+    hb.close()
