@@ -170,6 +170,16 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
         }
     }
     const bool leader = active && tl == 0;
+    // The accumulator loads go out together, before any store of this
+    // node: the three arrays may alias as far as the compiler knows, so a
+    // load placed after a store would wait a full round trip for it.
+    double s_old = 0.0, h_old = 0.0, e_old = 0.0;
+    if (leader && ch) {
+        s_old = a.sumd[v];
+        h_old = a.harm[v];
+        e_old = F32 ? (double)static_cast<const float *>(a.ecache)[v]
+                    : static_cast<const double *>(a.ecache)[v];
+    }
     if (leader) a.changed[v] = ch ? 1 : 0;
     const unsigned lb = __ballot_sync(FULL, leader && ch);
     if (lb == 0u) return;
@@ -188,19 +198,17 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
     if (leader && ch) {
         // Sec. 5: the new layer sits at distance t+1
         if (F32) {
-            float *ec = static_cast<float *>(a.ecache);
             const float E = estimate32(V, S, C::P, a.b, a.c32, a.thr_x, a.lc32);
-            const float d = __fsub_rn(E, ec[v]);
-            ec[v] = E;
-            a.sumd[v] = __fma_rn((double)(t + 1), (double)d, a.sumd[v]);   // exact product
-            a.harm[v] = __dadd_rn(a.harm[v], (double)__fmul_rn(d, rdist32));
+            const float d = __fsub_rn(E, (float)e_old);
+            static_cast<float *>(a.ecache)[v] = E;
+            a.sumd[v] = __fma_rn((double)(t + 1), (double)d, s_old);   // exact product
+            a.harm[v] = __dadd_rn(h_old, (double)__fmul_rn(d, rdist32));
         } else {
-            double *ec = static_cast<double *>(a.ecache);
             const double E = estimate64(V, S, C::P, a.b, a.c64, a.thr_x, a.lc64);
-            const double d = __dsub_rn(E, ec[v]);
-            ec[v] = E;
-            a.sumd[v] = __fma_rn((double)(t + 1), d, a.sumd[v]);
-            a.harm[v] = __fma_rn(d, rdist64, a.harm[v]);
+            const double d = __dsub_rn(E, e_old);
+            static_cast<double *>(a.ecache)[v] = E;
+            a.sumd[v] = __fma_rn((double)(t + 1), d, s_old);
+            a.harm[v] = __fma_rn(d, rdist64, h_old);
         }
     }
     if (lane == 0) atomicAdd(s_changed, (unsigned long long)__popc(lb));
