@@ -5,6 +5,9 @@ One bench step is one whole HyperBall computation on the resident graph:
 re-initialise the counters (Algorithm 2, first loop), iterate to the
 fixpoint (every iteration: frontier, gather + union, estimator and
 accumulators), and finalise the four centralities into device buffers.
+Setup (outside the timed region, like the degree relabelling): the
+light-class sizing of the gather kernel, chosen by the library's
+autotuner unless --aps fixes it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -272,6 +275,10 @@ def run_ours(args, world, rank, local):
     opts = dict(log2m=log2m, seed=wl["seed"], n=n, fp32=fp32, frontier=args.frontier,
                 stream=stream, profile=True, relabel=not args.no_relabel)
     hb = hbl.HyperBall(g.offsets, g.targets, **opts)
+    # class sizing (arcs per slot): part of setup, like the relabelling
+    aps = hb.tune() if args.aps == "tune" else int(args.aps)
+    if args.aps != "tune":
+        hb.set_class_sizing(aps)
     cen = {k: torch.empty(n, dtype=torch.float64, device="cuda")
            for k in ("closeness", "harmonic", "lin", "reachable")}
 
@@ -324,7 +331,7 @@ def run_ours(args, world, rank, local):
     # back to pinned host memory, handle created and destroyed every step
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, g, opts, wl, world, cen)
+        e2e = run_e2e(args, g, opts, wl, world, cen, aps)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(g.numpy(), log2m, wl["seed"])
@@ -335,7 +342,8 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": n, "m": m, "log2m": log2m,
                        "estimate": "fp32" if fp32 else "fp64", "accumulators": "fp64",
-                       "frontier": args.frontier,
+                       "frontier": args.frontier, "arcs_per_slot": aps,
+                       "arcs_per_slot_source": "autotuner" if args.aps == "tune" else "fixed",
                        "iterations_to_fixpoint": steps_list,
                        "arc_updates_per_step": arcs / args.steps,
                        "time_to_fixpoint_ms": ms_max / args.steps,
@@ -371,10 +379,11 @@ def trace_run(hb, seed, log2m):
             break
 
 
-def run_e2e(args, g, opts, wl, world, cen):
+def run_e2e(args, g, opts, wl, world, cen, aps):
     """Same metric through the public API from host memory: pinned host CSR
-    in, handle created (upload + setup), run to the fixpoint, centralities
-    back to pinned host memory, handle destroyed, every step."""
+    in, handle created (upload + setup) with the class sizing chosen above,
+    run to the fixpoint, centralities back to pinned host memory, handle
+    destroyed, every step."""
     from paper_1308_2144_gb300 import hyperball as hbl
     n = g.n
     off_h = g.offsets.cpu().pin_memory()
@@ -389,6 +398,7 @@ def run_e2e(args, g, opts, wl, world, cen):
     t0 = time.perf_counter()
     for k in range(e2e_steps):
         h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=wl["seed"] + 100 + k))
+        h.set_class_sizing(aps)
         h.run()
         hbl.hb_get_centralities(h._h, outs_h["closeness"], outs_h["harmonic"], outs_h["lin"],
                                 outs_h["reachable"])
@@ -416,6 +426,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-relabel", action="store_true", help="keep the generator's node order")
     ap.add_argument("--trace", action="store_true", help="per-iteration diagnostics on stderr")
+    ap.add_argument("--aps", choices=["1", "2", "4", "8", "16", "32", "64", "128", "tune"], default="tune",
+                    help="light-class sizing (arcs per slot), or 'tune' for the autotuner")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

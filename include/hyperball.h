@@ -169,13 +169,15 @@ hb_status hb_reset(hb_graph *g, uint64_t seed);
 
 /* Autotuner: choose how many lanes each light degree class of the gather
  * kernel gets (the class sizing: about *arcs_per_slot arcs per lane slot;
- * candidates 1, 2, 4, 8, 16) by timing the first two iterations with each
- * candidate, then re-initialise the counters with the handle's seed.
+ * candidates the powers of two from 1 to 128) by timing the first two
+ * iterations with each candidate, then re-initialise the counters with
+ * the handle's seed.
  * Results never depend on the choice.  *arcs_per_slot (may be NULL)
  * receives the choice. */
 hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
 
-/* Set the class sizing directly (1, 2, 4, 8 or 16) and re-initialise. */
+/* Set the class sizing directly (a power of two from 1 to 128) and
+ * re-initialise. */
 hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot);
 
 /* Checkpoint: write t, counters, last frontier and accumulators (and the

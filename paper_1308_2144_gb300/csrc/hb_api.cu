@@ -680,7 +680,7 @@ hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot) {
     if (st != HB_OK) return st;
     bool ok = false;
     for (int c : kTuneAps) ok |= c == arcs_per_slot;
-    if (!ok) return fail(HB_ERR_INVALID, "arcs_per_slot must be 1, 2, 4, 8 or 16");
+    if (!ok) return fail(HB_ERR_INVALID, "arcs_per_slot must be a power of two from 1 to 128");
     st = retune(g, arcs_per_slot);
     return st == HB_OK ? init_state(g, g->seed) : st;
 }

@@ -65,7 +65,7 @@ void drop_run_state(hb_graph *g);
 // Re-size the light degree classes of a handle (autotuner).
 hb_status retune(hb_graph *g, int aps);
 // Candidate class sizings the autotuners try.
-constexpr int kTuneAps[] = {1, 2, 4, 8, 16};
+constexpr int kTuneAps[] = {1, 2, 4, 8, 16, 32, 64, 128};
 
 }  // namespace hb
 

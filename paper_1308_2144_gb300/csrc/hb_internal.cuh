@@ -11,7 +11,7 @@ constexpr int kWarp = 32;
 constexpr int kMaxLog2m = 12;
 constexpr int kMinLog2m = 4;
 constexpr int kSegs = 7;          // segment 0: heavy nodes; 1..6: light classes
-constexpr int kArcsPerSlot = 4;   // default class sizing: about this many arcs per lane slot
+constexpr int kArcsPerSlot = 16;  // default class sizing: about this many arcs per lane slot
 constexpr int kStepThreads = 256;
 constexpr int kBigRdeg = 1024;    // changed nodes with more predecessors are pushed grid-wide
 
@@ -41,7 +41,7 @@ struct Layout {
     int64_t lo[kSegs], hi[kSegs];
 };
 
-// aps (arcs per slot, a power of two from 1 to 16) sizes the light degree
+// aps (arcs per slot, a power of two from 1 to 128) sizes the light degree
 // classes: a node of degree d gets the smallest team whose slots each take
 // at most aps arcs.  The autotuner picks it per graph.
 inline Layout make_layout(int log2m, int aps = kArcsPerSlot) {

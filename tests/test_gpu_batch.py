@@ -128,7 +128,7 @@ def test_batch_autotuner_keeps_results():
     mix = _mix(count=8, seed=9)
     batch = hbl.HyperBallBatch(_descs(mix))
     aps = batch.tune()
-    assert aps in (1, 2, 4, 8, 16)
+    assert aps in (1, 2, 4, 8, 16, 32, 64, 128)
     batch.run()
     for i, (g, b, s) in enumerate(mix):
         solo = hbl.HyperBall(g.offsets.cuda(), g.targets.cuda(), log2m=b, seed=s, n=g.n)

@@ -104,15 +104,20 @@ def test_frontier_policies_and_layouts(orc, frontier, relabel):
 
 
 def _degree_boundary_graph(b, seed=3):
-    """Nodes whose degrees sit on every class boundary of the step kernel:
-    0, 1, 4, 5, 8, 9, ..., the heavy threshold +-1, several heavy chunks."""
+    """Nodes whose degrees sit on every class boundary of the step kernel
+    for every class sizing: 0, 1, 2^k - 1, 2^k, 2^k + 1 up to the heavy
+    threshold, the heavy threshold +-1, several heavy chunks."""
     p = 1 << b
     L = min(p // 16, 32)
     smax = 32 // L
     chunk = 64 * smax
     heavy = 2 * chunk
-    degs = [0, 1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129,
-            heavy - 1, heavy, heavy + 1, 3 * chunk + 5, 7 * chunk]
+    # light class bounds are aps * 2^k (aps and 2^k powers of two)
+    degs = [0, 3, heavy - 1, heavy, heavy + 1, 3 * chunk + 5, 7 * chunk]
+    k = 1
+    while k < heavy:
+        degs += [k - 1, k, k + 1]
+        k *= 2
     degs = sorted(set(d for d in degs if d >= 0))
     n = max(4 * max(degs), 5000)
     rng = np.random.default_rng(seed)
@@ -322,9 +327,9 @@ def test_every_class_sizing_gives_the_same_result(orc, b, relabel):
     off, tgt = _degree_boundary_graph(b, seed=11)
     ref = orc.run(off, tgt, b, 3)
     hb = hbl.HyperBall(*to_dev(off, tgt), log2m=b, seed=3, n=off.size - 1, relabel=relabel)
-    for aps in (1, 2, 4, 8, 16, None):
+    for aps in (1, 2, 4, 8, 16, 32, 64, 128, None):
         if aps is None:
-            assert hb.tune() in (1, 2, 4, 8, 16)
+            assert hb.tune() in (1, 2, 4, 8, 16, 32, 64, 128)
         else:
             hb.set_class_sizing(aps)
         assert hb.run() == ref.steps
