@@ -169,9 +169,9 @@ hb_status hb_reset(hb_graph *g, uint64_t seed);
 
 /* Autotuner: choose how many lanes each light degree class of the gather
  * kernel gets (the class sizing: about *arcs_per_slot arcs per lane slot;
- * candidates the powers of two from 1 to 128) by timing the first two
- * iterations with each candidate, then re-initialise the counters with
- * the handle's seed.
+ * candidates the powers of two from 1 to 128) by timing the first eight
+ * iterations (or all, if the fixpoint comes sooner) with each candidate,
+ * then re-initialise the counters with the handle's seed.
  * Results never depend on the choice.  *arcs_per_slot (may be NULL)
  * receives the choice. */
 hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);

@@ -698,9 +698,8 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
         st = retune(g, aps);
         if (st == HB_OK) st = init_state(g, seed);
         if (st != HB_OK) break;
-        // time the first two iterations (every node recomputed and changing)
         cudaEventRecord(e0, g->s);
-        for (int i = 0; i < 2 && st == HB_OK; ++i) st = hb_step(g, nullptr);
+        for (int i = 0; i < kTuneIters && st == HB_OK && !g->converged; ++i) st = hb_step(g, nullptr);
         cudaEventRecord(e1, g->s);
         float ms = 0.f;
         if (st == HB_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&

@@ -672,7 +672,7 @@ hb_status hb_batch_tune(hb_batch *b, int32_t *arcs_per_slot) {
         st = apply(aps);
         if (st != HB_OK) break;
         cudaEventRecord(e0, b->s);
-        for (int i = 0; i < 2; ++i) cudaGraphLaunch(b->step_exec, b->s);
+        for (int i = 0; i < kTuneIters; ++i) cudaGraphLaunch(b->step_exec, b->s);
         cudaEventRecord(e1, b->s);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&

@@ -66,6 +66,9 @@ void drop_run_state(hb_graph *g);
 hb_status retune(hb_graph *g, int aps);
 // Candidate class sizings the autotuners try.
 constexpr int kTuneAps[] = {1, 2, 4, 8, 16, 32, 64, 128};
+// The autotuner times each candidate over the first iterations (most of a
+// run's work: the dense ones), up to the fixpoint.
+constexpr int kTuneIters = 8;
 
 }  // namespace hb
 

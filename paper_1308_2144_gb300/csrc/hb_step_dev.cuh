@@ -13,7 +13,7 @@
 #define HB_UNROLL 8
 #endif
 #ifndef HB_MIN_BLOCKS
-#define HB_MIN_BLOCKS 6
+#define HB_MIN_BLOCKS 5
 #endif
 // L2 eviction hints on counter gathers, and streaming stores for data the
 // next iteration reads only after it has left L2.
