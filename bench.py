@@ -296,6 +296,7 @@ def run_ours(args, world, rank, local):
         trace_run(hb, wl["seed"], log2m)
     launches0 = hb.info()["launches"]
     arcs, kms, kbytes, klaunch, steps_list = 0, 0.0, 0.0, 0, []
+    pms, pbytes, plaunch = 0.0, 0.0, 0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     barrier(world)
@@ -308,6 +309,9 @@ def run_ours(args, world, rank, local):
             kms += info["kernel_ms"]
             kbytes += info["kernel_bytes"]
             klaunch += info["kernel_launches"]
+            pms += info["push_ms"]
+            pbytes += info["push_bytes"]
+            plaunch += info["push_launches"]
             steps_list.append(steps)
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -325,7 +329,11 @@ def run_ours(args, world, rank, local):
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s", "kernel": "step_kernel (gather + union + estimator)",
                 "bytes_per_launch": kbytes / klaunch if klaunch else 0.0,
-                "ms_per_launch": kms / klaunch if klaunch else 0.0}
+                "ms_per_launch": kms / klaunch if klaunch else 0.0,
+                # frontier iterations done by the pushed union (separate kernels)
+                "pushed_iterations": {"per_step": plaunch / args.steps,
+                                      "ms_per_iteration": pms / plaunch if plaunch else 0.0,
+                                      "GBps": pbytes / pms / 1e6 if pms else 0.0}}
 
     # end to end through the public API: host CSR in pinned memory, results
     # back to pinned host memory, handle created and destroyed every step
@@ -368,9 +376,9 @@ def trace_run(hb, seed, log2m):
     while True:
         k = hb.step()
         info = hb.info()
-        ms = info["kernel_ms"] - prev_ms
-        by = info["kernel_bytes"] - prev_b
-        prev_ms, prev_b = info["kernel_ms"], info["kernel_bytes"]
+        ms = info["kernel_ms"] + info["push_ms"] - prev_ms
+        by = info["kernel_bytes"] + info["push_bytes"] - prev_b
+        prev_ms, prev_b = info["kernel_ms"] + info["push_ms"], info["kernel_bytes"] + info["push_bytes"]
         print(json.dumps({"t": info["t"] - 1, "sparse": info["last_sparse"], "nodes": info["last_nodes"],
                           "arcs": info["last_arcs"], "changed": k, "kernel_ms": round(ms, 4),
                           "GBps": round(by / ms / 1e6, 1) if ms > 0 else None}), file=sys.stderr,

@@ -61,6 +61,9 @@ typedef enum {
 #define HB_FP32_ESTIMATE      0x4u  /* precision form: FP32 estimates and deltas, FP64 accumulators */
 #define HB_NO_RELABEL         0x8u  /* keep the caller's node order on the device (no degree sort) */
 #define HB_PROFILE            0x10u /* time the gather kernel of every iteration with CUDA events */
+#define HB_PULL_GATHER        0x20u /* frontier iterations gather every successor of the nodes they
+                                       recompute, instead of pushing last iteration's changed
+                                       counters along the reverse CSR (results are the same) */
 
 /* hb_options.frontier: how the nodes to recompute are chosen each step
  * (Sec. 5 / 5.1 modification tracking).  Results never depend on it. */
@@ -94,6 +97,9 @@ typedef struct {
     int64_t kernel_launches;     /* HB_PROFILE: gather-kernel launches timed since the last reset */
     double kernel_ms;            /* HB_PROFILE: their summed duration (CUDA events, same stream) */
     double kernel_bytes;         /* HB_PROFILE: their summed algorithmic bytes (see below) */
+    int64_t push_launches;       /* HB_PROFILE: pushed frontier iterations timed since the last reset */
+    double push_ms;              /* HB_PROFILE: their summed duration (push + per-node tail) */
+    double push_bytes;           /* HB_PROFILE: their summed algorithmic bytes (see below) */
 } hb_info;
 
 /* Algorithmic bytes of one gather-kernel launch, counted from the nodes it
@@ -102,7 +108,16 @@ typedef struct {
  *   + N * (8 + 2p + 1)            offset, own counter read, counter write, flag
  *   + N * 4                       list entry (frontier iterations only)
  *   + C * (4 + 32 + 2e)           list append, sumd/harm read+write, cached
- *                                 estimate read+write (e = 8, or 4 in FP32) */
+ *                                 estimate read+write (e = 8, or 4 in FP32)
+ * and of one pushed frontier iteration, from the reverse arcs of the C'
+ * nodes changed in the iteration before (P), the nodes recomputed (K) and
+ * the nodes that changed (C):
+ *     P * (4 + 2p)                predecessor index, its counter read+write
+ *   + C' * (8 + p)                reverse offsets, the pushed counter
+ *   + K * (5 + 3p)                list entry, pushed union, own counter,
+ *                                 counter write, flag
+ *   + C * (4 + 32 + 2e)           as above
+ * In a pushed iteration last_arcs (the arc-updates) counts the P arcs. */
 
 /* Fill *opt with the defaults: flags 0, HB_FRONTIER_AUTO, max_steps 1<<20,
  * stream NULL. */
@@ -171,7 +186,8 @@ hb_status hb_reset(hb_graph *g, uint64_t seed);
  * kernel gets (the class sizing: about *arcs_per_slot arcs per lane slot;
  * candidates the powers of two from 1 to 128) by timing the first eight
  * iterations (or all, if the fixpoint comes sooner) with each candidate,
- * then re-initialise the counters with the handle's seed.
+ * twice (ascending, then descending order; the faster time counts), then
+ * re-initialise the counters with the handle's seed.
  * Results never depend on the choice.  *arcs_per_slot (may be NULL)
  * receives the choice. */
 hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);

@@ -109,6 +109,7 @@ hb_status setup_shared(hb_graph *g) {
     a.roff = g->roff;
     a.rtgt = g->rtgt;
     a.has_reverse = want_reverse ? 1 : 0;
+    g->push_union = want_reverse && (g->opt.flags & HB_PULL_GATHER) == 0;
     a.plan_dense = M.alloc<Plan>(1);
     a.owner_dense = M.alloc<int32_t>(g->heavy_total);
     a.cstart_dense = M.alloc<int64_t>(g->seg_count[0] + 1);
@@ -330,6 +331,8 @@ hb_status init_state(hb_graph *g, uint64_t seed) {
     g->launches += g->n > 0 ? 2 : 1;
     g->kernel_launches = 0;
     g->kernel_ms = g->kernel_bytes = 0.0;
+    g->push_launches = 0;
+    g->push_ms = g->push_bytes = 0.0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
     if (e != cudaSuccess) return cuda_fail(e, "init");
     g->t = 0;
@@ -369,9 +372,12 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     g->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
     g->relabel = (o.flags & HB_NO_RELABEL) == 0;
     g->profile = (o.flags & HB_PROFILE) != 0;
-    if (g->profile && (cudaEventCreate(&g->ev[0]) != cudaSuccess || cudaEventCreate(&g->ev[1]) != cudaSuccess)) {
-        delete g;
-        return fail(HB_ERR_CUDA, "cannot create profiling events");
+    if (g->profile) {
+        for (cudaEvent_t &x : g->ev)
+            if (cudaEventCreate(&x) != cudaSuccess) {
+                delete g;
+                return fail(HB_ERR_CUDA, "cannot create profiling events");
+            }
     }
     cudaStream_t s = g->s;
     DevMem &M = g->mem;
@@ -523,8 +529,9 @@ hb_status hb_create32(const int32_t *offsets, const int32_t *targets, int64_t n,
 hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
-    cudaError_t e = launch_iteration(g->a, g->y, g->fp32, g->step_grid, g->s,
-                                     g->profile ? g->ev[0] : nullptr, g->profile ? g->ev[1] : nullptr,
+    StepArgs a = g->a;
+    a.push_union = g->push_union ? 1 : 0;
+    cudaError_t e = launch_iteration(a, g->y, g->fp32, g->step_grid, g->s, g->profile ? g->ev : nullptr,
                                      &g->launches);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->s);
@@ -534,6 +541,10 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
         return cuda_fail(e, "step");
     }
     const Counters &c = *g->ctr_host;
+    if (c.err) {
+        g->broken = true;
+        return fail(HB_ERR_STATE, "a device-side check failed during the step");
+    }
     g->t = c.steps_done;
     g->last_changed = (int64_t)c.n_changed;
     g->last_sparse = c.mode;
@@ -548,7 +559,21 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     }
     g->total_arcs += g->last_arcs;
     if (c.n_changed == 0) g->converged = true;
-    if (g->profile) {
+    const bool pushed = c.mode == 1 && g->push_union;
+    if (g->profile && pushed) {
+        // pushed union: P arcs into the C' nodes changed last time, K nodes
+        // recomputed, C changed
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->ev[2], g->ev[3]) == cudaSuccess) {
+            const double p = (double)(1 << g->b);
+            const double esz = g->fp32 ? 4.0 : 8.0;
+            g->push_ms += ms;
+            g->push_launches += 1;
+            g->push_bytes += (double)c.arcs * (4.0 + 2.0 * p) + (double)c.prev_list_len * (8.0 + p) +
+                             (double)g->last_nodes * (5.0 + 3.0 * p) +
+                             (double)c.n_changed * (4.0 + 32.0 + 2.0 * esz);
+        }
+    } else if (g->profile) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]) == cudaSuccess) {
             const double p = (double)(1 << g->b);
@@ -672,6 +697,9 @@ hb_status hb_get_info(hb_graph *g, hb_info *info) {
     info->kernel_launches = g->kernel_launches;
     info->kernel_ms = g->kernel_ms;
     info->kernel_bytes = g->kernel_bytes;
+    info->push_launches = g->push_launches;
+    info->push_ms = g->push_ms;
+    info->push_bytes = g->push_bytes;
     return HB_OK;
 }
 
@@ -692,10 +720,15 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(HB_ERR_CUDA, "tuning events");
-    int best = g->y.aps;
-    float best_ms = 1e30f;
-    for (int aps : kTuneAps) {
-        st = retune(g, aps);
+    // every candidate twice, in ascending then descending order, keeping
+    // its faster time: a drift of the clocks during tuning then favours no
+    // end of the list
+    constexpr int nc = sizeof(kTuneAps) / sizeof(kTuneAps[0]);
+    float cand_ms[nc];
+    for (float &x : cand_ms) x = 1e30f;
+    for (int pass = 0; pass < 2 * nc && st == HB_OK; ++pass) {
+        const int ci = pass < nc ? pass : 2 * nc - 1 - pass;
+        st = retune(g, kTuneAps[ci]);
         if (st == HB_OK) st = init_state(g, seed);
         if (st != HB_OK) break;
         cudaEventRecord(e0, g->s);
@@ -703,11 +736,16 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
         cudaEventRecord(e1, g->s);
         float ms = 0.f;
         if (st == HB_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-            ms < best_ms) {
-            best_ms = ms;
-            best = aps;
-        }
+            ms < cand_ms[ci])
+            cand_ms[ci] = ms;
     }
+    int best = g->y.aps;
+    float best_ms = 1e30f;
+    for (int ci = 0; ci < nc; ++ci)
+        if (cand_ms[ci] < best_ms) {
+            best_ms = cand_ms[ci];
+            best = kTuneAps[ci];
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != HB_OK) return st;

@@ -665,22 +665,30 @@ hb_status hb_batch_tune(hb_batch *b, int32_t *arcs_per_slot) {
         if (e != cudaSuccess) return bfail(HB_ERR_CUDA, "batch tune upload");
         return reset_ctl(b);
     };
-    int best = kArcsPerSlot;
-    float best_ms = 1e30f;
+    // as hb_tune: every candidate twice, ascending then descending
+    constexpr int nc = sizeof(kTuneAps) / sizeof(kTuneAps[0]);
+    float cand_ms[nc];
+    for (float &x : cand_ms) x = 1e30f;
     hb_status st = HB_OK;
-    for (int aps : kTuneAps) {
-        st = apply(aps);
+    for (int pass = 0; pass < 2 * nc; ++pass) {
+        const int ci = pass < nc ? pass : 2 * nc - 1 - pass;
+        st = apply(kTuneAps[ci]);
         if (st != HB_OK) break;
         cudaEventRecord(e0, b->s);
         for (int i = 0; i < kTuneIters; ++i) cudaGraphLaunch(b->step_exec, b->s);
         cudaEventRecord(e1, b->s);
         float ms = 0.f;
         if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-            ms < best_ms) {
-            best_ms = ms;
-            best = aps;
-        }
+            ms < cand_ms[ci])
+            cand_ms[ci] = ms;
     }
+    int best = kArcsPerSlot;
+    float best_ms = 1e30f;
+    for (int ci = 0; ci < nc; ++ci)
+        if (cand_ms[ci] < best_ms) {
+            best_ms = cand_ms[ci];
+            best = kTuneAps[ci];
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st == HB_OK) st = apply(best);

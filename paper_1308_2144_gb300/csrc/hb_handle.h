@@ -82,6 +82,7 @@ struct hb_graph {
     hb_options opt{};
     cudaStream_t s = nullptr;
     bool fp32 = false, relabel = true, broken = false;
+    bool push_union = false;   // frontier iterations push changed counters (reverse CSR)
     int step_grid = 0;
     DevMem mem;
     int64_t *off = nullptr;
@@ -102,15 +103,17 @@ struct hb_graph {
     int32_t last_sparse = 0;
     int launches = 0;
     bool profile = false;
-    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int64_t kernel_launches = 0;
     double kernel_ms = 0.0, kernel_bytes = 0.0;
+    int64_t push_launches = 0;
+    double push_ms = 0.0, push_bytes = 0.0;
 
     bool own_ctr_host = true;
 
     ~hb_graph() {
-        if (ev[0]) cudaEventDestroy(ev[0]);
-        if (ev[1]) cudaEventDestroy(ev[1]);
+        for (cudaEvent_t &x : ev)
+            if (x) cudaEventDestroy(x);
         if (ctr_host && own_ctr_host) cudaFreeHost(ctr_host);
         mem.free_all();
     }

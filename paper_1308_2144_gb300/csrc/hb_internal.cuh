@@ -145,6 +145,7 @@ struct StepArgs {
     int32_t has_reverse;          // roff/rtgt present
     int32_t hot_nodes;            // counters of nodes below this id are kept in L2
     int32_t aps;                  // class sizing (arcs per slot) of the layout
+    int32_t push_union;           // frontier iterations push changed counters along reverse arcs
     double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
 };
 
@@ -160,6 +161,25 @@ __device__ __forceinline__ uint32_t bmax4(uint32_t a, uint32_t b) {
     uint32_t m;
     asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(m) : "r"(t));
     return (a & m) | (b & ~m);
+}
+
+// *addr = bmax4(*addr, v) atomically.  Every byte of *addr only grows, so
+// each failed compare-and-swap means another thread raised a byte: the
+// loop ends after at most 4 x 64 retries; the bound below only guards
+// against a broken invariant (it sets err and gives up).
+__device__ __forceinline__ void atomic_bmax4(uint32_t *addr, uint32_t v, unsigned long long *err) {
+    uint32_t old = __ldcg(addr);
+    uint32_t nv = bmax4(old, v);
+    for (int guard = 0; nv != old; ++guard) {
+        const uint32_t seen = atomicCAS(addr, old, nv);
+        if (seen == old) return;
+        old = seen;
+        nv = bmax4(old, v);
+        if (guard == 1024) {
+            atomicOr(err, 2ull);
+            return;
+        }
+    }
 }
 
 __device__ __forceinline__ uint4 vmax16(uint4 a, uint4 b) {
@@ -359,9 +379,11 @@ cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, b
 cudaError_t launch_dense_plan(const StepArgs &a, const Layout &y, const int64_t *seg_count,
                               Plan *plan, int32_t *owner, int64_t *cstart, cudaStream_t s);
 // One iteration: the whole launch sequence, sizes read on the device.
+// With ev (four events): ev[0], ev[1] around the gather kernel, ev[2],
+// ev[3] around the pushed union (when a.push_union).
 cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int step_grid,
-                             cudaStream_t s, cudaEvent_t ev_before = nullptr,
-                             cudaEvent_t ev_after = nullptr, int *launches = nullptr);
+                             cudaStream_t s, const cudaEvent_t *ev = nullptr,
+                             int *launches = nullptr);
 int step_blocks_per_sm(int log2m, bool fp32);
 // The gather kernel alone (mode and t already set in the counters).
 cudaError_t launch_step_kernel(const StepArgs &a, int log2m, bool fp32, int grid, cudaStream_t s);

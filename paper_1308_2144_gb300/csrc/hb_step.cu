@@ -162,6 +162,7 @@ __global__ void copy_forward_kernel(StepArgs a) {
 // block scan, then the chunk -> node map), then each light class packs
 // 2^j nodes per warp item.
 __global__ void plan_kernel(StepArgs a, PlanParams pp, Plan *plan, int32_t *owner, int64_t *cstart) {
+    if (!pp.dense && a.push_union) return;   // pushed frontier iterations need no gather plan
     plan_block(a, pp, plan, owner, cstart);
 }
 
@@ -195,6 +196,7 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
     uint8_t *nxt = a.regs[(t + 1) & 1];
     int32_t *clist = a.clist[t & 1];
     int32_t *biglist = a.biglist[t & 1];
+    if (sparse && a.push_union) return;   // the pushed union does this iteration
     const int64_t items = pl->items;
     const int64_t hch = pl->heavy_chunks;
     int64_t ib[C::NLIGHT + 1], cnt[C::NLIGHT];
@@ -232,6 +234,147 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
                                    clist, biglist, sparse, &s_changed, rdist64, rdist32, s_pow2,
                                    prefetch);
         }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_changed) atomicAdd(&a.ctr->n_changed, s_changed);
+}
+
+// ------------------------------------------------ pushed frontier union --
+
+// Frontier iteration with the reverse CSR: the counter of every node that
+// changed in the last iteration is folded into each predecessor's write
+// buffer counter, and the predecessor is marked for recomputation (the
+// frontier of Sec. 5.1, as mark_push does).  The work is the set of pairs
+// (changed node w, predecessor v): a warp takes 32 changed nodes at a time
+// and spreads all their pairs over teams of G lanes (a scan of their
+// predecessor counts, then a binary search over it by shuffles), so nodes
+// with few predecessors leave no lane idle; nodes with many predecessors
+// are done by the whole grid.  Each team folds one pair, G 16-byte chunks
+// at a time.
+__global__ void __launch_bounds__(kStepThreads, 4) push_union_kernel(StepArgs a) {
+    const Counters *c = a.ctr;
+    if (c->mode != 1 || !a.push_union) return;
+    const int t = c->t;
+    const uint4 *cur4 = reinterpret_cast<const uint4 *>(a.regs[t & 1]);
+    uint4 *nxt4 = reinterpret_cast<uint4 *>(a.regs[(t + 1) & 1]);
+    const int32_t *prev = a.clist[(t + 1) & 1];
+    const int32_t *bigp = a.biglist[(t + 1) & 1];
+    const int64_t np = (int64_t)c->prev_list_len, nb = (int64_t)c->prev_big;
+    const int logCH = a.b - 4;
+    const int logG = logCH < 5 ? logCH : 5;
+    const int lane = threadIdx.x & 31;
+    const int team = lane >> logG;
+    const int tl = lane & ((1 << logG) - 1);
+    const int ppw = 32 >> logG;   // pairs per warp pass
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * 32; base < np; base += nw * 32) {
+        const int64_t i = base + lane;
+        int32_t w = 0;
+        int64_t r0 = 0;
+        int cnt = 0;   // predecessors, <= kBigRdeg
+        if (i < np) {
+            w = prev[i];
+            r0 = a.roff[w];
+            const int64_t rd = a.roff[w + 1] - r0;
+            if (rd <= kBigRdeg) cnt = (int)rd;
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - cnt;
+        for (int eb = 0; eb < total; eb += ppw) {
+            const int e = eb + team;
+            // owner: the first lane whose inclusive count exceeds e
+            int q = 0;
+#pragma unroll
+            for (int s = 16; s; s >>= 1)
+                if (__shfl_sync(FULL, incl, q + s - 1) <= e) q += s;
+            const int32_t ow = __shfl_sync(FULL, w, q);
+            const int64_t or0 = __shfl_sync(FULL, r0, q);
+            const int oex = __shfl_sync(FULL, excl, q);
+            int32_t v = -1;
+            if (e < total) {
+                v = a.rtgt[or0 + (e - oex)];
+                push_pair(a, cur4, nxt4, ow, v, logCH, tl, 1 << logG);
+            }
+            mark_append(a, tl == 0 ? v : -1, lane);
+        }
+    }
+    for (int64_t q = 0; q < nb; ++q) {
+        const int32_t w = bigp[q];
+        const int64_t r0 = a.roff[w], rd = a.roff[w + 1] - r0;
+        for (int64_t pb = gw * ppw; pb < rd; pb += nw * ppw) {
+            const int64_t e = pb + team;
+            int32_t v = -1;
+            if (e < rd) {
+                v = a.rtgt[r0 + e];
+                push_pair(a, cur4, nxt4, w, v, logCH, tl, 1 << logG);
+            }
+            mark_append(a, tl == 0 ? v : -1, lane);
+        }
+    }
+}
+
+// The per-node tail of a pushed frontier iteration: every node marked for
+// recomputation (the sparse list, by degree segment) takes its pushed
+// union from the write buffer and goes through the same tail as a gathered
+// node (own counter folded in, changed flag, estimator, accumulators,
+// changed list).  One team of L lanes per node.
+template <int LOG2P, bool F32>
+__global__ void __launch_bounds__(kStepThreads) union_tail_kernel(StepArgs a) {
+    using C = Cfg<LOG2P>;
+    const Counters *ctr = a.ctr;
+    if (ctr->mode != 1 || !a.push_union) return;
+    const int t = ctr->t;
+    const uint8_t *cur = a.regs[t & 1];
+    uint8_t *nxt = a.regs[(t + 1) & 1];
+    int32_t *clist = a.clist[t & 1];
+    int32_t *biglist = a.biglist[t & 1];
+    int64_t start[kSegs + 1];
+    start[0] = 0;
+#pragma unroll
+    for (int s = 0; s < kSegs; ++s) start[s + 1] = start[s] + (int64_t)ctr->fill[s];
+    const int64_t total = start[kSegs];
+    __shared__ unsigned long long s_changed;
+    __shared__ unsigned long long s_pow2[64];
+    const double rdist64 = 1.0 / (double)(t + 1);
+    const float rdist32 = 1.0f / (float)(t + 1);
+    if (threadIdx.x == 0) s_changed = 0;
+    if (threadIdx.x < 64) {
+        const int M = threadIdx.x, sh = 64 - a.b;
+        s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int team = lane >> C::LOGL;
+    const int tl = lane & (C::L - 1);
+    constexpr int NPW = 32 / C::L;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * NPW; base < total; base += nw * NPW) {
+        const int64_t i = base + team;
+        const bool active = i < total;
+        int64_t v = 0;
+        uint4 acc[C::CPL];
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
+        if (active) {
+            int64_t pos = a.seg_begin[0] + i;
+#pragma unroll
+            for (int s = 1; s < kSegs; ++s)
+                if (i >= start[s]) pos = a.seg_begin[s] + (i - start[s]);
+            v = a.slist[pos];
+            const uint4 *row = reinterpret_cast<const uint4 *>(nxt + v * C::P) + tl;
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c) acc[c] = __ldcg(row + c * C::L);
+        }
+        node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, tl, tl, team, C::LOGL, clist, biglist,
+                                  true, &s_changed, rdist64, rdist32, s_pow2);
     }
     __syncthreads();
     if (threadIdx.x == 0 && s_changed) atomicAdd(&a.ctr->n_changed, s_changed);
@@ -324,6 +467,18 @@ cudaError_t launch_step_t(const StepArgs &a, int log2m, int grid, cudaStream_t s
 }
 
 template <bool F32>
+cudaError_t launch_union_tail_t(const StepArgs &a, int log2m, int grid, cudaStream_t s) {
+    switch (log2m) {
+#define HB_CASE(B) case B: union_tail_kernel<B, F32><<<grid, kStepThreads, 0, s>>>(a); break;
+        HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+        HB_CASE(12)
+#undef HB_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <bool F32>
 const void *step_kernel_ptr(int log2m) {
     switch (log2m) {
 #define HB_CASE(B) case B: return reinterpret_cast<const void *>(&step_kernel<B, F32>);
@@ -391,8 +546,7 @@ cudaError_t launch_dense_plan(const StepArgs &a, const Layout &y, const int64_t 
 }
 
 cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int step_grid,
-                             cudaStream_t s, cudaEvent_t ev_before, cudaEvent_t ev_after,
-                             int *launches) {
+                             cudaStream_t s, const cudaEvent_t *ev, int *launches) {
     int k = 0;
     step_begin_kernel<<<1, 1, 0, s>>>(a);
     ++k;
@@ -401,8 +555,13 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
         clear_bits_kernel<<<grid_for(words, 256), 256, 0, s>>>(a, words);
         if (a.frontier == HB_FRONTIER_PULL)
             mark_pull_kernel<<<step_grid, kStepThreads, 0, s>>>(a);
-        else if (a.has_reverse)
+        else if (a.has_reverse && !a.push_union)
             mark_push_kernel<<<step_grid, kStepThreads, 0, s>>>(a);
+        if (a.push_union) {
+            // marks and pushes in one pass (frontier iterations only)
+            if (ev) cudaEventRecord(ev[2], s);
+            push_union_kernel<<<step_grid, kStepThreads, 0, s>>>(a);
+        }
         copy_forward_kernel<<<step_grid, kStepThreads, 0, s>>>(a);
         PlanParams pp{};
         pp.chunk = y.chunk;
@@ -410,12 +569,19 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
         pp.dense = 0;
         plan_kernel<<<1, 1024, 0, s>>>(a, pp, a.plan_sparse, a.owner_sparse, a.cstart_sparse);
         k += (a.frontier == HB_FRONTIER_PULL || a.has_reverse) ? 4 : 3;
+        if (a.push_union) ++k;   // push_union in place of mark_push, plus the tail below
     }
-    if (ev_before) cudaEventRecord(ev_before, s);
+    if (ev) cudaEventRecord(ev[0], s);
     cudaError_t e = fp32 ? launch_step_t<true>(a, y.log2m, step_grid, s)
                          : launch_step_t<false>(a, y.log2m, step_grid, s);
     if (e != cudaSuccess) return e;
-    if (ev_after) cudaEventRecord(ev_after, s);
+    if (ev) cudaEventRecord(ev[1], s);
+    if (a.push_union) {
+        e = fp32 ? launch_union_tail_t<true>(a, y.log2m, step_grid, s)
+                 : launch_union_tail_t<false>(a, y.log2m, step_grid, s);
+        if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[3], s);
+    }
     if (a.frontier != HB_FRONTIER_OFF) {
         compact_changed_kernel<<<grid_for(a.n, 256), 256, 0, s>>>(a);
         ++k;

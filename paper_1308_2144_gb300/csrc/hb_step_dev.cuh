@@ -57,6 +57,7 @@ __device__ __forceinline__ void mark_append(const StepArgs &a, int32_t u, int la
         base = atomicAdd(&a.ctr->fill[key], (unsigned long long)__popc(peers));
     base = __shfl_sync(FULL, base, leader);
     if (key >= 0) a.slist[a.seg_begin[key] + (int64_t)base + __popc(peers & lanemask_lt())] = u;
+    if (a.push_union) return;   // arcs are then counted where they are pushed
     unsigned long long dd = key >= 0 ? (unsigned long long)d : 0ULL;
 #pragma unroll
     for (int o = 16; o; o >>= 1) dd += __shfl_xor_sync(FULL, dd, o);
@@ -359,6 +360,9 @@ __device__ __forceinline__ void begin_one(const StepArgs &a) {
             sparse = a.has_reverse && (double)c->prev_push_arcs <= a.sparse_frac * (double)a.m;
     }
     c->mode = sparse;
+    // pushed frontier iterations examine exactly the arcs into last
+    // iteration's changed nodes
+    if (sparse && a.push_union) c->arcs = c->prev_push_arcs;
 }
 
 // End of an iteration: count it and record convergence (Sec. 4.2: stop
@@ -394,6 +398,35 @@ __device__ __forceinline__ void copy_forward_one(const StepArgs &a, int t, int64
     if (!((a.mustbits[w >> 5] >> (w & 31)) & 1u)) {
         const int64_t o = ((int64_t)w << logCH) + ch;
         reinterpret_cast<uint4 *>(nxt)[o] = reinterpret_cast<const uint4 *>(cur)[o];
+    }
+}
+
+// Pushed union (frontier iterations with the reverse CSR).  For t >= 1 a
+// successor w that did not change in iteration t-1 has c_t[w] = c_{t-1}[w]
+// <= c_t[v] register by register (Jacobi: c_t[v] already holds the max over
+// v's successors at t-1), so it adds nothing to v's union.  The union of a
+// recomputed node therefore needs only its successors that changed last
+// time, which the reverse CSR of those nodes enumerates: each changed
+// node's counter is folded into the write-buffer counter of each
+// predecessor with a byte-wise atomic max.  The write buffer holds c_{t-1}
+// before the iteration (<= c_t), and the per-node tail folds in c_t[v], so
+// every recomputed node ends with exactly the union of Algorithm 2.
+// One pair (w, v) by a team of G lanes, chunks tl, tl + G, ...; only words
+// that would grow are written.
+__device__ __forceinline__ void push_pair(const StepArgs &a, const uint4 *cur4, uint4 *nxt4, int32_t w,
+                                          int32_t v, int logCH, int tl, int G) {
+    const int CH = 1 << logCH;
+    const uint4 *src = cur4 + ((int64_t)w << logCH);
+    uint4 *dst = nxt4 + ((int64_t)v << logCH);
+    for (int ch = tl; ch < CH; ch += G) {
+        const uint4 x = __ldg(src + ch);
+        const uint4 y = __ldcg(dst + ch);
+        if (!ne16(vmax16(y, x), y)) continue;
+        uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + ch);
+        if (bmax4(y.x, x.x) != y.x) atomic_bmax4(d32 + 0, x.x, &a.ctr->err);
+        if (bmax4(y.y, x.y) != y.y) atomic_bmax4(d32 + 1, x.y, &a.ctr->err);
+        if (bmax4(y.z, x.z) != y.z) atomic_bmax4(d32 + 2, x.z, &a.ctr->err);
+        if (bmax4(y.w, x.w) != y.w) atomic_bmax4(d32 + 3, x.w, &a.ctr->err);
     }
 }
 

@@ -34,6 +34,7 @@ HB_BORROW_DEVICE_PTRS = 0x2
 HB_FP32_ESTIMATE = 0x4
 HB_NO_RELABEL = 0x8
 HB_PROFILE = 0x10
+HB_PULL_GATHER = 0x20
 
 FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
 
@@ -73,7 +74,9 @@ class Info(ctypes.Structure):
                 ("total_arcs", ctypes.c_int64), ("last_sparse", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("kernel_ms", ctypes.c_double), ("kernel_bytes", ctypes.c_double)]
+                ("kernel_ms", ctypes.c_double), ("kernel_bytes", ctypes.c_double),
+                ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
+                ("push_bytes", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -234,12 +237,12 @@ def _stream_ptr(stream):
 
 
 def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
-                 max_steps=1 << 20, stream=None, profile=False) -> Options:
+                 max_steps=1 << 20, stream=None, profile=False, pull_gather=False) -> Options:
     o = Options()
     load().hb_default_options(ctypes.byref(o))
     o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
                | (HB_FP32_ESTIMATE if fp32 else 0) | (0 if relabel else HB_NO_RELABEL)
-               | (HB_PROFILE if profile else 0))
+               | (HB_PROFILE if profile else 0) | (HB_PULL_GATHER if pull_gather else 0))
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
     o.max_steps = int(max_steps)
     o.stream = _stream_ptr(stream)

@@ -96,11 +96,49 @@ def test_every_log2m(orc, b):
     walk_parity(orc, off, tgt, b, 1000 + b)
 
 
-@pytest.mark.parametrize("frontier", ["auto", "push", "pull", "off"])
+@pytest.mark.parametrize("frontier,pull_gather", [("auto", False), ("auto", True), ("push", False),
+                                                  ("push", True), ("pull", False), ("off", False)])
 @pytest.mark.parametrize("relabel", [True, False])
-def test_frontier_policies_and_layouts(orc, frontier, relabel):
+def test_frontier_policies_and_layouts(orc, frontier, pull_gather, relabel):
     off, tgt = graphs.rmat_graph(scale=12, edge_factor=8, seed=21).numpy()
-    walk_parity(orc, off, tgt, 5, 77, frontier=frontier, relabel=relabel)
+    walk_parity(orc, off, tgt, 5, 77, frontier=frontier, relabel=relabel, pull_gather=pull_gather)
+
+
+@pytest.mark.parametrize("b", list(range(4, 13)))
+def test_pushed_union_every_log2m(orc, b):
+    """Every iteration after the first is a frontier iteration (push policy),
+    done by the pushed union: counters, frontier and accumulators equal the
+    oracle's full recomputation at every step, for every log2m."""
+    off, tgt = graphs.rmat_graph(scale=11, edge_factor=8, seed=30 + b).numpy()
+    walk_parity(orc, off, tgt, b, 500 + b, frontier="push")
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("frontier", ["auto", "push"])
+def test_pushed_and_gathered_frontiers_agree_bitwise(fp32, frontier):
+    """Pushing last iteration's changed counters and gathering every
+    successor give the same union, so the two runs agree bit for bit in
+    counters, frontier, accumulators and centralities (both precisions)."""
+    g = graphs.rmat_graph(scale=14, edge_factor=12, seed=5, device="cuda")
+    hs = [hbl.HyperBall(g.offsets, g.targets, log2m=6, seed=3, n=g.n, fp32=fp32, frontier=frontier,
+                        pull_gather=pg) for pg in (False, True)]
+    while True:
+        ks = [h.step() for h in hs]
+        assert ks[0] == ks[1]
+        assert torch.equal(hs[0].registers(), hs[1].registers())
+        f0, f1 = hs[0].frontier(), hs[1].frontier()
+        assert torch.equal(f0[0], f1[0]) and torch.equal(f0[1], f1[1])
+        if ks[0] == 0:
+            break
+    for x, y in zip(hs[0].accumulators(), hs[1].accumulators()):
+        assert torch.equal(x, y)
+    c0, c1 = hs[0].centralities(), hs[1].centralities()
+    for key in c0:
+        assert torch.equal(c0[key], c1[key])
+    i0, i1 = hs[0].info(), hs[1].info()
+    assert i0["t"] == i1["t"] and i0["total_arcs"] <= i1["total_arcs"]
+    for h in hs:
+        h.close()
 
 
 def _degree_boundary_graph(b, seed=3):
@@ -145,6 +183,7 @@ def test_hub_with_many_predecessors(orc):
     edges += [(int(u), int(w)) for u, w in rng.integers(1, n, size=(3 * n, 2))]
     off, tgt = graphs.from_edges(n, edges, keep_all=False).numpy()
     walk_parity(orc, off, tgt, 4, 9, frontier="push")
+    walk_parity(orc, off, tgt, 4, 9, frontier="push", pull_gather=True)
 
 
 @pytest.mark.parametrize("name", ["path", "cycle", "star_out", "star_in", "complete", "loops_dups",
