@@ -47,6 +47,9 @@ WORKLOADS = {
                                       "transpose scanned, log2m=4, FP32 estimates"),
     "web24": dict(log2m=4, seed=42, desc="R-MAT scale 24 (16,777,216 nodes), edge factor 16, dedup, "
                                         "transpose scanned, log2m=4, FP32 estimates (profiling size)"),
+    "web25": dict(log2m=4, seed=42, desc="R-MAT scale 25 (33,554,432 nodes), edge factor 16, dedup, "
+                                        "transpose scanned, log2m=4, FP32 estimates (profiling size: "
+                                        "counters well above L2)"),
 }
 
 
@@ -60,6 +63,8 @@ def make_graph(name, device):
         return graphs.web_graph(device=device)
     if name == "web24":
         return graphs.web_graph(scale=24, device=device, bucket_bits=2)
+    if name == "web25":
+        return graphs.web_graph(scale=25, device=device, bucket_bits=3)
     raise ValueError(name)
 
 
