@@ -110,6 +110,7 @@ hb_status setup_shared(hb_graph *g) {
     a.rtgt = g->rtgt;
     a.has_reverse = want_reverse ? 1 : 0;
     g->push_union = want_reverse && (g->opt.flags & HB_PULL_GATHER) == 0;
+    a.push_union = g->push_union ? 1 : 0;
     a.plan_dense = M.alloc<Plan>(1);
     a.owner_dense = M.alloc<int32_t>(g->heavy_total);
     a.cstart_dense = M.alloc<int64_t>(g->seg_count[0] + 1);
@@ -301,7 +302,7 @@ hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_
     g->n = tmpl->n; g->m = tmpl->m; g->b = tmpl->b; g->y = tmpl->y;
     g->opt = tmpl->opt;
     g->s = s;
-    g->fp32 = tmpl->fp32; g->relabel = tmpl->relabel;
+    g->fp32 = tmpl->fp32; g->relabel = tmpl->relabel; g->push_union = tmpl->push_union;
     g->step_grid = tmpl->step_grid;
     g->off = tmpl->off; g->tgt = tmpl->tgt; g->roff = tmpl->roff; g->rtgt = tmpl->rtgt;
     g->perm = tmpl->perm; g->inv = tmpl->inv;
@@ -529,9 +530,7 @@ hb_status hb_create32(const int32_t *offsets, const int32_t *targets, int64_t n,
 hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
-    StepArgs a = g->a;
-    a.push_union = g->push_union ? 1 : 0;
-    cudaError_t e = launch_iteration(a, g->y, g->fp32, g->step_grid, g->s, g->profile ? g->ev : nullptr,
+    cudaError_t e = launch_iteration(g->a, g->y, g->fp32, g->step_grid, g->s, g->profile ? g->ev : nullptr,
                                      &g->launches);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->s);

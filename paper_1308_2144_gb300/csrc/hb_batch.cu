@@ -37,6 +37,8 @@ struct BatchArrays {
     int64_t *item_prefix;          // [9][k+1] work items of the running iteration, per log2m
     int64_t *list_prefix;          // [k+1] previous changed lists (push marking)
     int64_t *big_prefix;           // [k+1] previous many-predecessor lists
+    int64_t *push_prefix;          // [k+1] pushed union: warp items of 32 previous changed nodes
+    int64_t *pbig_prefix;          // [k+1] pushed union: previous many-predecessor lists
     int64_t *copy_prefix;          // [k+1] copy-forward elements
     int64_t *word_prefix;          // [k+1] must-check bitmap words to clear
     const int64_t *tile_prefix;    // [k+1] 256-node tiles (static)
@@ -96,8 +98,16 @@ __global__ void batch_begin_kernel(BatchArrays B) {
     __syncthreads();
     auto push_ok = [&](int g) {
         const StepArgs &a = B.args[g];
-        return a.ctr->mode == 1 && a.has_reverse && a.frontier != HB_FRONTIER_PULL;
+        return a.ctr->mode == 1 && a.has_reverse && a.frontier != HB_FRONTIER_PULL && !a.push_union;
     };
+    auto pushed = [&](int g) {
+        const StepArgs &a = B.args[g];
+        return a.ctr->mode == 1 && a.push_union;
+    };
+    graph_prefix(B.k, B.push_prefix, [&](int g) {
+        return pushed(g) ? ((int64_t)B.args[g].ctr->prev_list_len + 31) / 32 : 0; });
+    graph_prefix(B.k, B.pbig_prefix, [&](int g) {
+        return pushed(g) ? (int64_t)B.args[g].ctr->prev_big : 0; });
     graph_prefix(B.k, B.list_prefix, [&](int g) {
         return push_ok(g) ? (int64_t)B.args[g].ctr->prev_list_len : 0; });
     graph_prefix(B.k, B.big_prefix, [&](int g) {
@@ -148,6 +158,33 @@ __global__ void batch_mark_push_kernel(BatchArrays B) {
     }
 }
 
+// Pushed union of the graphs in a pushed frontier iteration: a warp per 32
+// changed nodes, a block per node with many predecessors.
+__global__ void __launch_bounds__(kStepThreads, 4) batch_push_union_kernel(BatchArrays B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = B.push_prefix[B.k];
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = gw; i < total; i += nw) {
+        const int g = find_graph(B.push_prefix, B.k, i);
+        const StepArgs &a = B.args[g];
+        const int t = a.ctr->t;
+        push_union_item(a, reinterpret_cast<const uint4 *>(a.regs[t & 1]),
+                        reinterpret_cast<uint4 *>(a.regs[(t + 1) & 1]), a.clist[(t + 1) & 1],
+                        (int64_t)a.ctr->prev_list_len, (i - B.push_prefix[g]) * 32, a.b - 4, lane);
+    }
+    const int64_t nbig = B.pbig_prefix[B.k];
+    const int wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int64_t q = blockIdx.x; q < nbig; q += gridDim.x) {
+        const int g = find_graph(B.pbig_prefix, B.k, q);
+        const StepArgs &a = B.args[g];
+        const int t = a.ctr->t;
+        push_union_big(a, reinterpret_cast<const uint4 *>(a.regs[t & 1]),
+                       reinterpret_cast<uint4 *>(a.regs[(t + 1) & 1]),
+                       a.biglist[(t + 1) & 1][q - B.pbig_prefix[g]], wid, nwarps, a.b - 4, lane);
+    }
+}
+
 __global__ void batch_copy_forward_kernel(BatchArrays B) {
     const int64_t total = B.copy_prefix[B.k];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -162,7 +199,7 @@ __global__ void batch_copy_forward_kernel(BatchArrays B) {
 __global__ void batch_plan_kernel(BatchArrays B) {
     for (int g = blockIdx.x; g < B.k; g += gridDim.x) {
         const StepArgs &a = B.args[g];
-        if (a.ctr->mode != 1) continue;
+        if (a.ctr->mode != 1 || a.push_union) continue;   // pushed iterations need no gather plan
         PlanParams pp{};
         const int ls = logsmax_of(a.b);
         pp.chunk = 64LL << ls;
@@ -181,6 +218,12 @@ __global__ void batch_items_kernel(BatchArrays B) {
             const StepArgs &a = B.args[g];
             const int mode = a.ctr->mode;
             if (mode == kMode_Idle || a.b != lb) return 0;
+            if (mode == 1 && a.push_union) {   // tail items of 32/L marked nodes
+                int64_t nodes = 0;
+                for (int s = 0; s < kSegs; ++s) nodes += (int64_t)a.ctr->fill[s];
+                const int npw = 32 >> ((lb - 4) < 5 ? (lb - 4) : 5);
+                return (nodes + npw - 1) / npw;
+            }
             return mode == 1 ? a.plan_sparse->items : a.plan_dense->items;
         });
     }
@@ -240,7 +283,7 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : 4)
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int cur_g = -1, t = 0;
-    bool sparse = false, prefetch = false;
+    bool sparse = false, prefetch = false, pushed = false;
     double rd64 = 1.0;
     float rd32 = 1.0f;
     for (int64_t it = gw; it < total; it += nw) {
@@ -255,12 +298,17 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : 4)
             const Counters *c = a.ctr;
             t = c->t;
             sparse = c->mode == 1;
+            pushed = sparse && a.push_union;
             prefetch = !sparse && (t == 0 || 4 * (int64_t)c->prev_changed > a.n_pos);
             rd64 = 1.0 / (double)(t + 1);
             rd32 = 1.0f / (float)(t + 1);
         }
         __syncwarp();
-        batch_item<LOG2P, F32>(a, it - s_prefix[g], t, sparse, rd64, rd32, s_pow2, prefetch, &s_cnt[wid]);
+        if (pushed)
+            union_tail_item<LOG2P, F32>(a, t, (it - s_prefix[g]) * (32 / Cfg<LOG2P>::L), &s_cnt[wid], rd64,
+                                        rd32, s_pow2);
+        else
+            batch_item<LOG2P, F32>(a, it - s_prefix[g], t, sparse, rd64, rd32, s_pow2, prefetch, &s_cnt[wid]);
     }
     __syncwarp();
     if (cur_g >= 0 && lane == 0 && s_cnt[wid]) atomicAdd(&B.args[cur_g].ctr->n_changed, s_cnt[wid]);
@@ -389,6 +437,7 @@ cudaError_t enqueue_iteration(hb_batch *b, const BatchArrays &B) {
     batch_begin_kernel<<<1, 1024, 0, s>>>(B);
     batch_clear_bits_kernel<<<b->aux_grid, 256, 0, s>>>(B);
     batch_mark_push_kernel<<<b->step_grid, kStepThreads, 0, s>>>(B);
+    batch_push_union_kernel<<<b->step_grid, kStepThreads, 0, s>>>(B);
     batch_copy_forward_kernel<<<b->aux_grid, 256, 0, s>>>(B);
     batch_plan_kernel<<<b->k < 65535 ? b->k : 65535, 1024, 0, s>>>(B);
     batch_items_kernel<<<1, 1024, 0, s>>>(B);
@@ -474,7 +523,7 @@ hb_status batch_setup(hb_batch *b, const std::vector<StepArgs> &hargs, const std
     const int k = b->k;
     DevMem &M = b->mem;
     StepArgs *args = M.alloc<StepArgs>(k);
-    int64_t *pref = M.alloc<int64_t>((size_t)14 * (k + 1));
+    int64_t *pref = M.alloc<int64_t>((size_t)17 * (k + 1));
     int64_t *garcs = M.alloc<int64_t>(k);
     int32_t *done = M.alloc<int32_t>(k);
     BatchCtl *ctl = M.alloc<BatchCtl>(1);
@@ -487,7 +536,9 @@ hb_status batch_setup(hb_batch *b, const std::vector<StepArgs> &hargs, const std
     if (e != cudaSuccess) return bfail(HB_ERR_CUDA, "batch upload");
     BatchArrays &B = b->B;
     B.args = args;
-    B.item_prefix = pref + 6 * (k + 1);   // 9 arrays, one per log2m
+    B.item_prefix = pref + 6 * (k + 1);   // 9 arrays, one per log2m (6 .. 14)
+    B.push_prefix = pref + 15 * (k + 1);
+    B.pbig_prefix = pref + 16 * (k + 1);
     B.list_prefix = pref + (k + 1);
     B.big_prefix = pref + 2 * (k + 1);
     B.copy_prefix = pref + 3 * (k + 1);

@@ -244,13 +244,8 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
 // Frontier iteration with the reverse CSR: the counter of every node that
 // changed in the last iteration is folded into each predecessor's write
 // buffer counter, and the predecessor is marked for recomputation (the
-// frontier of Sec. 5.1, as mark_push does).  The work is the set of pairs
-// (changed node w, predecessor v): a warp takes 32 changed nodes at a time
-// and spreads all their pairs over teams of G lanes (a scan of their
-// predecessor counts, then a binary search over it by shuffles), so nodes
-// with few predecessors leave no lane idle; nodes with many predecessors
-// are done by the whole grid.  Each team folds one pair, G 16-byte chunks
-// at a time.
+// frontier of Sec. 5.1, as mark_push does): a warp per 32 changed nodes
+// (push_union_item), the nodes with many predecessors by the whole grid.
 __global__ void __launch_bounds__(kStepThreads, 4) push_union_kernel(StepArgs a) {
     const Counters *c = a.ctr;
     if (c->mode != 1 || !a.push_union) return;
@@ -261,85 +256,24 @@ __global__ void __launch_bounds__(kStepThreads, 4) push_union_kernel(StepArgs a)
     const int32_t *bigp = a.biglist[(t + 1) & 1];
     const int64_t np = (int64_t)c->prev_list_len, nb = (int64_t)c->prev_big;
     const int logCH = a.b - 4;
-    const int logG = logCH < 5 ? logCH : 5;
     const int lane = threadIdx.x & 31;
-    const int team = lane >> logG;
-    const int tl = lane & ((1 << logG) - 1);
-    const int ppw = 32 >> logG;   // pairs per warp pass
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = gw * 32; base < np; base += nw * 32) {
-        const int64_t i = base + lane;
-        int32_t w = 0;
-        int64_t r0 = 0;
-        int cnt = 0;   // predecessors, <= kBigRdeg
-        if (i < np) {
-            w = prev[i];
-            r0 = a.roff[w];
-            const int64_t rd = a.roff[w + 1] - r0;
-            if (rd <= kBigRdeg) cnt = (int)rd;
-        }
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int total = __shfl_sync(FULL, incl, 31);
-        const int excl = incl - cnt;
-        for (int eb = 0; eb < total; eb += ppw) {
-            const int e = eb + team;
-            // owner: the first lane whose inclusive count exceeds e
-            int q = 0;
-#pragma unroll
-            for (int s = 16; s; s >>= 1)
-                if (__shfl_sync(FULL, incl, q + s - 1) <= e) q += s;
-            const int32_t ow = __shfl_sync(FULL, w, q);
-            const int64_t or0 = __shfl_sync(FULL, r0, q);
-            const int oex = __shfl_sync(FULL, excl, q);
-            int32_t v = -1;
-            if (e < total) {
-                v = a.rtgt[or0 + (e - oex)];
-                push_pair(a, cur4, nxt4, ow, v, logCH, tl, 1 << logG);
-            }
-            mark_append(a, tl == 0 ? v : -1, lane);
-        }
-    }
-    for (int64_t q = 0; q < nb; ++q) {
-        const int32_t w = bigp[q];
-        const int64_t r0 = a.roff[w], rd = a.roff[w + 1] - r0;
-        for (int64_t pb = gw * ppw; pb < rd; pb += nw * ppw) {
-            const int64_t e = pb + team;
-            int32_t v = -1;
-            if (e < rd) {
-                v = a.rtgt[r0 + e];
-                push_pair(a, cur4, nxt4, w, v, logCH, tl, 1 << logG);
-            }
-            mark_append(a, tl == 0 ? v : -1, lane);
-        }
-    }
+    for (int64_t base = gw * 32; base < np; base += nw * 32)
+        push_union_item(a, cur4, nxt4, prev, np, base, logCH, lane);
+    for (int64_t q = 0; q < nb; ++q) push_union_big(a, cur4, nxt4, bigp[q], gw, nw, logCH, lane);
 }
 
-// The per-node tail of a pushed frontier iteration: every node marked for
-// recomputation (the sparse list, by degree segment) takes its pushed
-// union from the write buffer and goes through the same tail as a gathered
-// node (own counter folded in, changed flag, estimator, accumulators,
-// changed list).  One team of L lanes per node.
+// The per-node tail of a pushed frontier iteration over the marked nodes.
 template <int LOG2P, bool F32>
 __global__ void __launch_bounds__(kStepThreads) union_tail_kernel(StepArgs a) {
     using C = Cfg<LOG2P>;
     const Counters *ctr = a.ctr;
     if (ctr->mode != 1 || !a.push_union) return;
     const int t = ctr->t;
-    const uint8_t *cur = a.regs[t & 1];
-    uint8_t *nxt = a.regs[(t + 1) & 1];
-    int32_t *clist = a.clist[t & 1];
-    int32_t *biglist = a.biglist[t & 1];
-    int64_t start[kSegs + 1];
-    start[0] = 0;
+    int64_t total = 0;
 #pragma unroll
-    for (int s = 0; s < kSegs; ++s) start[s + 1] = start[s] + (int64_t)ctr->fill[s];
-    const int64_t total = start[kSegs];
+    for (int s = 0; s < kSegs; ++s) total += (int64_t)ctr->fill[s];
     __shared__ unsigned long long s_changed;
     __shared__ unsigned long long s_pow2[64];
     const double rdist64 = 1.0 / (double)(t + 1);
@@ -350,32 +284,11 @@ __global__ void __launch_bounds__(kStepThreads) union_tail_kernel(StepArgs a) {
         s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int team = lane >> C::LOGL;
-    const int tl = lane & (C::L - 1);
     constexpr int NPW = 32 / C::L;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = gw * NPW; base < total; base += nw * NPW) {
-        const int64_t i = base + team;
-        const bool active = i < total;
-        int64_t v = 0;
-        uint4 acc[C::CPL];
-#pragma unroll
-        for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-        if (active) {
-            int64_t pos = a.seg_begin[0] + i;
-#pragma unroll
-            for (int s = 1; s < kSegs; ++s)
-                if (i >= start[s]) pos = a.seg_begin[s] + (i - start[s]);
-            v = a.slist[pos];
-            const uint4 *row = reinterpret_cast<const uint4 *>(nxt + v * C::P) + tl;
-#pragma unroll
-            for (int c = 0; c < C::CPL; ++c) acc[c] = __ldcg(row + c * C::L);
-        }
-        node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, tl, tl, team, C::LOGL, clist, biglist,
-                                  true, &s_changed, rdist64, rdist32, s_pow2);
-    }
+    for (int64_t base = gw * NPW; base < total; base += nw * NPW)
+        union_tail_item<LOG2P, F32>(a, t, base, &s_changed, rdist64, rdist32, s_pow2);
     __syncthreads();
     if (threadIdx.x == 0 && s_changed) atomicAdd(&a.ctr->n_changed, s_changed);
 }

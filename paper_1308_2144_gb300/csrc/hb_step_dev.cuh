@@ -430,6 +430,117 @@ __device__ __forceinline__ void push_pair(const StepArgs &a, const uint4 *cur4, 
     }
 }
 
+// The changed nodes prev[base .. base + 32) of the last iteration (np in
+// all): every pair (w, predecessor v) is pushed and v marked.  The pairs of
+// the 32 nodes are spread over teams of G lanes (a warp scan of their
+// predecessor counts, then a binary search over it by shuffles), so nodes
+// with few predecessors leave no lane idle.  Nodes with more than kBigRdeg
+// predecessors are skipped here (push_union_big).  Called by a whole warp.
+__device__ __forceinline__ void push_union_item(const StepArgs &a, const uint4 *cur4, uint4 *nxt4,
+                                                const int32_t *prev, int64_t np, int64_t base,
+                                                int logCH, int lane) {
+    const int logG = logCH < 5 ? logCH : 5;
+    const int team = lane >> logG;
+    const int tl = lane & ((1 << logG) - 1);
+    const int ppw = 32 >> logG;   // pairs per warp pass
+    const int64_t i = base + lane;
+    int32_t w = 0;
+    int64_t r0 = 0;
+    int cnt = 0;   // predecessors, <= kBigRdeg
+    if (i < np) {
+        w = prev[i];
+        r0 = a.roff[w];
+        const int64_t rd = a.roff[w + 1] - r0;
+        if (rd <= kBigRdeg) cnt = (int)rd;
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    const int excl = incl - cnt;
+    for (int eb = 0; eb < total; eb += ppw) {
+        const int e = eb + team;
+        // owner: the first lane whose inclusive count exceeds e
+        int q = 0;
+#pragma unroll
+        for (int s = 16; s; s >>= 1)
+            if (__shfl_sync(FULL, incl, q + s - 1) <= e) q += s;
+        const int32_t ow = __shfl_sync(FULL, w, q);
+        const int64_t or0 = __shfl_sync(FULL, r0, q);
+        const int oex = __shfl_sync(FULL, excl, q);
+        int32_t v = -1;
+        if (e < total) {
+            v = a.rtgt[or0 + (e - oex)];
+            push_pair(a, cur4, nxt4, ow, v, logCH, tl, 1 << logG);
+        }
+        mark_append(a, tl == 0 ? v : -1, lane);
+    }
+}
+
+// The pairs of one changed node w with many predecessors, by warp wi of
+// nwi warps.
+__device__ __forceinline__ void push_union_big(const StepArgs &a, const uint4 *cur4, uint4 *nxt4,
+                                               int32_t w, int64_t wi, int64_t nwi, int logCH, int lane) {
+    const int logG = logCH < 5 ? logCH : 5;
+    const int team = lane >> logG;
+    const int tl = lane & ((1 << logG) - 1);
+    const int ppw = 32 >> logG;
+    const int64_t r0 = a.roff[w], rd = a.roff[w + 1] - r0;
+    for (int64_t pb = wi * ppw; pb < rd; pb += nwi * ppw) {
+        const int64_t e = pb + team;
+        int32_t v = -1;
+        if (e < rd) {
+            v = a.rtgt[r0 + e];
+            push_pair(a, cur4, nxt4, w, v, logCH, tl, 1 << logG);
+        }
+        mark_append(a, tl == 0 ? v : -1, lane);
+    }
+}
+
+// Per-node tail of a pushed frontier iteration for the marked nodes at
+// flat positions base .. base + 32/L of the sparse list (by degree
+// segment): the pushed union is read back from the write buffer and goes
+// through the same tail as a gathered node (own counter folded in,
+// changed flag, estimator, accumulators, changed list).  One team of L
+// lanes per node; called by a whole warp.
+template <int LOG2P, bool F32>
+__device__ __forceinline__ void union_tail_item(const StepArgs &a, int t, int64_t base,
+                                                unsigned long long *cnt, double rdist64, float rdist32,
+                                                const unsigned long long *pow2) {
+    using C = Cfg<LOG2P>;
+    const Counters *ctr = a.ctr;
+    const uint8_t *cur = a.regs[t & 1];
+    uint8_t *nxt = a.regs[(t + 1) & 1];
+    int64_t start[kSegs + 1];
+    start[0] = 0;
+#pragma unroll
+    for (int s = 0; s < kSegs; ++s) start[s + 1] = start[s] + (int64_t)ctr->fill[s];
+    const int lane = threadIdx.x & 31;
+    const int team = lane >> C::LOGL;
+    const int tl = lane & (C::L - 1);
+    const int64_t i = base + team;
+    const bool active = i < start[kSegs];
+    int64_t v = 0;
+    uint4 acc[C::CPL];
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
+    if (active) {
+        int64_t pos = a.seg_begin[0] + i;
+#pragma unroll
+        for (int s = 1; s < kSegs; ++s)
+            if (i >= start[s]) pos = a.seg_begin[s] + (i - start[s]);
+        v = a.slist[pos];
+        const uint4 *row = reinterpret_cast<const uint4 *>(nxt + v * C::P) + tl;
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) acc[c] = __ldcg(row + c * C::L);
+    }
+    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, tl, tl, team, C::LOGL, a.clist[t & 1],
+                              a.biglist[t & 1], true, cnt, rdist64, rdist32, pow2);
+}
+
 struct PlanParams {
     int64_t count[kSegs];   // dense: segment sizes
     int64_t chunk;

@@ -138,3 +138,29 @@ def test_batch_autotuner_keeps_results():
             assert torch.equal(x, y)
         solo.close()
     batch.close()
+
+
+def test_batch_pushed_and_gathered_frontiers_agree_at_every_log2m(orc):
+    """Frontier iterations done by the pushed union (default) and by the
+    gather (HB_PULL_GATHER) give identical batch results, on a mix that spans
+    every log2m from 4 to 12 (one gather kernel and item prefix per log2m)."""
+    mix = [(graphs.rmat_graph(scale=10, edge_factor=8, seed=300 + i), b, 50 + i)
+           for i, b in enumerate(range(4, 13))]
+    res = []
+    for pg in (False, True):
+        batch = hbl.HyperBallBatch(_descs(mix), pull_gather=pg)
+        batch.run()
+        res.append([(batch.registers(i).cpu(), [x.cpu() for x in batch.accumulators(i)], batch.info(i)["t"])
+                    for i in range(len(mix))])
+        batch.close()
+    for (r0, a0, t0), (r1, a1, t1) in zip(*res):
+        assert t0 == t1 and torch.equal(r0, r1)
+        for x, y in zip(a0, a1):
+            assert torch.equal(x, y)
+    for i in (0, 4, 8):
+        g, b, s = mix[i]
+        off, tgt = g.numpy()
+        ref = orc.run(off, tgt, b, s)
+        assert res[0][i][2] == ref.steps
+        assert np.array_equal(res[0][i][0].numpy(), ref.regs)
+        np.testing.assert_allclose(res[0][i][1][0].numpy(), ref.sumd, rtol=1e-9, atol=0)
