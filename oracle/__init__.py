@@ -73,6 +73,17 @@ def _load(path: str):
     L.orc_get_threads.argtypes = []
     L.orc_init.restype = None
     L.orc_init.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, _u8p]
+    L.orc_init_weighted.restype = None
+    L.orc_init_weighted.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, _i64p, _u8p]
+    L.orc_step_ex.restype = ctypes.c_int64
+    L.orc_step_ex.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int, ctypes.c_int32,
+                              _u8p, _u8p, _f64p, _f64p, ctypes.c_double, _f64p, _u8p]
+    L.orc_discount.restype = ctypes.c_double
+    L.orc_discount.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int64]
+    L.orc_run_ex.restype = ctypes.c_int
+    L.orc_run_ex.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int, ctypes.c_uint64,
+                             _i64p, _f64p, ctypes.c_int32, ctypes.c_int32, _u8p, _f64p, _f64p,
+                             _f64p, _i32p, _u8p]
     L.orc_step.restype = ctypes.c_int64
     L.orc_step.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int, ctypes.c_int32,
                            _u8p, _u8p, _f64p, _f64p, _u8p]
@@ -167,34 +178,61 @@ def init(n: int, b: int, seed: int) -> np.ndarray:
     return c
 
 
+def init_weighted(n: int, b: int, seed: int, weights) -> np.ndarray:
+    """Initial counters with node weights simulated by replicas (Sec. 6)."""
+    w = np.ascontiguousarray(weights, dtype=np.int64)
+    assert w.size == n and (w >= 0).all()
+    c = np.zeros((n, 1 << b), dtype=np.uint8)
+    lib().orc_init_weighted(n, b, seed & (2**64 - 1), _p(w, _i64p), _p(c, _u8p))
+    return c
+
+
+def discount(table, d: int) -> float:
+    """f(d) of a discount table: table[d-1] for 1 <= d <= len, else 0."""
+    f = np.ascontiguousarray(table, dtype=np.float64)
+    return float(lib().orc_discount(_p(f, _f64p), f.size, d))
+
+
 def step(offsets, targets, b: int, t: int, cur: np.ndarray,
-         sumd: np.ndarray, harm: np.ndarray):
+         sumd: np.ndarray, harm: np.ndarray, disc: np.ndarray | None = None,
+         fdist: float = 0.0):
     """One Algorithm 2 iteration at loop index t.  Returns (next, changed,
-    n_changed); sumd and harm are updated in place."""
+    n_changed); sumd and harm (and disc, with discount fdist = f(t+1), when
+    given) are updated in place."""
     off, tgt = _csr(offsets, targets)
     n = off.size - 1
     cur = np.ascontiguousarray(cur, dtype=np.uint8)
     nxt = np.empty_like(cur)
     changed = np.zeros(n, dtype=np.uint8)
     assert sumd.dtype == np.float64 and harm.dtype == np.float64
-    k = lib().orc_step(n, _p(off, _i64p), _p(tgt, _i32p), b, t, _p(cur, _u8p),
-                       _p(nxt, _u8p), _p(sumd, _f64p), _p(harm, _f64p), _p(changed, _u8p))
+    if disc is None:
+        k = lib().orc_step(n, _p(off, _i64p), _p(tgt, _i32p), b, t, _p(cur, _u8p),
+                           _p(nxt, _u8p), _p(sumd, _f64p), _p(harm, _f64p), _p(changed, _u8p))
+    else:
+        assert disc.dtype == np.float64 and disc.flags.c_contiguous
+        k = lib().orc_step_ex(n, _p(off, _i64p), _p(tgt, _i32p), b, t, _p(cur, _u8p),
+                              _p(nxt, _u8p), _p(sumd, _f64p), _p(harm, _f64p), float(fdist),
+                              _p(disc, _f64p), _p(changed, _u8p))
     return nxt, changed, int(k)
 
 
 class RunResult:
-    def __init__(self, regs, sumd, harm, steps, converged, changed_hist):
+    def __init__(self, regs, sumd, harm, steps, converged, changed_hist, disc=None):
         self.regs = regs
         self.sumd = sumd
         self.harm = harm
         self.steps = steps
         self.converged = converged
         self.changed_hist = changed_hist
+        self.disc = disc
 
 
 def run(offsets, targets, b: int, seed: int, max_steps: int = 1 << 20,
-        keep_changed: bool = False) -> RunResult:
-    """Algorithm 2 to its fixpoint (or max_steps iterations)."""
+        keep_changed: bool = False, weights=None, discount=None) -> RunResult:
+    """Algorithm 2 to its fixpoint (or max_steps iterations).  ``weights``
+    (one non-negative integer per node, Sec. 6) and ``discount`` (a table
+    f(1), f(2), ...; Sec. 7, which adds the ``disc`` accumulator) are
+    optional."""
     off, tgt = _csr(offsets, targets)
     n = off.size - 1
     p = 1 << b
@@ -207,13 +245,22 @@ def run(offsets, targets, b: int, seed: int, max_steps: int = 1 << 20,
     if keep_changed:
         cap = min(max_steps, 4096)
         hist = np.zeros((cap, n), dtype=np.uint8)
-    rc = lib().orc_run(n, _p(off, _i64p), _p(tgt, _i32p), b, seed & (2**64 - 1), cap,
-                       _p(regs, _u8p), _p(sumd, _f64p), _p(harm, _f64p),
-                       ctypes.byref(steps), _p(hist, _u8p) if hist is not None else None)
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(weights, dtype=np.int64)
+        assert w.size == n and (w >= 0).all()
+    f, disc = None, None
+    if discount is not None:
+        f = np.ascontiguousarray(discount, dtype=np.float64)
+        disc = np.zeros(n, dtype=np.float64)
+    rc = lib().orc_run_ex(n, _p(off, _i64p), _p(tgt, _i32p), b, seed & (2**64 - 1),
+                          _p(w, _i64p), _p(f, _f64p), 0 if f is None else f.size, cap,
+                          _p(regs, _u8p), _p(sumd, _f64p), _p(harm, _f64p), _p(disc, _f64p),
+                          ctypes.byref(steps), _p(hist, _u8p) if hist is not None else None)
     if rc < 0:
         raise MemoryError("oracle run: allocation failed")
     s = int(steps.value)
-    return RunResult(regs, sumd, harm, s, rc == 0, hist[:s] if hist is not None else None)
+    return RunResult(regs, sumd, harm, s, rc == 0, hist[:s] if hist is not None else None, disc)
 
 
 def finalize(b: int, regs: np.ndarray, sumd: np.ndarray, harm: np.ndarray):

@@ -13,7 +13,9 @@
  *     (new counters are applied only after the whole scan);
  *   - Sec. 5: the three per-node accumulators (sum of distances, sum of
  *     reciprocal distances, coreachable-set size);
- *   - Sec. 3: closeness, Lin and harmonic centrality from them.
+ *   - Sec. 3: closeness, Lin and harmonic centrality from them;
+ *   - Sec. 6: integer node weights simulated by replicas at initialisation;
+ *   - Sec. 7: a discounted accumulator sum_t f(t) * (new layer at t).
  * Everything is written as plain loops in the paper's order, in double
  * precision, compiled with -ffp-contract=off so that every floating-point
  * operation rounds once, as written.
@@ -32,7 +34,14 @@
  *   - at loop index t the scanned counter a estimates |B(v,t+1)| and c[v]
  *     estimates |B(v,t)|, so the new layer sits at distance t+1;
  *   - steps counts every executed iteration, including the last one, in
- *     which no counter changed.
+ *     which no counter changed;
+ *   - replicas (Sec. 6): the replicas of node v are the items numbered
+ *     W_v, W_v+1, ..., W_v+w(v)-1 with W_v = w(0)+...+w(v-1), hashed like
+ *     node ids, so distinct nodes have disjoint replicas and unit weights
+ *     give back the unweighted counters exactly; a weight of 0 (outside the
+ *     paper's 1..W) leaves the node's own counter empty;
+ *   - discount (Sec. 7): f is given as a table, f(d) = table[d-1] for
+ *     d = 1..len and 0 for longer distances.
  */
 #include <math.h>
 #include <stdint.h>
@@ -150,18 +159,38 @@ void orc_init(int64_t n, int b, uint64_t seed, uint8_t *c)
         orc_add(c + v * p, b, orc_hash(seed, (uint64_t)v));
 }
 
+/* Sec. 6: the weighted ball of radius 0 is the set of v's replicas, so
+ * the initial counter of v receives add() of each of its w(v) replica
+ * items.  Replica items are numbered consecutively across nodes in node
+ * order (first item of v = sum of the weights of the nodes before it). */
+void orc_init_weighted(int64_t n, int b, uint64_t seed, const int64_t *w, uint8_t *c)
+{
+    int64_t p = (int64_t)1 << b;
+    memset(c, 0, (size_t)(n * p));
+    uint64_t first = 0;
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t k = 0; k < w[v]; ++k)
+            orc_add(c + v * p, b, orc_hash(seed, first + (uint64_t)k));
+        first += (uint64_t)w[v];
+    }
+}
+
 /* One iteration of the do/until loop of Algorithm 2 at loop index t.
  * Reads only `cur` (c_t) and writes `next` (c_{t+1}): the update file of
  * the paper is applied after the whole scan.  For every node whose counter
  * changed, the Sec. 5 accumulators receive the new layer at distance t+1:
  *     sumd[v] += (t+1) * (size(a) - size(c[v]))
  *     harm[v] += (size(a) - size(c[v])) / (t+1)
+ * and, if disc is not NULL, the Sec. 7 discounted accumulator with the
+ * discount fdist = f(t+1) of the new layer's distance:
+ *     disc[v] += f(t+1) * (size(a) - size(c[v]))
  * changed[v] is 1 when a differs from c[v].  Returns the number of changed
  * nodes.  Nodes are independent, so the parallel loop gives the same
  * result for any thread count. */
-int64_t orc_step(int64_t n, const int64_t *offsets, const int32_t *targets,
-                 int b, int32_t t, const uint8_t *cur, uint8_t *next,
-                 double *sumd, double *harm, uint8_t *changed)
+int64_t orc_step_ex(int64_t n, const int64_t *offsets, const int32_t *targets,
+                    int b, int32_t t, const uint8_t *cur, uint8_t *next,
+                    double *sumd, double *harm, double fdist, double *disc,
+                    uint8_t *changed)
 {
     int64_t p = (int64_t)1 << b;
     int64_t n_changed = 0;
@@ -184,6 +213,7 @@ int64_t orc_step(int64_t n, const int64_t *offsets, const int32_t *targets,
             double dist = (double)(t + 1);
             sumd[v] = sumd[v] + dist * delta;
             harm[v] = harm[v] + delta / dist;
+            if (disc) disc[v] = disc[v] + fdist * delta;
             n_changed += 1;
         }
         memcpy(next + v * p, a, (size_t)p);                  /* write <v, a> */
@@ -191,29 +221,53 @@ int64_t orc_step(int64_t n, const int64_t *offsets, const int32_t *targets,
     return n_changed;
 }
 
+/* The unweighted, undiscounted iteration. */
+int64_t orc_step(int64_t n, const int64_t *offsets, const int32_t *targets,
+                 int b, int32_t t, const uint8_t *cur, uint8_t *next,
+                 double *sumd, double *harm, uint8_t *changed)
+{
+    return orc_step_ex(n, offsets, targets, b, t, cur, next, sumd, harm, 0.0, NULL, changed);
+}
+
+/* f(d) of a discount table (Sec. 7): table[d-1] for 1 <= d <= len, else 0. */
+double orc_discount(const double *table, int32_t len, int64_t d)
+{
+    return (d >= 1 && d <= len) ? table[d - 1] : 0.0;
+}
+
 /* The whole of Algorithm 2: init, then iterate until an iteration leaves
  * every counter unchanged, or max_steps iterations ran.  On return `c`
  * holds the final counters, *steps the number of iterations executed
  * (including the final unchanged one).  If changed_hist is not NULL it
  * receives, for each executed iteration s, the changed set in row s
- * (capacity max_steps * n bytes).  Returns 0 on convergence, 1 if
- * max_steps ran out first, -1 on allocation failure. */
-int orc_run(int64_t n, const int64_t *offsets, const int32_t *targets,
-            int b, uint64_t seed, int32_t max_steps,
-            uint8_t *c, double *sumd, double *harm, int32_t *steps,
-            uint8_t *changed_hist)
+ * (capacity max_steps * n bytes).  weights (Sec. 6) may be NULL (every
+ * node weighs 1); disc (Sec. 7, discount table ftable of flen entries) may
+ * be NULL.  Returns 0 on convergence, 1 if max_steps ran out first, -1 on
+ * allocation failure. */
+int orc_run_ex(int64_t n, const int64_t *offsets, const int32_t *targets,
+               int b, uint64_t seed, const int64_t *weights,
+               const double *ftable, int32_t flen, int32_t max_steps,
+               uint8_t *c, double *sumd, double *harm, double *disc,
+               int32_t *steps, uint8_t *changed_hist)
 {
     int64_t p = (int64_t)1 << b;
     uint8_t *other = (uint8_t *)malloc((size_t)(n * p > 0 ? n * p : 1));
     uint8_t *changed = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     if (!other || !changed) { free(other); free(changed); return -1; }
-    orc_init(n, b, seed, c);
-    for (int64_t v = 0; v < n; ++v) { sumd[v] = 0.0; harm[v] = 0.0; }
+    if (weights) orc_init_weighted(n, b, seed, weights, c);
+    else orc_init(n, b, seed, c);
+    for (int64_t v = 0; v < n; ++v) {
+        sumd[v] = 0.0;
+        harm[v] = 0.0;
+        if (disc) disc[v] = 0.0;
+    }
     uint8_t *cur = c, *nxt = other;
     int32_t t = 0;
     int converged = 0;
     while (t < max_steps) {
-        int64_t k = orc_step(n, offsets, targets, b, t, cur, nxt, sumd, harm, changed);
+        double fdist = disc ? orc_discount(ftable, flen, (int64_t)t + 1) : 0.0;
+        int64_t k = orc_step_ex(n, offsets, targets, b, t, cur, nxt, sumd, harm, fdist, disc,
+                                changed);
         if (changed_hist) memcpy(changed_hist + (int64_t)t * n, changed, (size_t)n);
         uint8_t *tmp = cur; cur = nxt; nxt = tmp;
         t += 1;
@@ -224,6 +278,15 @@ int orc_run(int64_t n, const int64_t *offsets, const int32_t *targets,
     free(other);
     free(changed);
     return converged ? 0 : 1;
+}
+
+int orc_run(int64_t n, const int64_t *offsets, const int32_t *targets,
+            int b, uint64_t seed, int32_t max_steps,
+            uint8_t *c, double *sumd, double *harm, int32_t *steps,
+            uint8_t *changed_hist)
+{
+    return orc_run_ex(n, offsets, targets, b, seed, NULL, NULL, 0, max_steps, c, sumd, harm,
+                      NULL, steps, changed_hist);
 }
 
 /* Sec. 3 from the Sec. 5 accumulators:

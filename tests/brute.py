@@ -81,3 +81,28 @@ def linear_counting(p: int, k: int) -> float:
     """Estimate of a counter with k distinct nonzero registers (and its raw
     estimate below 5p/2): p ln(p / (p - k))."""
     return p * math.log(p / (p - k))
+
+
+def replica_starts(weights) -> list[int]:
+    """First replica item of each node: the running total of the weights of
+    the nodes before it (Sec. 6 asks only that distinct nodes have disjoint
+    replicas; consecutive numbering is the reading taken)."""
+    starts, run = [], 0
+    for w in weights:
+        starts.append(run)
+        run += int(w)
+    return starts
+
+
+def hll_of_items(items, b: int, seed: int) -> np.ndarray:
+    """Algorithm 1's add() applied to items hashed like node ids."""
+    M = np.zeros(1 << b, dtype=np.uint8)
+    for x in items:
+        i, r = split_bits(node_hash(seed, int(x)), b)
+        if r > M[i]:
+            M[i] = r
+    return M
+
+
+def replica_items(nodes, weights, starts):
+    return [starts[y] + k for y in nodes for k in range(int(weights[y]))]

@@ -11,6 +11,7 @@ import pytest
 import oracle
 from tests import test_oracle_counter as tc
 from tests import test_oracle_hyperball as th
+from tests import test_oracle_weights_discount as tw
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "hb_oracle.c")
 
@@ -41,6 +42,15 @@ MUTANTS = {
                                "if (closeness) closeness[v] = s > 0.0 ? 1.0 / s : 1.0;"),
     "must_check_own_flag": ("if (changed[targets[e]]) { m = 1; break; }",
                             "if (changed[v]) { m = 1; break; }"),
+    "replicas_overlap_across_nodes": ("orc_add(c + v * p, b, orc_hash(seed, first + (uint64_t)k));",
+                                      "orc_add(c + v * p, b, orc_hash(seed, (uint64_t)v + (uint64_t)k));"),
+    "replica_dropped": ("for (int64_t k = 0; k < w[v]; ++k)", "for (int64_t k = 1; k < w[v]; ++k)"),
+    "discount_at_distance_t": ("double fdist = disc ? orc_discount(ftable, flen, (int64_t)t + 1) : 0.0;",
+                               "double fdist = disc ? orc_discount(ftable, flen, (int64_t)t) : 0.0;"),
+    "discount_table_shifted": ("return (d >= 1 && d <= len) ? table[d - 1] : 0.0;",
+                               "return (d >= 0 && d < len) ? table[d] : 0.0;"),
+    "discount_not_accumulated": ("if (disc) disc[v] = disc[v] + fdist * delta;",
+                                 "if (disc) disc[v] = fdist * delta;"),
 }
 
 
@@ -60,6 +70,9 @@ def _checks(orc):
     for name in ("zipf", "path"):
         yield lambda name=name: th.test_run_matches_stepwise(orc, name)
     yield lambda: th.test_must_check_definition(orc)
+    yield lambda: tw.test_weighted_counters_equal_hll_of_replica_balls(orc, "dag", 4, 42)
+    yield lambda: tw.test_weighted_discounted_accumulators_closed_form(orc, "log", 10, 8, 1)
+    yield lambda: tw.test_discounts_that_reduce_to_the_accumulators(orc, "dag")
 
 
 def test_unmutated_oracle_passes_every_check(orc):
