@@ -196,9 +196,39 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
  * re-initialise. */
 hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot);
 
+/* Node weights (Sec. 6).  The paper simulates an integer weight w(v) by
+ * replicas: the ball of radius 0 around v holds w(v) distinct items, and
+ * distinct nodes have disjoint replicas, so the growth of a counter between
+ * iterations estimates the total weight of the new layer.  sumd, harm and
+ * the discounted accumulator then estimate sum_y w(y) d(y,x),
+ * sum_y w(y)/d(y,x) and sum_y w(y) f(d(y,x)), and reachable the weight of
+ * the coreachable set (x included).
+ *   weights: n integers in [0, 2^31), host or device, in the caller's node
+ *   order, copied; NULL restores unit weights.  The replicas of node u are
+ *   the items W_u .. W_u + w(u) - 1, W_u = w(0) + ... + w(u-1), hashed like
+ *   node ids, so unit weights give exactly the unweighted counters.
+ * The computation restarts from t = 0 with the handle's current seed.
+ * Initialisation costs one hash per replica, w(u) of them in one thread.
+ * HB_ERR_INVALID (handle unchanged) if a weight is out of range.
+ * Single-graph handles only (not the batched or served forms). */
+hb_status hb_set_weights(hb_graph *g, const int64_t *weights);
+
+/* Discount function (Sec. 7): a further per-node accumulator
+ *     disc[v] = sum over iterations t of f(t+1) * (size(c_{t+1}[v]) - size(c_t[v]))
+ * which estimates the discounted-gain centrality sum_{y != v} f(d(y,v)),
+ * weighted by w(y) under hb_set_weights.  f(d) = f[d-1] for d = 1..len and
+ * 0 for longer distances; f is host or device memory, copied.  len = 0 (f
+ * may then be NULL) removes the accumulator.  The computation restarts from
+ * t = 0 with the handle's current seed.  Single-graph handles only. */
+hb_status hb_set_discount(hb_graph *g, const double *f, int32_t len);
+
+/* The discounted accumulator, n doubles in the caller's node order (host or
+ * device).  HB_ERR_STATE if no discount is set. */
+hb_status hb_get_discounted(hb_graph *g, double *out);
+
 /* Checkpoint: write t, counters, last frontier and accumulators (and the
- * graph) to a file; hb_load rebuilds a handle that continues exactly
- * where the saved one stopped. */
+ * graph, the weights and the discount) to a file; hb_load rebuilds a
+ * handle that continues exactly where the saved one stopped. */
 hb_status hb_save(hb_graph *g, const char *path);
 hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out);
 
@@ -235,6 +265,27 @@ typedef struct hb_batch hb_batch;
  * PULL is taken as AUTO; max_steps caps hb_batch_run).  With a NULL stream
  * the batch makes its own. */
 hb_status hb_batch_create(int k, const hb_graph_desc *gs, const hb_options *opt, hb_batch **out);
+
+/* Multiple runs (Sec. 5): the paper repeats HyperBall with independent
+ * hash seeds to tighten its estimates and to measure their empirical
+ * standard deviation.  This creates a batch of `runs` (1..4096) runs of
+ * one graph (CSR as for hb_create, int64 offsets), run r with seed
+ * seeds[r]: the graph is uploaded, validated and laid out once and every
+ * run reads that one copy; each run owns only its counters, flags and
+ * accumulators (2np + about 30n bytes).  Options as for hb_batch_create.
+ * Run r's results equal those of hb_create(..., seeds[r], ...) run alone. */
+hb_status hb_batch_create_runs(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                               int log2m, int runs, const uint64_t *seeds, const hb_options *opt,
+                               hb_batch **out);
+
+/* Per-node mean and empirical standard deviation (sample form, divisor
+ * k-1; 0 when k = 1) over the k graphs of a batch of one centrality of the
+ * current state: which = 0 closeness, 1 harmonic, 2 Lin, 3 reachable
+ * (Sec. 3, as hb_get_centralities).  n doubles each in the caller's node
+ * order, host or device; either may be NULL.  Every graph of the batch
+ * must have the same node count (HB_ERR_INVALID otherwise): a batch from
+ * hb_batch_create_runs, or one graph passed k times. */
+hb_status hb_batch_get_run_stats(hb_batch *b, int32_t which, double *mean, double *sd);
 
 /* One iteration of every graph that has not converged; *n_active (may be
  * NULL) receives the number of graphs still changing afterwards. */

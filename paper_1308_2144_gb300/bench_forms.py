@@ -4,6 +4,7 @@ runs on the same GPU.
 
     python -m paper_1308_2144_gb300.bench_forms batch [--graphs 512]
     python -m paper_1308_2144_gb300.bench_forms serve [--rate 200 --seconds 60 --warm 10]
+    python -m paper_1308_2144_gb300.bench_forms runs [--runs 16]
 
 batch: independent R-MAT graphs (0.57, 0.19, 0.19, 0.05) with node counts
 log-uniform in [1e3, 2e6], edge factor uniform in 4..32, log2m uniform in
@@ -18,6 +19,15 @@ pool, log2m 4 or 6, seed = request id).  The continuous-batching server
 (many slots) versus the same server with one slot (a FIFO one at a time),
 on the same arrival stream.  Prints one JSON line per server: p50/p99
 latency from arrival to results in host memory, and arc-updates/s.
+
+runs: the paper's multiple runs (Sec. 5) on the encyclopedia-like graph
+(log2m 6): R runs with seeds 42..42+R-1 in one batch sharing one copy of the
+graph (hb_batch_create_runs, hb_batch_run), then the per-node mean and
+standard deviation of all four centralities, versus the same R runs one
+after the other on one handle (hb_reset, hb_run_to_fixpoint,
+hb_get_centralities, statistics of the R results on the GPU).  Prints one
+JSON line: time for all R runs and their statistics both ways, and
+arc-updates/s.
 """
 from __future__ import annotations
 
@@ -168,6 +178,62 @@ def serve_main(args):
         print(json.dumps(r), flush=True)
 
 
+def runs_main(args):
+    g = graphs.enwiki_graph(device="cuda")
+    n, b = g.n, 6
+    seeds = [42 + r for r in range(args.runs)]
+    batch = hbl.HyperBallBatch.runs(g.offsets, g.targets, n, b, seeds, fp32=args.fp32)
+    outs = {k: (torch.empty(n, dtype=torch.float64, device="cuda"),
+                torch.empty(n, dtype=torch.float64, device="cuda")) for k in hbl.HyperBallBatch.CENTRALITIES}
+    lib = hbl.load()
+
+    def batched():
+        batch.reset(seeds)
+        iters = batch.run()
+        for w, k in enumerate(hbl.HyperBallBatch.CENTRALITIES):
+            hbl._check(lib.hb_batch_get_run_stats(batch._h, w, hbl._ptr(outs[k][0]), hbl._ptr(outs[k][1])))
+        return iters
+
+    solo = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seeds[0], n=n, fp32=args.fp32)
+    vals = torch.empty((4, args.runs, n), dtype=torch.float64, device="cuda")
+
+    def one_at_a_time():
+        arcs = 0
+        for r, s in enumerate(seeds):
+            hbl.hb_reset(solo._h, s)
+            solo.run()
+            hbl.hb_get_centralities(solo._h, vals[0, r], vals[1, r], vals[2, r], vals[3, r])
+            arcs += solo.info()["total_arcs"]
+        torch.std_mean(vals, dim=1)
+        return arcs
+
+    batched()
+    one_at_a_time()
+    bt, st = [], []
+    for _ in range(args.repeat):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        iters = batched()
+        torch.cuda.synchronize()
+        bt.append(time.perf_counter() - t)
+        t = time.perf_counter()
+        solo_arcs = one_at_a_time()
+        torch.cuda.synchronize()
+        st.append(time.perf_counter() - t)
+    _, _, arcs = batch.totals()
+    batch.close()
+    solo.close()
+    b_s, s_s = min(bt), min(st)
+    print(json.dumps({
+        "form": "runs", "graph": "encyclopedia-like (R-MAT scale 23, 4,206,785 nodes), transpose, log2m 6",
+        "runs": args.runs, "n": n, "m": g.m, "batch_ms": round(1e3 * b_s, 3), "batch_iterations": iters,
+        "batch_arc_updates_per_s": arcs / b_s, "one_at_a_time_ms": round(1e3 * s_s, 3),
+        "one_at_a_time_arc_updates_per_s": solo_arcs / s_s, "speedup": s_s / b_s,
+        "estimate": "fp32" if args.fp32 else "fp64",
+        "includes": "all runs to their fixpoints and the per-node mean and std of the four centralities"}),
+        flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -187,10 +253,14 @@ def main():
     s.add_argument("--reserve-gb", type=int, default=8)
     s.add_argument("--seed", type=int, default=5)
     s.add_argument("--fp32", action="store_true")
+    r = sub.add_parser("runs")
+    r.add_argument("--runs", type=int, default=16)
+    r.add_argument("--repeat", type=int, default=3)
+    r.add_argument("--fp32", action="store_true")
     args = ap.parse_args()
     build.build()
     hbl.load()
-    (batch_main if args.cmd == "batch" else serve_main)(args)
+    {"batch": batch_main, "serve": serve_main, "runs": runs_main}[args.cmd](args)
 
 
 if __name__ == "__main__":

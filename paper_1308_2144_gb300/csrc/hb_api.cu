@@ -310,6 +310,9 @@ hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_
     g->n_pos = tmpl->n_pos;
     g->heavy_total = tmpl->heavy_total;
     g->a = tmpl->a;
+    g->a.disc = nullptr;   // weights and discounts belong to single-graph handles
+    g->a.ftab = nullptr;
+    g->a.flen = 0;
     hb_status st = setup_run(g);
     if (st == HB_OK) st = init_state(g, seed);
     if (st != HB_OK) { delete g; return st; }
@@ -328,7 +331,7 @@ hb_status finish_setup(hb_graph *g) {
 
 hb_status init_state(hb_graph *g, uint64_t seed) {
     g->seed = seed;
-    cudaError_t e = launch_init(g->a, g->perm, seed, g->fp32, g->s);
+    cudaError_t e = launch_init(g->a, g->perm, seed, g->fp32, g->s, g->wfirst);
     g->launches += g->n > 0 ? 2 : 1;
     g->kernel_launches = 0;
     g->kernel_ms = g->kernel_bytes = 0.0;
@@ -760,10 +763,109 @@ hb_status hb_reset(hb_graph *g, uint64_t seed) {
     return init_state(g, seed);
 }
 
+hb_status hb_set_weights(hb_graph *g, const int64_t *weights) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    DevMem &M = g->mem;
+    if (!weights) {
+        if (g->wfirst) M.release(g->wfirst);
+        g->wfirst = nullptr;
+        return init_state(g, g->seed);
+    }
+    const int64_t n = g->n;
+    DevMem tmp;
+    int64_t *w = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (is_device_ptr(weights)) {
+        w = const_cast<int64_t *>(weights);
+    } else {
+        w = tmp.alloc<int64_t>(n);
+        if (w) e = to_device(w, weights, sizeof(int64_t) * n, g->s);
+    }
+    unsigned long long *err = tmp.alloc<unsigned long long>(1);
+    int64_t *wf = M.alloc<int64_t>(n + 1);
+    if (!w || !err || !wf) {
+        tmp.free_all();
+        if (wf) M.release(wf);
+        return fail(HB_ERR_OOM, "out of device memory (weights)");
+    }
+    unsigned long long err_host = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(unsigned long long), g->s);
+    if (e == cudaSuccess) e = replica_starts(w, n, wf, err, g->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err_host, err, sizeof(err_host), cudaMemcpyDeviceToHost, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) {
+        M.release(wf);
+        return cuda_fail(e, "weights");
+    }
+    if (err_host) {
+        M.release(wf);
+        return fail(HB_ERR_INVALID, "every weight must lie in [0, 2^31)");
+    }
+    if (g->wfirst) M.release(g->wfirst);
+    g->wfirst = wf;
+    return init_state(g, g->seed);
+}
+
+hb_status hb_set_discount(hb_graph *g, const double *f, int32_t len) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    if (len < 0) return fail(HB_ERR_INVALID, "len must be >= 0");
+    if (len > 0 && !f) return fail(HB_ERR_INVALID, "f is NULL");
+    DevMem &M = g->mem;
+    StepArgs &a = g->a;
+    if (g->ftab) M.release(g->ftab);
+    g->ftab = nullptr;
+    if (len == 0) {
+        if (g->disc) M.release(g->disc);
+        g->disc = nullptr;
+        a.disc = nullptr;
+        a.ftab = nullptr;
+        a.flen = 0;
+        return init_state(g, g->seed);
+    }
+    if (!g->disc) g->disc = M.alloc<double>(g->n);
+    g->ftab = M.alloc<double>(len);
+    if (!g->disc || !g->ftab) {
+        if (g->disc) M.release(g->disc);
+        if (g->ftab) M.release(g->ftab);
+        g->disc = g->ftab = nullptr;
+        a.disc = nullptr;
+        a.ftab = nullptr;
+        a.flen = 0;
+        return fail(HB_ERR_OOM, "out of device memory (discount)");
+    }
+    cudaError_t e = to_device(g->ftab, f, sizeof(double) * len, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    if (e != cudaSuccess) return cuda_fail(e, "discount table");
+    a.disc = g->disc;
+    a.ftab = g->ftab;
+    a.flen = len;
+    return init_state(g, g->seed);
+}
+
+hb_status hb_get_discounted(hb_graph *g, double *out) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    if (!g->a.disc) return fail(HB_ERR_STATE, "no discount function set (hb_set_discount)");
+    if (g->n > 0 && !out) return fail(HB_ERR_INVALID, "out is NULL");
+    const int64_t n = g->n;
+    DevMem tmp;
+    double *d = is_device_ptr(out) ? out : tmp.alloc<double>(n);
+    if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = launch_gather_f64(g->a.disc, g->inv, n, d, g->s);
+    if (e == cudaSuccess && d != out) e = to_caller(out, d, sizeof(double) * n, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "discounted accumulator");
+    return HB_OK;
+}
+
 // ------------------------------------------------------------ checkpoint --
 
 namespace {
-constexpr uint64_t kMagic = 0x31304c4c41425948ULL;   // "HYBALL01"
+constexpr uint64_t kMagic = 0x32304c4c41425948ULL;   // "HYBALL02"
 
 struct SaveHeader {
     uint64_t magic;
@@ -772,6 +874,7 @@ struct SaveHeader {
     uint64_t seed;
     int32_t converged, frontier;
     int64_t total_arcs;
+    int32_t weighted, flen;   // Sec. 6 replica starts and Sec. 7 discount follow when set
 };
 
 bool write_dev(FILE *f, const void *dev, size_t bytes, cudaStream_t s) {
@@ -796,7 +899,7 @@ hb_status hb_save(hb_graph *g, const char *path) {
     FILE *f = fopen(path, "wb");
     if (!f) return fail(HB_ERR_INVALID, std::string("cannot open ") + path);
     SaveHeader h{kMagic, g->n, g->m, g->b, g->fp32, g->relabel, g->t, g->seed,
-                 g->converged, g->opt.frontier, g->total_arcs};
+                 g->converged, g->opt.frontier, g->total_arcs, g->wfirst ? 1 : 0, g->a.flen};
     const size_t P = (size_t)1 << g->b;
     const size_t n = (size_t)g->n;
     bool ok = fwrite(&h, sizeof(h), 1, f) == 1;
@@ -818,6 +921,11 @@ hb_status hb_save(hb_graph *g, const char *path) {
     const int last = (g->t + 1) & 1;
     ok = ok && write_dev(f, g->a.clist[last], sizeof(int32_t) * c.list_len, g->s);
     ok = ok && write_dev(f, g->a.biglist[last], sizeof(int32_t) * c.n_big, g->s);
+    if (g->wfirst) ok = ok && write_dev(f, g->wfirst, sizeof(int64_t) * (n + 1), g->s);
+    if (g->a.flen) {
+        ok = ok && write_dev(f, g->ftab, sizeof(double) * g->a.flen, g->s);
+        ok = ok && write_dev(f, g->disc, sizeof(double) * n, g->s);
+    }
     fclose(f);
     if (!ok) return fail(HB_ERR_CUDA, "checkpoint write failed");
     return HB_OK;
@@ -877,6 +985,19 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     const int last = (h.t + 1) & 1;
     ok = ok && read_dev(f, g->a.clist[last], sizeof(int32_t) * c.list_len, g->s);
     ok = ok && read_dev(f, g->a.biglist[last], sizeof(int32_t) * c.n_big, g->s);
+    if (ok && h.weighted) {
+        g->wfirst = M.alloc<int64_t>(n + 1);
+        ok = g->wfirst && read_dev(f, g->wfirst, sizeof(int64_t) * (n + 1), g->s);
+    }
+    if (ok && h.flen > 0) {
+        g->ftab = M.alloc<double>(h.flen);
+        g->disc = M.alloc<double>(n);
+        ok = g->ftab && g->disc && read_dev(f, g->ftab, sizeof(double) * h.flen, g->s) &&
+             read_dev(f, g->disc, sizeof(double) * n, g->s);
+        g->a.disc = g->disc;
+        g->a.ftab = g->ftab;
+        g->a.flen = h.flen;
+    }
     fclose(f);
     if (!ok) { delete g; return fail(HB_ERR_INVALID, "truncated checkpoint"); }
     *out = g;

@@ -380,6 +380,38 @@ int grid_for(int64_t work, int threads) {
     return (int)g;
 }
 
+// Sec. 5 (multiple runs): per node u of the caller's order, the mean and
+// the empirical (sample, k-1) standard deviation over the k graphs of the
+// batch of one centrality (which: 0 closeness, 1 harmonic, 2 Lin,
+// 3 reachable), in two passes over the runs.  Graph r maps u to its own
+// node index through invs[r] (null: identity) and reads its current
+// counters (buffer of its completed-iteration parity).
+template <bool F32>
+__device__ __forceinline__ double run_value(const StepArgs &a, const int32_t *inv, int64_t u, int which) {
+    const int64_t v = inv ? (int64_t)inv[u] : u;
+    double c[4];
+    node_centralities<F32>(a, a.regs[a.ctr->steps_done & 1], v, c);
+    return c[which];
+}
+
+template <bool F32>
+__global__ void run_stats_kernel(const StepArgs *args, const int32_t *const *invs, int k, int64_t n,
+                                 int which, double *mean, double *sd) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int r = 0; r < k; ++r) sum += run_value<F32>(args[r], invs[r], u, which);
+        const double mu = sum / (double)k;
+        double q = 0.0;
+        for (int r = 0; r < k; ++r) {
+            const double d = run_value<F32>(args[r], invs[r], u, which) - mu;
+            q += d * d;
+        }
+        if (mean) mean[u] = mu;
+        if (sd) sd[u] = k > 1 ? sqrt(q / (double)(k - 1)) : 0.0;
+    }
+}
+
 }  // namespace
 
 }  // namespace hb
@@ -417,7 +449,8 @@ struct hb_batch {
         if (run_exec) cudaGraphExecDestroy(run_exec);
         if (step_graph) cudaGraphDestroy(step_graph);
         if (run_graph) cudaGraphDestroy(run_graph);
-        for (hb_graph *g : graphs) hb_destroy(g);
+        // instances before the graph whose arrays they share
+        for (size_t i = graphs.size(); i-- > 0;) hb_destroy(graphs[i]);
         if (ctl_host) cudaFreeHost(ctl_host);
         mem.free_all();
         if (own_stream && s) cudaStreamDestroy(s);
@@ -573,6 +606,44 @@ hb_status batch_setup(hb_batch *b, const std::vector<StepArgs> &hargs, const std
     return st;
 }
 
+// A batch of k slots with the options' stream (or its own), before its
+// graphs are added.
+hb_status new_batch(int k, const hb_options *opt, hb_options *o, hb_batch **out) {
+    if (opt) *o = *opt; else hb_default_options(o);
+    if (o->max_steps <= 0) o->max_steps = 1 << 20;
+    if (o->frontier == HB_FRONTIER_PULL) o->frontier = HB_FRONTIER_AUTO;
+    o->flags &= ~(uint32_t)HB_PROFILE;
+    hb_batch *b = new hb_batch();
+    b->k = k;
+    b->fp32 = (o->flags & HB_FP32_ESTIMATE) != 0;
+    b->max_steps = o->max_steps;
+    if (o->stream) {
+        b->s = static_cast<cudaStream_t>(o->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(HB_ERR_CUDA, "cannot create the batch stream");
+        }
+        b->own_stream = true;
+    }
+    o->stream = b->s;
+    *out = b;
+    return HB_OK;
+}
+
+// Per-graph arguments, tiles and captured graphs once every graph is in.
+hb_status finish_batch(hb_batch *b) {
+    const int k = b->k;
+    std::vector<StepArgs> hargs(k);
+    std::vector<int64_t> tiles(k + 1, 0);
+    for (int i = 0; i < k; ++i) {
+        hargs[i] = b->graphs[i]->a;
+        tiles[i + 1] = tiles[i] + (b->graphs[i]->n + 255) / 256;
+        b->log2m_mask |= 1u << (b->graphs[i]->b - kMinLog2m);
+    }
+    return batch_setup(b, hargs, tiles);
+}
+
 }  // namespace
 
 extern "C" {
@@ -584,24 +655,9 @@ hb_status hb_batch_create(int k, const hb_graph_desc *gs, const hb_options *opt,
     if (k < 1 || k > kMaxBatch) return bfail(HB_ERR_INVALID, "k must lie in [1, 4096]");
     if (!gs) return bfail(HB_ERR_INVALID, "gs is NULL");
     hb_options o;
-    if (opt) o = *opt; else hb_default_options(&o);
-    if (o.max_steps <= 0) o.max_steps = 1 << 20;
-    if (o.frontier == HB_FRONTIER_PULL) o.frontier = HB_FRONTIER_AUTO;
-    o.flags &= ~(uint32_t)HB_PROFILE;
-    hb_batch *b = new hb_batch();
-    b->k = k;
-    b->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
-    b->max_steps = o.max_steps;
-    if (o.stream) {
-        b->s = static_cast<cudaStream_t>(o.stream);
-    } else {
-        if (cudaStreamCreateWithFlags(&b->s, cudaStreamNonBlocking) != cudaSuccess) {
-            delete b;
-            return bfail(HB_ERR_CUDA, "cannot create the batch stream");
-        }
-        b->own_stream = true;
-    }
-    o.stream = b->s;
+    hb_batch *b = nullptr;
+    hb_status st0 = new_batch(k, opt, &o, &b);
+    if (st0 != HB_OK) return st0;
     for (int i = 0; i < k; ++i) {
         hb_graph *g = nullptr;
         hb_status st = create_handle64(gs[i].offsets, gs[i].targets, gs[i].n, gs[i].m, gs[i].log2m,
@@ -613,16 +669,79 @@ hb_status hb_batch_create(int k, const hb_graph_desc *gs, const hb_options *opt,
         }
         b->graphs.push_back(g);
     }
-    std::vector<StepArgs> hargs(k);
-    std::vector<int64_t> tiles(k + 1, 0);
-    for (int i = 0; i < k; ++i) {
-        hargs[i] = b->graphs[i]->a;
-        tiles[i + 1] = tiles[i] + (b->graphs[i]->n + 255) / 256;
-        b->log2m_mask |= 1u << (b->graphs[i]->b - kMinLog2m);
-    }
-    hb_status st = batch_setup(b, hargs, tiles);
+    hb_status st = finish_batch(b);
     if (st != HB_OK) { delete b; return st; }
     *out = b;
+    return HB_OK;
+}
+
+hb_status hb_batch_create_runs(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                               int log2m, int runs, const uint64_t *seeds, const hb_options *opt,
+                               hb_batch **out) {
+    set_last_error("");
+    if (!out) return bfail(HB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (runs < 1 || runs > kMaxBatch) return bfail(HB_ERR_INVALID, "runs must lie in [1, 4096]");
+    if (!seeds) return bfail(HB_ERR_INVALID, "seeds is NULL");
+    hb_options o;
+    hb_batch *b = nullptr;
+    hb_status st = new_batch(runs, opt, &o, &b);
+    if (st != HB_OK) return st;
+    hb_graph *tmpl = nullptr;
+    st = create_handle64(offsets, targets, n, m, log2m, seeds[0], &o, &tmpl);
+    if (st != HB_OK) { delete b; return st; }
+    b->graphs.push_back(tmpl);
+    // the other runs share the first one's graph, layout and tables
+    for (int r = 1; r < runs; ++r) {
+        hb_graph *g = nullptr;
+        st = make_instance(tmpl, seeds[r], b->s, &g);
+        if (st != HB_OK) { delete b; return st; }
+        b->graphs.push_back(g);
+    }
+    st = finish_batch(b);
+    if (st != HB_OK) { delete b; return st; }
+    *out = b;
+    return HB_OK;
+}
+
+hb_status hb_batch_get_run_stats(hb_batch *b, int32_t which, double *mean, double *sd) {
+    if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    if (which < 0 || which > 3) return bfail(HB_ERR_INVALID, "which must lie in [0, 3]");
+    const int64_t n = b->graphs[0]->n;
+    for (hb_graph *g : b->graphs)
+        if (g->n != n) return bfail(HB_ERR_INVALID, "run statistics need graphs of one node count");
+    if (n > 0 && !mean && !sd) return bfail(HB_ERR_INVALID, "mean and sd are both NULL");
+    DevMem tmp;
+    std::vector<const int32_t *> inv_h(b->k);
+    for (int i = 0; i < b->k; ++i) inv_h[i] = b->graphs[i]->inv;
+    auto dev_or_tmp = [&](double *p) -> double * {
+        if (!p) return nullptr;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) == cudaSuccess &&
+            (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
+            return p;
+        cudaGetLastError();
+        return tmp.alloc<double>(n);
+    };
+    double *dm = dev_or_tmp(mean), *ds = dev_or_tmp(sd);
+    const int32_t **invs = tmp.alloc<const int32_t *>(b->k);
+    if (tmp.err != cudaSuccess) { tmp.free_all(); return bfail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = cudaMemcpyAsync(invs, inv_h.data(), sizeof(const int32_t *) * b->k,
+                                    cudaMemcpyHostToDevice, b->s);
+    if (e == cudaSuccess && n > 0) {
+        if (b->fp32)
+            run_stats_kernel<true><<<grid_for(n, 256), 256, 0, b->s>>>(b->B.args, invs, b->k, n, which, dm, ds);
+        else
+            run_stats_kernel<false><<<grid_for(n, 256), 256, 0, b->s>>>(b->B.args, invs, b->k, n, which, dm, ds);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && mean && dm != mean)
+        e = cudaMemcpyAsync(mean, dm, sizeof(double) * n, cudaMemcpyDeviceToHost, b->s);
+    if (e == cudaSuccess && sd && ds != sd)
+        e = cudaMemcpyAsync(sd, ds, sizeof(double) * n, cudaMemcpyDeviceToHost, b->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("run statistics: ") + cudaGetErrorString(e));
     return HB_OK;
 }
 

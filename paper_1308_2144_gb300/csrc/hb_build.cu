@@ -285,6 +285,31 @@ cudaError_t validate_csr(const int64_t *off, const int32_t *tgt, int64_t n, int6
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void weights_in_kernel(const int64_t *w, int64_t n, int64_t *tmp, unsigned long long *err) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = u < n ? w[u] : 0;
+        if (x < 0 || x >= ((int64_t)1 << 31)) {
+            atomicOr(err, 1ULL);
+            x = 0;
+        }
+        tmp[u] = x;
+    }
+}
+}  // namespace
+
+cudaError_t replica_starts(const int64_t *w, int64_t n, int64_t *wfirst, unsigned long long *err,
+                           cudaStream_t s) {
+    int64_t *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, sizeof(int64_t) * (n + 1), s);
+    if (e != cudaSuccess) return e;
+    weights_in_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(w, n, tmp, err);
+    e = scan_exclusive_i64(tmp, wfirst, n + 1, s);
+    cudaFreeAsync(tmp, s);
+    return e;
+}
+
 cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaStream_t s) {
     widen_kernel<<<grid_for(count, 256), 256, 0, s>>>(in, out, count);
     return cudaGetLastError();

@@ -90,6 +90,9 @@ struct hb_graph {
     int64_t *roff = nullptr;
     int32_t *rtgt = nullptr;
     int32_t *perm = nullptr, *inv = nullptr;
+    int64_t *wfirst = nullptr;     // Sec. 6: first replica item of each caller node (n+1), or null
+    double *disc = nullptr;        // Sec. 7: discounted accumulator (n), or null
+    double *ftab = nullptr;        // its discount table
     Counters *ctr = nullptr;
     Counters *ctr_host = nullptr;
     int64_t seg_count[kSegs] = {0};

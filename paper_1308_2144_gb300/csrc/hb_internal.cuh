@@ -113,6 +113,8 @@ struct StepArgs {
     uint8_t *regs[2];             // counters: iteration t reads regs[t&1], writes regs[(t+1)&1]
     double *sumd;
     double *harm;
+    double *disc;                 // Sec. 7 discounted accumulator (null: no discount)
+    const double *ftab;           // discount table: f(d) = ftab[d-1] for d <= flen, else 0
     void *ecache;                 // double[n] (FP64 form) or float[n] (FP32 form)
     uint8_t *changed;             // 1 if the node changed in the last iteration
     uint32_t *mustbits;           // frontier bitmap of the running iteration
@@ -146,6 +148,7 @@ struct StepArgs {
     int32_t hot_nodes;            // counters of nodes below this id are kept in L2
     int32_t aps;                  // class sizing (arcs per slot) of the layout
     int32_t push_union;           // frontier iterations push changed counters along reverse arcs
+    int32_t flen;                 // entries of ftab
     double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
 };
 
@@ -319,6 +322,30 @@ __device__ __forceinline__ float estimate32(uint32_t V, unsigned long long S, in
     return __fmul_rn(c32, __frcp_rn(__ull2float_rn(X)));
 }
 
+// Sec. 3 centralities of node v (internal index) from its counter row in
+// `regs` and its Sec. 5 accumulators, in the order closeness, harmonic,
+// Lin, reachable:
+//     reachable = size(c[v]); closeness = 1/sumd (0 if sumd = 0);
+//     lin = reachable^2/sumd (1 if sumd = 0); harmonic = harm.
+template <bool F32>
+__device__ __forceinline__ void node_centralities(const StepArgs &a, const uint8_t *regs, int64_t v,
+                                                  double out[4]) {
+    const int P = 1 << a.b;
+    const int CH = P >> 4;
+    uint32_t V = 0;
+    unsigned long long S = 0;
+    const uint4 *row = reinterpret_cast<const uint4 *>(regs + v * P);
+    for (int c = 0; c < CH; ++c) chunk_sums(row[c], a.b, V, S);
+    double r;
+    if (F32) r = (double)estimate32(V, S, P, a.b, a.c32, a.thr_x, a.lc32);
+    else r = estimate64(V, S, P, a.b, a.c64, a.thr_x, a.lc64);
+    const double s = a.sumd[v];
+    out[0] = s > 0.0 ? __ddiv_rn(1.0, s) : 0.0;
+    out[1] = a.harm[v];
+    out[2] = s > 0.0 ? __ddiv_rn(__dmul_rn(r, r), s) : 1.0;
+    out[3] = r;
+}
+
 // Inclusive warp scan and exclusive block scan (one value per thread,
 // blockDim a multiple of 32 up to 1024); the block scan returns the total.
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
@@ -374,8 +401,15 @@ cudaError_t build_dense_list(const int64_t *off, int64_t n, const Layout &y,
 
 cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, int64_t *total_host,
                               cudaStream_t s);
+// Algorithm 2's first loop; with wfirst (Sec. 6), the counters of weighted
+// nodes, whose replicas are the items wfirst[u] .. wfirst[u+1]-1.
 cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, bool fp32,
-                        cudaStream_t s);
+                        cudaStream_t s, const int64_t *wfirst = nullptr);
+// First replica item of every node: wfirst = exclusive prefix sums of the
+// n weights w (device), n+1 entries; sets bit 1 of *err if a weight lies
+// outside [0, 2^31).
+cudaError_t replica_starts(const int64_t *w, int64_t n, int64_t *wfirst, unsigned long long *err,
+                           cudaStream_t s);
 cudaError_t launch_dense_plan(const StepArgs &a, const Layout &y, const int64_t *seg_count,
                               Plan *plan, int32_t *owner, int64_t *cstart, cudaStream_t s);
 // One iteration: the whole launch sequence, sizes read on the device.

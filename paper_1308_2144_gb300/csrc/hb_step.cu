@@ -57,6 +57,13 @@ __global__ void init_rows_kernel(uint8_t *r0, uint8_t *r1, const int32_t *perm, 
     }
 }
 
+__device__ __forceinline__ void reset_counters(Counters *c) {
+    c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
+    for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
+    c->prev_changed = 0; c->prev_list_len = 0; c->prev_push_arcs = 0; c->prev_big = 0;
+    c->mode = 0; c->t = 0; c->steps_done = 0; c->converged = 0; c->err = 0;
+}
+
 template <bool F32>
 __global__ void init_nodes_kernel(StepArgs a, const int32_t *perm, uint64_t seed) {
     const int P = 1 << a.b;
@@ -71,15 +78,50 @@ __global__ void init_nodes_kernel(StepArgs a, const int32_t *perm, uint64_t seed
         else static_cast<double *>(a.ecache)[v] = estimate64(V, S, P, a.b, a.c64, a.thr_x, a.lc64);
         a.sumd[v] = 0.0;
         a.harm[v] = 0.0;
+        if (a.disc) a.disc[v] = 0.0;
         a.changed[v] = 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        Counters *c = a.ctr;
-        c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
-        for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
-        c->prev_changed = 0; c->prev_list_len = 0; c->prev_push_arcs = 0; c->prev_big = 0;
-        c->mode = 0; c->t = 0; c->steps_done = 0; c->converged = 0; c->err = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_counters(a.ctr);
+}
+
+// Sec. 6: integer node weights simulated by replicas.  The replicas of the
+// caller's node u are the items wfirst[u] .. wfirst[u+1]-1 (numbered
+// consecutively in the caller's node order, so unit weights give the items
+// 0..n-1 of the unweighted init); each is hashed like a node id and added
+// to u's empty counter, which is then written to both buffers.  One thread
+// per node: its row is written by no other thread.
+template <bool F32>
+__global__ void init_weighted_kernel(StepArgs a, const int32_t *perm, const int64_t *wfirst,
+                                     uint64_t seed) {
+    const int P = 1 << a.b;
+    const int CH = P >> 4;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = perm ? (int64_t)perm[v] : v;
+        uint8_t *r0 = a.regs[0] + v * P;
+        uint4 *r1 = reinterpret_cast<uint4 *>(a.regs[1] + v * P);
+        for (int c = 0; c < CH; ++c) reinterpret_cast<uint4 *>(r0)[c] = z;
+        for (int64_t item = wfirst[u]; item < wfirst[u + 1]; ++item) {
+            uint32_t idx, rho;
+            hash_to_register(splitmix64(seed, (uint64_t)item), a.b, idx, rho);
+            if (r0[idx] < rho) r0[idx] = (uint8_t)rho;
+        }
+        uint32_t V = 0;
+        unsigned long long S = 0;
+        for (int c = 0; c < CH; ++c) {
+            const uint4 x = reinterpret_cast<const uint4 *>(r0)[c];
+            r1[c] = x;
+            chunk_sums(x, a.b, V, S);
+        }
+        if (F32) static_cast<float *>(a.ecache)[v] = estimate32(V, S, P, a.b, a.c32, a.thr_x, a.lc32);
+        else static_cast<double *>(a.ecache)[v] = estimate64(V, S, P, a.b, a.c64, a.thr_x, a.lc64);
+        a.sumd[v] = 0.0;
+        a.harm[v] = 0.0;
+        if (a.disc) a.disc[v] = 0.0;
+        a.changed[v] = 0;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_counters(a.ctr);
 }
 
 // -------------------------------------------------------- step control --
@@ -306,23 +348,15 @@ __global__ void __launch_bounds__(256) compact_changed_kernel(StepArgs a) {
 template <bool F32>
 __global__ void finalize_kernel(StepArgs a, const uint8_t *regs, const int32_t *perm, double *closeness,
                                 double *harmonic, double *lin, double *reachable) {
-    const int P = 1 << a.b;
-    const int CH = P >> 4;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n;
          v += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t V = 0;
-        unsigned long long S = 0;
-        const uint4 *row = reinterpret_cast<const uint4 *>(regs + v * P);
-        for (int c = 0; c < CH; ++c) chunk_sums(row[c], a.b, V, S);
-        double r;
-        if (F32) r = (double)estimate32(V, S, P, a.b, a.c32, a.thr_x, a.lc32);
-        else r = estimate64(V, S, P, a.b, a.c64, a.thr_x, a.lc64);
-        const double s = a.sumd[v];
+        double c[4];
+        node_centralities<F32>(a, regs, v, c);
         const int64_t o = perm ? (int64_t)perm[v] : v;
-        if (reachable) reachable[o] = r;
-        if (closeness) closeness[o] = s > 0.0 ? __ddiv_rn(1.0, s) : 0.0;
-        if (lin) lin[o] = s > 0.0 ? __ddiv_rn(__dmul_rn(r, r), s) : 1.0;
-        if (harmonic) harmonic[o] = a.harm[v];
+        if (closeness) closeness[o] = c[0];
+        if (harmonic) harmonic[o] = c[1];
+        if (lin) lin[o] = c[2];
+        if (reachable) reachable[o] = c[3];
     }
 }
 
@@ -437,8 +471,13 @@ cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, in
 }
 
 cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, bool fp32,
-                        cudaStream_t s) {
+                        cudaStream_t s, const int64_t *wfirst) {
     const int CH = (1 << a.b) >> 4;
+    if (wfirst) {
+        if (fp32) init_weighted_kernel<true><<<grid_for(a.n, 128), 128, 0, s>>>(a, perm, wfirst, seed);
+        else init_weighted_kernel<false><<<grid_for(a.n, 128), 128, 0, s>>>(a, perm, wfirst, seed);
+        return cudaGetLastError();
+    }
     if (a.n > 0)
         init_rows_kernel<<<grid_for(a.n * CH, 256), 256, 0, s>>>(a.regs[0], a.regs[1], perm, a.n,
                                                                 a.b, seed);

@@ -127,6 +127,12 @@ __device__ __forceinline__ void prefetch_accumulators(const StepArgs &a, int64_t
     asm volatile("prefetch.global.L2 [%0];" ::"l"(a.harm + v));
     if (f32) asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<float *>(a.ecache) + v));
     else asm volatile("prefetch.global.L2 [%0];" ::"l"(static_cast<double *>(a.ecache) + v));
+    if (a.disc) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.disc + v));
+}
+
+// f(t+1), the discount of the layer that iteration t adds (Sec. 7).
+__device__ __forceinline__ double discount_of(const StepArgs &a, int t) {
+    return t < a.flen ? a.ftab[t] : 0.0;
 }
 
 // Per-node tail, called by all 32 lanes.  acc holds the union of the
@@ -174,12 +180,13 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
     // The accumulator loads go out together, before any store of this
     // node: the three arrays may alias as far as the compiler knows, so a
     // load placed after a store would wait a full round trip for it.
-    double s_old = 0.0, h_old = 0.0, e_old = 0.0;
+    double s_old = 0.0, h_old = 0.0, e_old = 0.0, q_old = 0.0;
     if (leader && ch) {
         s_old = a.sumd[v];
         h_old = a.harm[v];
         e_old = F32 ? (double)static_cast<const float *>(a.ecache)[v]
                     : static_cast<const double *>(a.ecache)[v];
+        if (a.disc) q_old = a.disc[v];
     }
     if (leader) a.changed[v] = ch ? 1 : 0;
     const unsigned lb = __ballot_sync(FULL, leader && ch);
@@ -204,12 +211,14 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
             static_cast<float *>(a.ecache)[v] = E;
             a.sumd[v] = __fma_rn((double)(t + 1), (double)d, s_old);   // exact product
             a.harm[v] = __dadd_rn(h_old, (double)__fmul_rn(d, rdist32));
+            if (a.disc) a.disc[v] = __fma_rn(discount_of(a, t), (double)d, q_old);
         } else {
             const double E = estimate64(V, S, C::P, a.b, a.c64, a.thr_x, a.lc64);
             const double d = __dsub_rn(E, e_old);
             static_cast<double *>(a.ecache)[v] = E;
             a.sumd[v] = __fma_rn((double)(t + 1), d, s_old);
             a.harm[v] = __fma_rn(d, rdist64, h_old);
+            if (a.disc) a.disc[v] = __fma_rn(discount_of(a, t), d, q_old);
         }
     }
     if (lane == 0) atomicAdd(s_changed, (unsigned long long)__popc(lb));

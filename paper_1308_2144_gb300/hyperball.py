@@ -43,11 +43,12 @@ HB_REQ_QUEUED, HB_REQ_RUNNING, HB_REQ_DONE, HB_REQ_FAILED = 0, 1, 2, 3
 # every symbol include/hyperball.h declares
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
-           "hb_get_info", "hb_reset", "hb_save", "hb_load", "hb_destroy", "hb_last_error",
+           "hb_get_info", "hb_reset", "hb_set_weights", "hb_set_discount", "hb_get_discounted",
+           "hb_save", "hb_load", "hb_destroy", "hb_last_error",
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
            "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
-           "hb_batch_destroy", "hb_tune", "hb_set_class_sizing", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
+           "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
            "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_take",
            "hb_server_stats", "hb_server_destroy"]
 
@@ -139,6 +140,12 @@ def load():
         L.hb_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
         L.hb_reset.restype = st
         L.hb_reset.argtypes = [_vp, ctypes.c_uint64]
+        L.hb_set_weights.restype = st
+        L.hb_set_weights.argtypes = [_vp, _vp]
+        L.hb_set_discount.restype = st
+        L.hb_set_discount.argtypes = [_vp, _vp, ctypes.c_int32]
+        L.hb_get_discounted.restype = st
+        L.hb_get_discounted.argtypes = [_vp, _vp]
         L.hb_set_class_sizing.restype = st
         L.hb_set_class_sizing.argtypes = [_vp, ctypes.c_int32]
         L.hb_tune.restype = st
@@ -158,6 +165,12 @@ def load():
         L.hb_batch_create.restype = st
         L.hb_batch_create.argtypes = [ctypes.c_int, ctypes.POINTER(GraphDesc), ctypes.POINTER(Options),
                                       ctypes.POINTER(_vp)]
+        L.hb_batch_create_runs.restype = st
+        L.hb_batch_create_runs.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Options),
+                                           ctypes.POINTER(_vp)]
+        L.hb_batch_get_run_stats.restype = st
+        L.hb_batch_get_run_stats.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
         L.hb_batch_step.restype = st
         L.hb_batch_step.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
         L.hb_batch_run.restype = st
@@ -301,6 +314,22 @@ def hb_reset(h, seed: int):
     _check(load().hb_reset(h, int(seed) & (2**64 - 1)))
 
 
+def hb_set_weights(h, weights=None):
+    """Integer node weights (n int64 values in [0, 2^31), Sec. 6); None
+    restores unit weights.  Restarts the computation."""
+    _check(load().hb_set_weights(h, _ptr(weights)))
+
+
+def hb_set_discount(h, f=None):
+    """Discount table f(1), f(2), ... (float64, Sec. 7); None removes it.
+    Restarts the computation."""
+    _check(load().hb_set_discount(h, _ptr(f), 0 if f is None else int(f.shape[0])))
+
+
+def hb_get_discounted(h, out):
+    _check(load().hb_get_discounted(h, _ptr(out)))
+
+
 def hb_tune(h) -> int:
     """Autotune the degree-class sizing; returns the chosen arcs per slot."""
     a = ctypes.c_int32()
@@ -345,6 +374,8 @@ class HyperBallBatch:
     list of (offsets, targets, n, log2m, seed) with tensors kept alive by
     this object."""
 
+    CENTRALITIES = ("closeness", "harmonic", "lin", "reachable")
+
     def __init__(self, graphs, **opts):
         self._keep = []
         descs = (GraphDesc * len(graphs))()
@@ -358,6 +389,33 @@ class HyperBallBatch:
         self.options = make_options(**opts)
         self._h = _vp()
         _check(load().hb_batch_create(self.k, descs, ctypes.byref(self.options), ctypes.byref(self._h)))
+
+    @classmethod
+    def runs(cls, offsets, targets, n: int, log2m: int, seeds, **opts) -> "HyperBallBatch":
+        """Multiple runs of one graph (Sec. 5): run r uses seeds[r]; the runs
+        share one device copy of the graph."""
+        self = cls.__new__(cls)
+        self._keep = [offsets, targets]
+        self.k = len(seeds)
+        self.sizes = [(int(n), 1 << int(log2m))] * self.k
+        self.options = make_options(**opts)
+        self._h = _vp()
+        arr = (ctypes.c_uint64 * self.k)(*[int(x) & (2**64 - 1) for x in seeds])
+        _check(load().hb_batch_create_runs(_ptr(offsets), _ptr(targets) if targets.shape[0] else None,
+                                           int(n), int(targets.shape[0]), int(log2m), self.k, arr,
+                                           ctypes.byref(self.options), ctypes.byref(self._h)))
+        return self
+
+    def run_stats(self, which, device="cuda"):
+        """Per-node mean and empirical standard deviation over the graphs
+        of the batch of one centrality ("closeness", "harmonic", "lin",
+        "reachable")."""
+        n, _ = self.sizes[0]
+        w = self.CENTRALITIES.index(which) if isinstance(which, str) else int(which)
+        mean = torch.empty(n, dtype=torch.float64, device=device)
+        sd = torch.empty(n, dtype=torch.float64, device=device)
+        _check(load().hb_batch_get_run_stats(self._h, w, _ptr(mean), _ptr(sd)))
+        return mean, sd
 
     def step(self) -> int:
         a = ctypes.c_int32()
@@ -526,6 +584,23 @@ class HyperBall:
 
     def set_class_sizing(self, arcs_per_slot: int):
         _check(load().hb_set_class_sizing(self._h, int(arcs_per_slot)))
+
+    def set_weights(self, weights=None):
+        """Node weights by replicas (Sec. 6); restarts the computation."""
+        if weights is not None and not isinstance(weights, torch.Tensor):
+            weights = np.ascontiguousarray(weights, dtype=np.int64)
+        hb_set_weights(self._h, weights)
+
+    def set_discount(self, f=None):
+        """Discount table f(1), f(2), ... (Sec. 7); restarts the computation."""
+        if f is not None and not isinstance(f, torch.Tensor):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        hb_set_discount(self._h, f)
+
+    def discounted(self, device="cuda") -> torch.Tensor:
+        out = self._out(self.n, torch.float64, device)
+        hb_get_discounted(self._h, out)
+        return out
 
     def _out(self, shape, dtype, device):
         return torch.empty(shape, dtype=dtype, device=device)

@@ -76,3 +76,35 @@ def test_averaging_runs_shrinks_error(orc, plain):
     # error of a K-run mean ~ 1/sqrt(K) of one run's: allow 0.5 for K = 16
     assert mean16 < 0.5 * single
     assert single <= 1.06 / math.sqrt(1 << b) * 1.2
+
+
+def test_run_statistics_definition(orc):
+    """Sec. 5's multiple runs: the mean and sample standard deviation over
+    runs, against their definition on two runs and on repeated seeds."""
+    off, tgt = graphs.plain_graph(n=800, seed=3).numpy()
+    b = 5
+    x = [orc.finalize(b, r.regs, r.sumd, r.harm)["harmonic"]
+         for r in (orc.run(off, tgt, b, s) for s in (7, 8))]
+    mean, sd = orc.run_stats(off, tgt, b, [7, 8], "harmonic")
+    np.testing.assert_allclose(mean, (x[0] + x[1]) / 2, rtol=1e-15)
+    np.testing.assert_allclose(sd, np.abs(x[0] - x[1]) / math.sqrt(2), rtol=1e-12, atol=1e-12)
+    mean, sd = orc.run_stats(off, tgt, b, [7, 7, 7], "harmonic")
+    np.testing.assert_allclose(mean, x[0], rtol=1e-15)     # (3x)/3 may round by an ulp
+    assert np.all(sd <= 1e-14 * np.abs(x[0]))
+
+
+def test_run_spread_matches_counter_rsd(orc, plain):
+    """The empirical standard deviation over runs of the reachable-set
+    estimate, relative to its mean, is the counter's RSD (<= 1.06/sqrt(p),
+    Sec. 4.1), and the mean over R runs is R^(1/2) times closer to the
+    exact value than one run (Sec. 5: repeated runs tighten the estimate)."""
+    off, tgt, exact = plain
+    b, R = 6, 32
+    bound = 1.06 / math.sqrt(1 << b)
+    mean, sd = orc.run_stats(off, tgt, b, list(range(7000, 7000 + R)), "reachable")
+    big = exact["reach"] >= 200
+    rel_sd = sd[big] / mean[big]
+    assert 0.7 * bound < np.median(rel_sd) < 1.15 * bound
+    # error of the mean within 3 standard errors for almost every node
+    z = np.abs(mean[big] - exact["reach"][big]) / (sd[big] / math.sqrt(R))
+    assert np.mean(z < 3.0) > 0.95
