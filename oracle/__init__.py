@@ -93,6 +93,8 @@ def _load(path: str):
     L.orc_finalize.restype = None
     L.orc_finalize.argtypes = [ctypes.c_int64, ctypes.c_int, _u8p, _f64p, _f64p,
                                _f64p, _f64p, _f64p, _f64p]
+    L.orc_neighbourhood.restype = ctypes.c_double
+    L.orc_neighbourhood.argtypes = [ctypes.c_int64, ctypes.c_int, _u8p]
     L.orc_must_check.restype = None
     L.orc_must_check.argtypes = [ctypes.c_int64, _i64p, _i32p, _u8p, _u8p]
     L.orc_exact_centralities.restype = ctypes.c_int
@@ -313,3 +315,26 @@ def run_stats(offsets, targets, b: int, seeds, which: str, weights=None):
     vals = np.array(vals)
     sd = vals.std(axis=0, ddof=1) if len(seeds) > 1 else np.zeros(vals.shape[1])
     return vals.mean(axis=0), sd
+
+
+def neighbourhood(regs: np.ndarray, b: int) -> float:
+    """N(t) = sum over nodes of size(c_t[v]) for the counters c_t given."""
+    regs = np.ascontiguousarray(regs, dtype=np.uint8)
+    return float(lib().orc_neighbourhood(regs.shape[0], b, _p(regs, _u8p)))
+
+
+def neighbourhood_function(offsets, targets, b: int, seed: int, weights=None):
+    """N(0), N(1), ..., N(T) along a whole run of Algorithm 2 (T = the
+    iteration count): the estimate after every iteration."""
+    off, tgt = _csr(offsets, targets)
+    n = off.size - 1
+    c = init(n, b, seed) if weights is None else init_weighted(n, b, seed, weights)
+    sumd, harm = np.zeros(n), np.zeros(n)
+    out = [neighbourhood(c, b)]
+    t = 0
+    while True:
+        c, _, k = step(off, tgt, b, t, c, sumd, harm)
+        out.append(neighbourhood(c, b))
+        t += 1
+        if k == 0:
+            return np.array(out)

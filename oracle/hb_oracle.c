@@ -289,6 +289,17 @@ int orc_run(int64_t n, const int64_t *offsets, const int32_t *targets,
                       NULL, steps, changed_hist);
 }
 
+/* The neighbourhood function at t (Sec. 4: the single value per iteration
+ * that ANF and HyperANF aggregate, N(t) = sum over x of |B(x,t)|),
+ * estimated by adding size() of every counter c_t[v] in node order. */
+double orc_neighbourhood(int64_t n, int b, const uint8_t *c)
+{
+    int64_t p = (int64_t)1 << b;
+    double N = 0.0;
+    for (int64_t v = 0; v < n; ++v) N = N + orc_size(c + v * p, b);
+    return N;
+}
+
 /* Sec. 3 from the Sec. 5 accumulators:
  *   reachable = size(c[v])              (coreachable set, x included)
  *   closeness = 1 / sumd                (0 when no other node coreaches x)

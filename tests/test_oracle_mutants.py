@@ -51,6 +51,8 @@ MUTANTS = {
                                "return (d >= 0 && d < len) ? table[d] : 0.0;"),
     "discount_not_accumulated": ("if (disc) disc[v] = disc[v] + fdist * delta;",
                                  "if (disc) disc[v] = fdist * delta;"),
+    "neighbourhood_skips_a_node": ("for (int64_t v = 0; v < n; ++v) N = N + orc_size(c + v * p, b);",
+                                   "for (int64_t v = 1; v < n; ++v) N = N + orc_size(c + v * p, b);"),
 }
 
 
@@ -73,6 +75,7 @@ def _checks(orc):
     yield lambda: tw.test_weighted_counters_equal_hll_of_replica_balls(orc, "dag", 4, 42)
     yield lambda: tw.test_weighted_discounted_accumulators_closed_form(orc, "log", 10, 8, 1)
     yield lambda: tw.test_discounts_that_reduce_to_the_accumulators(orc, "dag")
+    yield lambda: tw.test_neighbourhood_function_closed_form(orc)
 
 
 def test_unmutated_oracle_passes_every_check(orc):

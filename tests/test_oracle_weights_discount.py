@@ -185,3 +185,54 @@ def test_weighted_reach_within_counter_error(orc):
     e = np.array(errs)
     assert np.median(np.sqrt((e ** 2).mean(axis=0))) <= 1.15 * bound
     assert abs(np.median(e.mean(axis=0))) <= 3 * bound / math.sqrt(K)
+
+
+# ------------------------------------------------ neighbourhood function --
+
+@pytest.mark.parametrize("name", ["path", "dag", "star_in", "loops_dups", "zipf"])
+def test_neighbourhood_function_is_sum_of_ball_counters(orc, name):
+    """N(t) is the sum over nodes of size() of the HyperLogLog counter of the
+    BFS ball of radius t, at every t of the run."""
+    off, tgt = SMALL[name]
+    n = off.size - 1
+    b, seed = 6, 21
+    nf = orc.neighbourhood_function(off, tgt, b, seed)
+    adj = brute.adjacency(off, tgt)
+    dists = [brute.bfs_dist(adj, x) for x in range(n)]
+    for t, N in enumerate(nf):
+        balls = np.array([brute.hll_of_set(brute.ball(dists[v], t), b, seed) for v in range(n)])
+        expect = sum(orc.size(balls[v], b) for v in range(n))
+        assert N == pytest.approx(expect, rel=1e-13)
+
+
+def test_neighbourhood_function_closed_form(orc):
+    """Every node in its own register: N(t) is the sum over nodes of
+    p ln(p/(p - |B(v,t)|)) with exact ball sizes, non-decreasing in t."""
+    n, b = 20, 9
+    p = 1 << b
+    rng = np.random.default_rng(4)
+    edges = [(int(u), int(v)) for u, v in rng.integers(0, n, size=(2 * n, 2)) if u != v]
+    off, tgt = graphs.from_edges(n, edges).numpy()
+    seed = _distinct_items_seed(n, b, 300)
+    nf = orc.neighbourhood_function(off, tgt, b, seed)
+    adj = brute.adjacency(off, tgt)
+    dists = [brute.bfs_dist(adj, x) for x in range(n)]
+    for t, N in enumerate(nf):
+        expect = sum(brute.linear_counting(p, len(brute.ball(dists[v], t))) for v in range(n))
+        assert N == pytest.approx(expect, rel=1e-12)
+    assert np.all(np.diff(nf) >= 0)
+
+
+def test_neighbourhood_function_accuracy(orc):
+    """Against the exact neighbourhood function (the sum of BFS ball
+    sizes): within the counter's error bound at every t (Sec. 4.1)."""
+    off, tgt = graphs.plain_graph(n=2000, seed=5).numpy()
+    n = off.size - 1
+    adj = brute.adjacency(off, tgt)
+    dists = [brute.bfs_dist(adj, x) for x in range(n)]
+    b = 8
+    nf = orc.neighbourhood_function(off, tgt, b, 77)
+    for t in range(1, len(nf)):
+        exact = sum(sum(1 for d in dv.values() if d <= t) for dv in dists)
+        # a sum of per-node estimates: the relative error stays below one counter's
+        assert abs(nf[t] / exact - 1) < 3 * 1.06 / math.sqrt(1 << b), t
