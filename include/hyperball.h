@@ -64,6 +64,8 @@ typedef enum {
 #define HB_PULL_GATHER        0x20u /* frontier iterations gather every successor of the nodes they
                                        recompute, instead of pushing last iteration's changed
                                        counters along the reverse CSR (results are the same) */
+#define HB_NEIGHBOURHOOD      0x40u /* record the neighbourhood function N(t) after every iteration
+                                       (hb_get_neighbourhood) */
 
 /* hb_options.frontier: how the nodes to recompute are chosen each step
  * (Sec. 5 / 5.1 modification tracking).  Results never depend on it. */
@@ -226,9 +228,24 @@ hb_status hb_set_discount(hb_graph *g, const double *f, int32_t len);
  * device).  HB_ERR_STATE if no discount is set. */
 hb_status hb_get_discounted(hb_graph *g, double *out);
 
+/* The neighbourhood function (the aggregate that ANF and HyperANF compute
+ * and that HyperBall generalises, Sec. 4): N(t) = sum over nodes x of
+ * |B(x,t)|, the number of pairs (x,y) with y reachable from x along the
+ * scanned arcs in at most t steps, estimated as the sum of size() over all
+ * counters after t iterations (weighted under hb_set_weights).  Needs
+ * HB_NEIGHBOURHOOD at creation: after initialisation and after every
+ * iteration the library sums the nodes' cached estimates on the device in
+ * a fixed order (one extra read of n estimates per iteration).
+ * out[t] = N(t) for t = 0..T, T the iterations done, at most cap values
+ * (host memory); *len (may be NULL) receives T+1.  N(T) - N(T-1) is the
+ * number of pairs at distance T.  HB_ERR_STATE without the flag.
+ * Single-graph handles only. */
+hb_status hb_get_neighbourhood(hb_graph *g, double *out, int32_t cap, int32_t *len);
+
 /* Checkpoint: write t, counters, last frontier and accumulators (and the
- * graph, the weights and the discount) to a file; hb_load rebuilds a
- * handle that continues exactly where the saved one stopped. */
+ * graph, the weights, the discount and the neighbourhood function) to a
+ * file; hb_load rebuilds a handle that continues exactly where the saved
+ * one stopped. */
 hb_status hb_save(hb_graph *g, const char *path);
 hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out);
 

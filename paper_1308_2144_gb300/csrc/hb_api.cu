@@ -120,6 +120,7 @@ hb_status setup_shared(hb_graph *g) {
     a.lc32 = lc32;
     int32_t *dense_list = nullptr;
     if (!g->relabel) dense_list = M.alloc<int32_t>(g->n_pos);
+    if (g->track_nf) g->nf_part = M.alloc<double>(kNfBlocks);
     if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (HyperBall tables)");
 
     const double alpha = hll_alpha(P);
@@ -333,6 +334,11 @@ hb_status init_state(hb_graph *g, uint64_t seed) {
     g->seed = seed;
     cudaError_t e = launch_init(g->a, g->perm, seed, g->fp32, g->s, g->wfirst);
     g->launches += g->n > 0 ? 2 : 1;
+    if (e == cudaSuccess && g->track_nf) {
+        e = launch_estimate_sum(g->a.ecache, g->fp32, g->n, g->nf_part, g->ctr, g->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->s);
+        g->launches += 2;
+    }
     g->kernel_launches = 0;
     g->kernel_ms = g->kernel_bytes = 0.0;
     g->push_launches = 0;
@@ -343,6 +349,8 @@ hb_status init_state(hb_graph *g, uint64_t seed) {
     g->converged = false;
     g->last_changed = g->last_nodes = g->last_arcs = g->total_arcs = 0;
     g->last_sparse = 0;
+    g->nf.clear();
+    if (g->track_nf) g->nf.push_back(g->ctr_host->nsum);
     return HB_OK;
 }
 
@@ -376,6 +384,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     g->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
     g->relabel = (o.flags & HB_NO_RELABEL) == 0;
     g->profile = (o.flags & HB_PROFILE) != 0;
+    g->track_nf = (o.flags & HB_NEIGHBOURHOOD) != 0;
     if (g->profile) {
         for (cudaEvent_t &x : g->ev)
             if (cudaEventCreate(&x) != cudaSuccess) {
@@ -535,6 +544,10 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     if (st != HB_OK) return st;
     cudaError_t e = launch_iteration(g->a, g->y, g->fp32, g->step_grid, g->s, g->profile ? g->ev : nullptr,
                                      &g->launches);
+    if (e == cudaSuccess && g->track_nf) {
+        e = launch_estimate_sum(g->a.ecache, g->fp32, g->n, g->nf_part, g->ctr, g->s);
+        g->launches += 2;
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g->ctr_host, g->ctr, sizeof(Counters), cudaMemcpyDeviceToHost, g->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
@@ -550,6 +563,7 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     g->t = c.steps_done;
     g->last_changed = (int64_t)c.n_changed;
     g->last_sparse = c.mode;
+    if (g->track_nf) g->nf.push_back(c.nsum);
     if (c.mode == 1) {
         int64_t nodes = 0;
         for (int k = 0; k < kSegs; ++k) nodes += (int64_t)c.fill[k];
@@ -862,6 +876,17 @@ hb_status hb_get_discounted(hb_graph *g, double *out) {
     return HB_OK;
 }
 
+hb_status hb_get_neighbourhood(hb_graph *g, double *out, int32_t cap, int32_t *len) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    if (!g->track_nf) return fail(HB_ERR_STATE, "the handle was created without HB_NEIGHBOURHOOD");
+    if (cap < 0 || (cap > 0 && !out)) return fail(HB_ERR_INVALID, "out is NULL or cap < 0");
+    const int32_t k = (int32_t)g->nf.size();
+    for (int32_t i = 0; i < k && i < cap; ++i) out[i] = g->nf[i];
+    if (len) *len = k;
+    return HB_OK;
+}
+
 // ------------------------------------------------------------ checkpoint --
 
 namespace {
@@ -875,6 +900,7 @@ struct SaveHeader {
     int32_t converged, frontier;
     int64_t total_arcs;
     int32_t weighted, flen;   // Sec. 6 replica starts and Sec. 7 discount follow when set
+    int32_t nf_len, pad;      // recorded neighbourhood function values follow when set
 };
 
 bool write_dev(FILE *f, const void *dev, size_t bytes, cudaStream_t s) {
@@ -899,7 +925,8 @@ hb_status hb_save(hb_graph *g, const char *path) {
     FILE *f = fopen(path, "wb");
     if (!f) return fail(HB_ERR_INVALID, std::string("cannot open ") + path);
     SaveHeader h{kMagic, g->n, g->m, g->b, g->fp32, g->relabel, g->t, g->seed,
-                 g->converged, g->opt.frontier, g->total_arcs, g->wfirst ? 1 : 0, g->a.flen};
+                 g->converged, g->opt.frontier, g->total_arcs, g->wfirst ? 1 : 0, g->a.flen,
+                 g->track_nf ? (int32_t)g->nf.size() : -1, 0};
     const size_t P = (size_t)1 << g->b;
     const size_t n = (size_t)g->n;
     bool ok = fwrite(&h, sizeof(h), 1, f) == 1;
@@ -926,6 +953,8 @@ hb_status hb_save(hb_graph *g, const char *path) {
         ok = ok && write_dev(f, g->ftab, sizeof(double) * g->a.flen, g->s);
         ok = ok && write_dev(f, g->disc, sizeof(double) * n, g->s);
     }
+    if (g->track_nf && !g->nf.empty())
+        ok = ok && fwrite(g->nf.data(), sizeof(double), g->nf.size(), f) == g->nf.size();
     fclose(f);
     if (!ok) return fail(HB_ERR_CUDA, "checkpoint write failed");
     return HB_OK;
@@ -953,6 +982,7 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     g->s = static_cast<cudaStream_t>(o.stream);
     g->fp32 = h.fp32 != 0;
     g->relabel = h.relabel != 0;
+    g->track_nf = h.nf_len >= 0;
     const size_t P = (size_t)1 << g->b, n = (size_t)g->n;
     DevMem &M = g->mem;
     g->off = M.alloc<int64_t>(n + 1);
@@ -997,6 +1027,10 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
         g->a.disc = g->disc;
         g->a.ftab = g->ftab;
         g->a.flen = h.flen;
+    }
+    if (ok && h.nf_len >= 0) {
+        g->nf.assign((size_t)h.nf_len, 0.0);
+        ok = fread(g->nf.data(), sizeof(double), (size_t)h.nf_len, f) == (size_t)h.nf_len;
     }
     fclose(f);
     if (!ok) { delete g; return fail(HB_ERR_INVALID, "truncated checkpoint"); }

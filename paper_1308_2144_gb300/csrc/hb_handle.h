@@ -93,6 +93,9 @@ struct hb_graph {
     int64_t *wfirst = nullptr;     // Sec. 6: first replica item of each caller node (n+1), or null
     double *disc = nullptr;        // Sec. 7: discounted accumulator (n), or null
     double *ftab = nullptr;        // its discount table
+    bool track_nf = false;         // HB_NEIGHBOURHOOD: N(t) after every iteration
+    double *nf_part = nullptr;     // block partials of the estimate sum
+    std::vector<double> nf;        // N(0), N(1), ... of the current run
     Counters *ctr = nullptr;
     Counters *ctr_host = nullptr;
     int64_t seg_count[kSegs] = {0};

@@ -98,6 +98,7 @@ struct Counters {
     int32_t steps_done;                // iterations completed
     int32_t converged;
     unsigned long long err;            // nonzero: a device-side check failed
+    double nsum;                       // sum of the nodes' cached estimates (neighbourhood function)
 };
 
 // Everything the step kernels read, passed by value.  Buffers that
@@ -405,6 +406,12 @@ cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, in
 // nodes, whose replicas are the items wfirst[u] .. wfirst[u+1]-1.
 cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, bool fp32,
                         cudaStream_t s, const int64_t *wfirst = nullptr);
+// Neighbourhood function: the sum of the n cached estimates (float or
+// double) into ctr->nsum, in a fixed order (grid kNfBlocks, partials in
+// part[kNfBlocks]) so that the result does not vary between runs.
+constexpr int kNfBlocks = 608;
+cudaError_t launch_estimate_sum(const void *ecache, bool fp32, int64_t n, double *part, Counters *ctr,
+                                cudaStream_t s);
 // First replica item of every node: wfirst = exclusive prefix sums of the
 // n weights w (device), n+1 entries; sets bit 1 of *err if a weight lies
 // outside [0, 2^31).

@@ -33,6 +33,36 @@ __global__ void lc_tables_kernel(double *lc64, float *lc32, int P) {
     }
 }
 
+// ------------------------------------------------ neighbourhood function --
+
+// Each block sums a fixed strided set of nodes, then a fixed tree in
+// shared memory; one block then sums the block partials the same way.
+__device__ __forceinline__ double block_tree_sum(double x, double *sh) {
+    sh[threadIdx.x] = x;
+    __syncthreads();
+    for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    return sh[0];
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) estimate_partials_kernel(const void *ecache, int64_t n, double *part) {
+    __shared__ double sh[256];
+    double x = 0.0;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        x += F32 ? (double)static_cast<const float *>(ecache)[v] : static_cast<const double *>(ecache)[v];
+    const double tot = block_tree_sum(x, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) estimate_total_kernel(const double *part, int np, Counters *ctr) {
+    __shared__ double sh[1024];
+    const double tot = block_tree_sum((int)threadIdx.x < np ? part[threadIdx.x] : 0.0, sh);
+    if (threadIdx.x == 0) ctr->nsum = tot;
+}
+
 // ---------------------------------------------------------------- init --
 
 // Algorithm 2, first loop: add(c[v], v) into an empty counter, in both
@@ -483,6 +513,14 @@ cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, b
                                                                 a.b, seed);
     if (fp32) init_nodes_kernel<true><<<grid_for(a.n, 256), 256, 0, s>>>(a, perm, seed);
     else init_nodes_kernel<false><<<grid_for(a.n, 256), 256, 0, s>>>(a, perm, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate_sum(const void *ecache, bool fp32, int64_t n, double *part, Counters *ctr,
+                                cudaStream_t s) {
+    if (fp32) estimate_partials_kernel<true><<<kNfBlocks, 256, 0, s>>>(ecache, n, part);
+    else estimate_partials_kernel<false><<<kNfBlocks, 256, 0, s>>>(ecache, n, part);
+    estimate_total_kernel<<<1, 1024, 0, s>>>(part, kNfBlocks, ctr);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,7 @@ HB_FP32_ESTIMATE = 0x4
 HB_NO_RELABEL = 0x8
 HB_PROFILE = 0x10
 HB_PULL_GATHER = 0x20
+HB_NEIGHBOURHOOD = 0x40
 
 FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
 
@@ -44,6 +45,7 @@ HB_REQ_QUEUED, HB_REQ_RUNNING, HB_REQ_DONE, HB_REQ_FAILED = 0, 1, 2, 3
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
            "hb_get_info", "hb_reset", "hb_set_weights", "hb_set_discount", "hb_get_discounted",
+           "hb_get_neighbourhood",
            "hb_save", "hb_load", "hb_destroy", "hb_last_error",
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
@@ -140,6 +142,8 @@ def load():
         L.hb_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
         L.hb_reset.restype = st
         L.hb_reset.argtypes = [_vp, ctypes.c_uint64]
+        L.hb_get_neighbourhood.restype = st
+        L.hb_get_neighbourhood.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.hb_set_weights.restype = st
         L.hb_set_weights.argtypes = [_vp, _vp]
         L.hb_set_discount.restype = st
@@ -250,12 +254,14 @@ def _stream_ptr(stream):
 
 
 def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
-                 max_steps=1 << 20, stream=None, profile=False, pull_gather=False) -> Options:
+                 max_steps=1 << 20, stream=None, profile=False, pull_gather=False,
+                 neighbourhood=False) -> Options:
     o = Options()
     load().hb_default_options(ctypes.byref(o))
     o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
                | (HB_FP32_ESTIMATE if fp32 else 0) | (0 if relabel else HB_NO_RELABEL)
-               | (HB_PROFILE if profile else 0) | (HB_PULL_GATHER if pull_gather else 0))
+               | (HB_PROFILE if profile else 0) | (HB_PULL_GATHER if pull_gather else 0)
+               | (HB_NEIGHBOURHOOD if neighbourhood else 0))
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
     o.max_steps = int(max_steps)
     o.stream = _stream_ptr(stream)
@@ -330,6 +336,15 @@ def hb_get_discounted(h, out):
     _check(load().hb_get_discounted(h, _ptr(out)))
 
 
+def hb_get_neighbourhood(h) -> np.ndarray:
+    """N(0), ..., N(T) recorded so far (handle created with neighbourhood=True)."""
+    k = ctypes.c_int32()
+    _check(load().hb_get_neighbourhood(h, None, 0, ctypes.byref(k)))
+    out = np.zeros(k.value, dtype=np.float64)
+    _check(load().hb_get_neighbourhood(h, _ptr(out), k.value, ctypes.byref(k)))
+    return out
+
+
 def hb_tune(h) -> int:
     """Autotune the degree-class sizing; returns the chosen arcs per slot."""
     a = ctypes.c_int32()
@@ -394,6 +409,8 @@ class HyperBallBatch:
     def runs(cls, offsets, targets, n: int, log2m: int, seeds, **opts) -> "HyperBallBatch":
         """Multiple runs of one graph (Sec. 5): run r uses seeds[r]; the runs
         share one device copy of the graph."""
+        if offsets.dtype in (torch.int32, np.int32):   # the entry point takes int64 offsets
+            offsets = offsets.to(torch.int64) if isinstance(offsets, torch.Tensor) else offsets.astype(np.int64)
         self = cls.__new__(cls)
         self._keep = [offsets, targets]
         self.k = len(seeds)
@@ -596,6 +613,10 @@ class HyperBall:
         if f is not None and not isinstance(f, torch.Tensor):
             f = np.ascontiguousarray(f, dtype=np.float64)
         hb_set_discount(self._h, f)
+
+    def neighbourhood(self) -> np.ndarray:
+        """The neighbourhood function N(0), ..., N(t) of the run so far."""
+        return hb_get_neighbourhood(self._h)
 
     def discounted(self, device="cuda") -> torch.Tensor:
         out = self._out(self.n, torch.float64, device)

@@ -189,3 +189,56 @@ def test_checkpoint_keeps_weights_and_discount(orc, tmp_path):
     close(out.cpu().numpy(), ref.disc)
     hbl.hb_destroy(h2)
     hb.close()
+
+
+# ------------------------------------------------ neighbourhood function --
+
+@pytest.mark.parametrize("b,frontier", [(4, "auto"), (8, "off"), (6, "pull")])
+def test_neighbourhood_function(orc, b, frontier):
+    """N(t) after every iteration equals the oracle's sum of size() over all
+    counters within 1e-9, in the same order of magnitude of terms; the
+    device sum has a fixed order, so two runs agree bit for bit."""
+    off, tgt = graphs.plain_graph(n=10_000, seed=3).numpy()
+    n = off.size - 1
+    ref = orc.neighbourhood_function(off, tgt, b, 42)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=b, seed=42, n=n, frontier=frontier, neighbourhood=True)
+    hb.run()
+    nf = hb.neighbourhood()
+    assert nf.size == ref.size
+    close(nf, ref)
+    hb.reset(42)
+    hb.run()
+    assert np.array_equal(hb.neighbourhood(), nf)
+    hb.close()
+
+
+def test_neighbourhood_function_weighted_fp32_checkpoint(orc, tmp_path):
+    off, tgt = graphs.rmat_graph(scale=12, edge_factor=8, seed=5).numpy()
+    n = off.size - 1
+    w = weights_of(n, 3)
+    ref = orc.neighbourhood_function(off, tgt, 6, 7, weights=w)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=6, seed=7, n=n, neighbourhood=True)
+    hb.set_weights(w)
+    hb.step()
+    hb.step()
+    path = str(tmp_path / "nf.ckpt")
+    hb.save(path)
+    hb.run()
+    close(hb.neighbourhood(), ref)
+    h2 = hbl.hb_load(path)
+    hbl.hb_run_to_fixpoint(h2)
+    assert np.array_equal(hbl.hb_get_neighbourhood(h2), hb.neighbourhood())
+    hbl.hb_destroy(h2)
+    hb.close()
+    # FP32 estimates: each within 2^-22 relative, so the sum too
+    h32 = hbl.HyperBall(*to_dev(off, tgt), log2m=6, seed=7, n=n, fp32=True, neighbourhood=True)
+    h32.set_weights(w)
+    h32.run()
+    got = h32.neighbourhood()
+    assert got.size == ref.size and np.all(np.abs(got / ref - 1) < 2.0 ** -21)
+    h32.close()
+    plain = hbl.HyperBall(*to_dev(off, tgt), log2m=6, seed=7, n=n)
+    with pytest.raises(hbl.HBError) as e:
+        plain.neighbourhood()
+    assert e.value.status == hbl.HB_ERR_STATE
+    plain.close()
