@@ -242,6 +242,47 @@ hb_status hb_get_discounted(hb_graph *g, double *out);
  * Single-graph handles only. */
 hb_status hb_get_neighbourhood(hb_graph *g, double *out, int32_t cap, int32_t *len);
 
+/* Several runs of one graph in one handle (Sec. 5: HyperBall repeated with
+ * independent hash seeds, so that the spread of the estimates gives their
+ * empirical standard deviation and their mean a tighter estimate).  Each
+ * node's row holds `runs` counters of p = 2^log2m registers, run r in
+ * bytes [r p, (r+1) p), hashed with seeds[r] (host or device memory, runs
+ * entries).  The register-wise maximum never mixes bytes, so one union over
+ * a row is every run's union: each iteration streams the graph once for all
+ * runs and every gathered row is runs * p contiguous bytes.  An iteration
+ * changes a node if any of its runs changes; the handle reaches its
+ * fixpoint when every run has, and each run's counters, accumulators and
+ * iteration count equal those of hb_create with its seed run alone.
+ *   runs: a power of two from 2 to 64; log2m: 4..9; runs * p <= 4096.
+ *   CSR and options as for hb_create, except HB_NEIGHBOURHOOD.
+ * hb_step, hb_run_to_fixpoint, hb_reset (the seeds are kept; the argument
+ * is ignored), hb_tune, hb_set_class_sizing, hb_get_frontier, hb_get_info
+ * and hb_destroy work as for one run; hb_get_registers returns rows of
+ * runs * p bytes.  Results come from the hb_get_run_* calls below;
+ * hb_get_centralities, hb_get_accumulators, weights, discounts and
+ * checkpoints return HB_ERR_STATE on such a handle.  Device memory: two
+ * rows of runs * p bytes and about 20 * runs + 20 bytes per node. */
+hb_status hb_create_runs(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
+                         int log2m, int32_t runs, const uint64_t *seeds, const hb_options *opt,
+                         hb_graph **out);
+
+/* Per run r: its iteration count, the final unchanged iteration included
+ * (steps[r] for every run; while a run is still changing, the iterations
+ * executed so far). */
+hb_status hb_get_run_steps(hb_graph *g, int32_t *steps);
+
+/* Run r's Sec. 3 centralities and Sec. 5 accumulators, as
+ * hb_get_centralities and hb_get_accumulators for one run. */
+hb_status hb_get_run_centralities(hb_graph *g, int32_t run, double *closeness, double *harmonic,
+                                  double *lin, double *reachable);
+hb_status hb_get_run_accumulators(hb_graph *g, int32_t run, double *sumd, double *harm);
+
+/* Per-node mean and empirical standard deviation (sample form, divisor
+ * runs - 1) over the runs of one centrality (which = 0 closeness,
+ * 1 harmonic, 2 Lin, 3 reachable), n doubles each in the caller's order,
+ * host or device; either may be NULL. */
+hb_status hb_get_run_stats(hb_graph *g, int32_t which, double *mean, double *sd);
+
 /* Checkpoint: write t, counters, last frontier and accumulators (and the
  * graph, the weights, the discount and the neighbourhood function) to a
  * file; hb_load rebuilds a handle that continues exactly where the saved

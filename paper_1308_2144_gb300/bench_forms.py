@@ -21,13 +21,13 @@ on the same arrival stream.  Prints one JSON line per server: p50/p99
 latency from arrival to results in host memory, and arc-updates/s.
 
 runs: the paper's multiple runs (Sec. 5) on the encyclopedia-like graph
-(log2m 6): R runs with seeds 42..42+R-1 in one batch sharing one copy of the
-graph (hb_batch_create_runs, hb_batch_run), then the per-node mean and
-standard deviation of all four centralities, versus the same R runs one
-after the other on one handle (hb_reset, hb_run_to_fixpoint,
-hb_get_centralities, statistics of the R results on the GPU).  Prints one
-JSON line: time for all R runs and their statistics both ways, and
-arc-updates/s.
+(log2m 6): R runs with seeds 42..42+R-1, each to its fixpoint, then the
+per-node mean and standard deviation of all four centralities, three ways:
+one handle whose rows hold every run (hb_create_runs), a batch of R runs
+sharing one copy of the graph (hb_batch_create_runs), and the R runs one
+after the other on one handle (statistics of the R results with torch).
+Prints one JSON line: time of each, and arc-updates/s counted per run (the
+arcs each run scans, summed over the runs).
 """
 from __future__ import annotations
 
@@ -179,21 +179,48 @@ def serve_main(args):
 
 
 def runs_main(args):
-    g = graphs.enwiki_graph(device="cuda")
-    n, b = g.n, 6
+    if args.graph == "web":
+        g = graphs.web_graph(device="cuda")
+        b, args.fp32 = 4, True
+        desc = "web-like (R-MAT scale 28, 268,435,456 nodes, edge factor 16), transpose, log2m 4, FP32 estimates"
+    else:
+        g = graphs.enwiki_graph(device="cuda")
+        b = 6
+        desc = "encyclopedia-like (R-MAT scale 23, 4,206,785 nodes), transpose, log2m 6"
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    n = g.n
     seeds = [42 + r for r in range(args.runs)]
-    batch = hbl.HyperBallBatch.runs(g.offsets, g.targets, n, b, seeds, fp32=args.fp32)
-    outs = {k: (torch.empty(n, dtype=torch.float64, device="cuda"),
-                torch.empty(n, dtype=torch.float64, device="cuda")) for k in hbl.HyperBallBatch.CENTRALITIES}
+    names = hbl.HyperBallBatch.CENTRALITIES
     lib = hbl.load()
+    out = {k: (torch.empty(n, dtype=torch.float64, device="cuda"),
+               torch.empty(n, dtype=torch.float64, device="cuda")) for k in names}
+
+    # one handle whose rows hold every run (hb_create_runs)
+    wide = hbl.HyperBall.runs(g.offsets, g.targets, b, seeds, n=n, fp32=args.fp32)
+
+    def one_handle():
+        hbl.hb_reset(wide._h, 0)
+        wide.run()
+        for w, k in enumerate(names):
+            hbl._check(lib.hb_get_run_stats(wide._h, w, hbl._ptr(out[k][0]), hbl._ptr(out[k][1])))
+        return wide.info()["total_arcs"], wide.info()["t"]
+
+    # a batch of R runs sharing one copy of the graph (hb_batch_create_runs);
+    # left out on the web-like graph, where it would hold a further copy of
+    # every run's state and adds nothing to the comparison
+    batch = None
+    if args.graph != "web":
+        batch = hbl.HyperBallBatch.runs(g.offsets, g.targets, n, b, seeds, fp32=args.fp32)
 
     def batched():
         batch.reset(seeds)
         iters = batch.run()
-        for w, k in enumerate(hbl.HyperBallBatch.CENTRALITIES):
-            hbl._check(lib.hb_batch_get_run_stats(batch._h, w, hbl._ptr(outs[k][0]), hbl._ptr(outs[k][1])))
-        return iters
+        for w, k in enumerate(names):
+            hbl._check(lib.hb_batch_get_run_stats(batch._h, w, hbl._ptr(out[k][0]), hbl._ptr(out[k][1])))
+        return batch.totals()[2], iters
 
+    # the same runs one after the other on one handle, statistics with torch
     solo = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seeds[0], n=n, fp32=args.fp32)
     vals = torch.empty((4, args.runs, n), dtype=torch.float64, device="cuda")
 
@@ -205,33 +232,41 @@ def runs_main(args):
             hbl.hb_get_centralities(solo._h, vals[0, r], vals[1, r], vals[2, r], vals[3, r])
             arcs += solo.info()["total_arcs"]
         torch.std_mean(vals, dim=1)
-        return arcs
+        return arcs, None
 
-    batched()
-    one_at_a_time()
-    bt, st = [], []
+    arms = {"one_handle": one_handle, "batch": batched, "one_at_a_time": one_at_a_time}
+    if batch is None:
+        del arms["batch"]
+    best = {k: float("inf") for k in arms}
+    work = {}
+    for f in arms.values():
+        f()
     for _ in range(args.repeat):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        iters = batched()
-        torch.cuda.synchronize()
-        bt.append(time.perf_counter() - t)
-        t = time.perf_counter()
-        solo_arcs = one_at_a_time()
-        torch.cuda.synchronize()
-        st.append(time.perf_counter() - t)
-    _, _, arcs = batch.totals()
-    batch.close()
+        for k, f in arms.items():
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            work[k] = f()
+            torch.cuda.synchronize()
+            best[k] = min(best[k], time.perf_counter() - t)
+    wide.close()
+    if batch is not None:
+        batch.close()
     solo.close()
-    b_s, s_s = min(bt), min(st)
-    print(json.dumps({
-        "form": "runs", "graph": "encyclopedia-like (R-MAT scale 23, 4,206,785 nodes), transpose, log2m 6",
-        "runs": args.runs, "n": n, "m": g.m, "batch_ms": round(1e3 * b_s, 3), "batch_iterations": iters,
-        "batch_arc_updates_per_s": arcs / b_s, "one_at_a_time_ms": round(1e3 * s_s, 3),
-        "one_at_a_time_arc_updates_per_s": solo_arcs / s_s, "speedup": s_s / b_s,
-        "estimate": "fp32" if args.fp32 else "fp64",
-        "includes": "all runs to their fixpoints and the per-node mean and std of the four centralities"}),
-        flush=True)
+    # arc-updates: arcs scanned per run summed over the runs (the one-handle
+    # form scans each arc once for all runs of a row)
+    solo_arcs = work["one_at_a_time"][0]
+    line = {"form": "runs", "graph": desc,
+            "runs": args.runs, "n": n, "m": g.m, "estimate": "fp32" if args.fp32 else "fp64",
+            "includes": "all runs to their fixpoints and the per-node mean and std of the four centralities"}
+    for k in arms:
+        line[f"{k}_ms"] = round(1e3 * best[k], 3)
+        line[f"{k}_run_arc_updates_per_s"] = solo_arcs / best[k]
+    line["one_handle_iterations"] = work["one_handle"][1]
+    line["one_handle_speedup"] = best["one_at_a_time"] / best["one_handle"]
+    if "batch" in arms:
+        line["batch_iterations"] = work["batch"][1]
+        line["batch_speedup"] = best["one_at_a_time"] / best["batch"]
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -255,6 +290,7 @@ def main():
     s.add_argument("--fp32", action="store_true")
     r = sub.add_parser("runs")
     r.add_argument("--runs", type=int, default=16)
+    r.add_argument("--graph", choices=["enwiki", "web"], default="enwiki")
     r.add_argument("--repeat", type=int, default=3)
     r.add_argument("--fp32", action="store_true")
     args = ap.parse_args()

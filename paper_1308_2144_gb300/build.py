@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhyperball.so")
-SOURCES = ["hb_build.cu", "hb_step.cu", "hb_api.cu", "hb_noalloc.cu", "hb_batch.cu"]
+SOURCES = ["hb_build.cu", "hb_step.cu", "hb_runs.cu", "hb_api.cu", "hb_noalloc.cu", "hb_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2", "-Xptxas", "-O3", "-I", os.path.join(ROOT, "include")]

@@ -83,7 +83,8 @@ cudaError_t to_caller(void *dst, const void *src, size_t bytes, cudaStream_t s) 
 hb_status setup_shared(hb_graph *g) {
     cudaStream_t s = g->s;
     const int64_t n = g->n, m = g->m;
-    const int P = 1 << g->b;
+    const int P = 1 << g->b;     // bytes of a row
+    const int Pe = 1 << g->gb;   // registers of one run: the estimator's p
     cudaError_t e = count_degree_segments(g->off, n, g->y, g->seg_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "degree segments");
     int64_t seg_begin[kSegs];
@@ -114,8 +115,8 @@ hb_status setup_shared(hb_graph *g) {
     a.plan_dense = M.alloc<Plan>(1);
     a.owner_dense = M.alloc<int32_t>(g->heavy_total);
     a.cstart_dense = M.alloc<int64_t>(g->seg_count[0] + 1);
-    double *lc64 = M.alloc<double>(P + 1);
-    float *lc32 = M.alloc<float>(P + 1);
+    double *lc64 = M.alloc<double>(Pe + 1);
+    float *lc32 = M.alloc<float>(Pe + 1);
     a.lc64 = lc64;
     a.lc32 = lc32;
     int32_t *dense_list = nullptr;
@@ -123,8 +124,8 @@ hb_status setup_shared(hb_graph *g) {
     if (g->track_nf) g->nf_part = M.alloc<double>(kNfBlocks);
     if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (HyperBall tables)");
 
-    const double alpha = hll_alpha(P);
-    a.c64 = std::ldexp(alpha * (double)P * (double)P, 64 - g->b);
+    const double alpha = hll_alpha(Pe);
+    a.c64 = std::ldexp(alpha * (double)Pe * (double)Pe, 64 - g->gb);
     a.c32 = (float)a.c64;
     // small-range switch: raw estimate <= 5p/2  <=>  X >= alpha 2^64 * 2/5
     const unsigned __int128 Y = (unsigned __int128)std::ldexp(alpha, 64);
@@ -138,6 +139,9 @@ hb_status setup_shared(hb_graph *g) {
         a.seg_hi[k] = g->y.hi[k];
     }
     a.b = g->b;
+    a.gb = g->gb;
+    a.lruns = g->lruns;
+    a.run_seeds = g->run_seeds;
     a.aps = g->y.aps;
     a.frontier = g->opt.frontier;
     a.sparse_frac = 0.25;
@@ -153,7 +157,7 @@ hb_status setup_shared(hb_graph *g) {
         M.release(fill);
     }
     a.dense_list = dense_list;
-    e = launch_lc_tables(lc64, lc32, P, s);
+    e = launch_lc_tables(lc64, lc32, Pe, s);
     if (e != cudaSuccess) return cuda_fail(e, "estimator tables");
     e = launch_dense_plan(a, g->y, g->seg_count, const_cast<Plan *>(a.plan_dense),
                           const_cast<int32_t *>(a.owner_dense), const_cast<int64_t *>(a.cstart_dense), s);
@@ -162,7 +166,7 @@ hb_status setup_shared(hb_graph *g) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-    g->step_grid = sms * step_blocks_per_sm(g->b, g->fp32);
+    g->step_grid = sms * (g->lruns ? runs_step_blocks_per_sm(g->b, g->fp32) : step_blocks_per_sm(g->b, g->fp32));
     // counters of the most gathered nodes (lowest ids after the degree sort)
     // that fit in half of L2, for the optional eviction hints
     const int64_t hot = g->relabel ? ((int64_t)l2 / 2) / P : 0;
@@ -183,9 +187,10 @@ size_t run_bytes(const hb_graph *g) {
     const int64_t big_cap = (m / kBigRdeg + 1) < n ? (m / kBigRdeg + 1) : (n > 0 ? n : 1);
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t b = 0;
+    const int64_t nr = n << g->lruns;   // (node, run) pairs
     b += 2 * up((size_t)n * P);
-    b += 2 * up(sizeof(double) * n);
-    b += up((g->fp32 ? sizeof(float) : sizeof(double)) * n);
+    b += 2 * up(sizeof(double) * nr);
+    b += up((g->fp32 ? sizeof(float) : sizeof(double)) * nr);
     b += up((size_t)n);
     b += up(sizeof(uint32_t) * ((n + 31) / 32 + 1));
     b += 2 * up(sizeof(int32_t) * n) + 2 * up(sizeof(int32_t) * big_cap);
@@ -209,9 +214,10 @@ hb_status setup_run(hb_graph *g) {
     StepArgs &a = g->a;
     a.regs[0] = take((size_t)n * P);
     a.regs[1] = take((size_t)n * P);
-    a.sumd = reinterpret_cast<double *>(take(sizeof(double) * n));
-    a.harm = reinterpret_cast<double *>(take(sizeof(double) * n));
-    a.ecache = take((g->fp32 ? sizeof(float) : sizeof(double)) * n);
+    const int64_t nr = n << g->lruns;
+    a.sumd = reinterpret_cast<double *>(take(sizeof(double) * nr));
+    a.harm = reinterpret_cast<double *>(take(sizeof(double) * nr));
+    a.ecache = take((g->fp32 ? sizeof(float) : sizeof(double)) * nr);
     a.changed = take((size_t)n);
     a.mustbits = reinterpret_cast<uint32_t *>(take(sizeof(uint32_t) * ((n + 31) / 32 + 1)));
     a.clist[0] = reinterpret_cast<int32_t *>(take(sizeof(int32_t) * n));
@@ -301,6 +307,7 @@ hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_
         g->own_ctr_host = false;
     }
     g->n = tmpl->n; g->m = tmpl->m; g->b = tmpl->b; g->y = tmpl->y;
+    g->gb = tmpl->gb; g->lruns = tmpl->lruns; g->run_seeds = tmpl->run_seeds;
     g->opt = tmpl->opt;
     g->s = s;
     g->fp32 = tmpl->fp32; g->relabel = tmpl->relabel; g->push_union = tmpl->push_union;
@@ -351,12 +358,16 @@ hb_status init_state(hb_graph *g, uint64_t seed) {
     g->last_sparse = 0;
     g->nf.clear();
     if (g->track_nf) g->nf.push_back(g->ctr_host->nsum);
+    g->run_last.assign(g->lruns ? (size_t)1 << g->lruns : 0, -1);
     return HB_OK;
 }
 
+// lruns > 0: 2^lruns runs of one graph per row (hb_create_runs), run r
+// hashed with seeds[r] (host or device memory).
 template <class OffT>
 hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
-                      uint64_t seed, const hb_options *opt, hb_graph **out) {
+                      uint64_t seed, const hb_options *opt, hb_graph **out, int lruns = 0,
+                      const uint64_t *seeds = nullptr) {
     if (!out) return fail(HB_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (log2m < kMinLog2m || log2m > kMaxLog2m)
@@ -377,8 +388,10 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     hb_graph *g = new hb_graph();
     g->n = n;
     g->m = m;
-    g->b = log2m;
-    g->y = make_layout(log2m);
+    g->b = log2m + lruns;
+    g->gb = log2m;
+    g->lruns = lruns;
+    g->y = make_layout(g->b);
     g->opt = o;
     g->s = static_cast<cudaStream_t>(o.stream);
     g->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
@@ -394,6 +407,12 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     }
     cudaStream_t s = g->s;
     DevMem &M = g->mem;
+    if (lruns) {
+        g->run_seeds = M.alloc<uint64_t>((size_t)1 << lruns);
+        if (!g->run_seeds) { delete g; return fail(HB_ERR_OOM, "out of device memory (run seeds)"); }
+        e = to_device(g->run_seeds, seeds, sizeof(uint64_t) << lruns, s);
+        if (e != cudaSuccess) { delete g; return cuda_fail(e, "run seeds"); }
+    }
 
     // 1. input CSR on the device (int64 offsets)
     const bool borrow = (o.flags & HB_BORROW_DEVICE_PTRS) != 0;
@@ -564,6 +583,8 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     g->last_changed = (int64_t)c.n_changed;
     g->last_sparse = c.mode;
     if (g->track_nf) g->nf.push_back(c.nsum);
+    for (size_t r = 0; r < g->run_last.size(); ++r)
+        if ((c.run_mask >> r) & 1ULL) g->run_last[r] = c.steps_done - 1;
     if (c.mode == 1) {
         int64_t nodes = 0;
         for (int k = 0; k < kSegs; ++k) nodes += (int64_t)c.fill[k];
@@ -621,6 +642,7 @@ hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic, 
                               double *reachable) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    if (g->lruns) return fail(HB_ERR_STATE, "a handle of several runs: use hb_get_run_centralities");
     const int64_t n = g->n;
     double *outs[4] = {closeness, harmonic, lin, reachable};
     double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -644,6 +666,7 @@ hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic, 
 hb_status hb_get_accumulators(hb_graph *g, double *sumd, double *harm) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    if (g->lruns) return fail(HB_ERR_STATE, "a handle of several runs: use hb_get_run_accumulators");
     const int64_t n = g->n;
     double *outs[2] = {sumd, harm};
     const double *src[2] = {g->a.sumd, g->a.harm};
@@ -780,6 +803,7 @@ hb_status hb_reset(hb_graph *g, uint64_t seed) {
 hb_status hb_set_weights(hb_graph *g, const int64_t *weights) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    if (g->lruns) return fail(HB_ERR_STATE, "weights need a handle of one run");
     DevMem &M = g->mem;
     if (!weights) {
         if (g->wfirst) M.release(g->wfirst);
@@ -825,6 +849,7 @@ hb_status hb_set_weights(hb_graph *g, const int64_t *weights) {
 hb_status hb_set_discount(hb_graph *g, const double *f, int32_t len) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    if (g->lruns) return fail(HB_ERR_STATE, "discounts need a handle of one run");
     if (len < 0) return fail(HB_ERR_INVALID, "len must be >= 0");
     if (len > 0 && !f) return fail(HB_ERR_INVALID, "f is NULL");
     DevMem &M = g->mem;
@@ -887,6 +912,107 @@ hb_status hb_get_neighbourhood(hb_graph *g, double *out, int32_t cap, int32_t *l
     return HB_OK;
 }
 
+hb_status hb_create_runs(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
+                         int32_t runs, const uint64_t *seeds, const hb_options *opt, hb_graph **out) {
+    g_err.clear();
+    if (!out) return fail(HB_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!seeds) return fail(HB_ERR_INVALID, "seeds is NULL");
+    int lr = 0;
+    while (lr < 7 && (1 << lr) < runs) ++lr;
+    if (runs < 2 || runs > 64 || (1 << lr) != runs)
+        return fail(HB_ERR_INVALID, "runs must be a power of two from 2 to 64");
+    if (log2m < kMinLog2m || log2m > 9) return fail(HB_ERR_INVALID, "log2m must lie in [4, 9] for several runs");
+    if (log2m + lr > kMaxLog2m) return fail(HB_ERR_INVALID, "runs * 2^log2m must not exceed 4096 bytes");
+    if (opt && (opt->flags & HB_NEIGHBOURHOOD))
+        return fail(HB_ERR_INVALID, "HB_NEIGHBOURHOOD needs a handle of one run");
+    return create_impl<int64_t>(offsets, targets, n, m, log2m, seeds[0], opt, out, lr, seeds);
+}
+
+namespace {
+hb_status check_runs(hb_graph *g) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    if (!g->lruns) return fail(HB_ERR_STATE, "not a handle of several runs (hb_create_runs)");
+    return HB_OK;
+}
+}  // namespace
+
+hb_status hb_get_run_steps(hb_graph *g, int32_t *steps) {
+    hb_status st = check_runs(g);
+    if (st != HB_OK) return st;
+    if (!steps) return fail(HB_ERR_INVALID, "steps is NULL");
+    // run r's fixpoint came one iteration after its last change (Sec. 4.2);
+    // until then it has run every iteration so far
+    for (size_t r = 0; r < g->run_last.size(); ++r) {
+        const int32_t fix = g->run_last[r] + 2;
+        steps[r] = fix < g->t ? fix : g->t;
+    }
+    return HB_OK;
+}
+
+hb_status hb_get_run_centralities(hb_graph *g, int32_t run, double *closeness, double *harmonic,
+                                  double *lin, double *reachable) {
+    hb_status st = check_runs(g);
+    if (st != HB_OK) return st;
+    if (run < 0 || run >= (1 << g->lruns)) return fail(HB_ERR_INVALID, "run out of range");
+    const int64_t n = g->n;
+    double *outs[4] = {closeness, harmonic, lin, reachable};
+    double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    DevMem tmp;
+    for (int k = 0; k < 4; ++k)
+        if (outs[k]) dev[k] = is_device_ptr(outs[k]) ? outs[k] : tmp.alloc<double>(n);
+    if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = launch_runs_centralities(g->a, current_regs(g), g->perm, g->fp32, run, dev[0], dev[1],
+                                             dev[2], dev[3], g->s);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+        if (outs[k] && dev[k] != outs[k]) e = to_caller(outs[k], dev[k], sizeof(double) * n, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "run centralities");
+    return HB_OK;
+}
+
+hb_status hb_get_run_accumulators(hb_graph *g, int32_t run, double *sumd, double *harm) {
+    hb_status st = check_runs(g);
+    if (st != HB_OK) return st;
+    if (run < 0 || run >= (1 << g->lruns)) return fail(HB_ERR_INVALID, "run out of range");
+    const int64_t n = g->n;
+    double *outs[2] = {sumd, harm};
+    const double *src[2] = {g->a.sumd, g->a.harm};
+    DevMem tmp;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        if (!outs[k]) continue;
+        double *d = is_device_ptr(outs[k]) ? outs[k] : tmp.alloc<double>(n);
+        if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+        e = launch_gather_strided(src[k], g->inv, n, g->lruns, run, d, g->s);
+        if (e == cudaSuccess && d != outs[k]) e = to_caller(outs[k], d, sizeof(double) * n, g->s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "run accumulators");
+    return HB_OK;
+}
+
+hb_status hb_get_run_stats(hb_graph *g, int32_t which, double *mean, double *sd) {
+    hb_status st = check_runs(g);
+    if (st != HB_OK) return st;
+    if (which < 0 || which > 3) return fail(HB_ERR_INVALID, "which must lie in [0, 3]");
+    const int64_t n = g->n;
+    DevMem tmp;
+    double *dm = mean ? (is_device_ptr(mean) ? mean : tmp.alloc<double>(n)) : nullptr;
+    double *ds = sd ? (is_device_ptr(sd) ? sd : tmp.alloc<double>(n)) : nullptr;
+    if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = launch_runs_stats(g->a, current_regs(g), g->perm, g->fp32, which, dm, ds, g->s);
+    if (e == cudaSuccess && mean && dm != mean) e = to_caller(mean, dm, sizeof(double) * n, g->s);
+    if (e == cudaSuccess && sd && ds != sd) e = to_caller(sd, ds, sizeof(double) * n, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "run statistics");
+    return HB_OK;
+}
+
 // ------------------------------------------------------------ checkpoint --
 
 namespace {
@@ -921,6 +1047,7 @@ bool read_dev(FILE *f, void *dev, size_t bytes, cudaStream_t s) {
 hb_status hb_save(hb_graph *g, const char *path) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    if (g->lruns) return fail(HB_ERR_STATE, "checkpoints need a handle of one run");
     if (!path) return fail(HB_ERR_INVALID, "path is NULL");
     FILE *f = fopen(path, "wb");
     if (!f) return fail(HB_ERR_INVALID, std::string("cannot open ") + path);
@@ -976,7 +1103,7 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     if (o.max_steps <= 0) o.max_steps = 1 << 20;
     cudaFree(nullptr);
     hb_graph *g = new hb_graph();
-    g->n = h.n; g->m = h.m; g->b = h.b; g->y = make_layout(h.b);
+    g->n = h.n; g->m = h.m; g->b = h.b; g->gb = h.b; g->y = make_layout(h.b);
     g->opt = o;
     g->opt.frontier = h.frontier;
     g->s = static_cast<cudaStream_t>(o.stream);

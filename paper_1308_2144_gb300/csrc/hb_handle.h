@@ -93,6 +93,10 @@ struct hb_graph {
     int64_t *wfirst = nullptr;     // Sec. 6: first replica item of each caller node (n+1), or null
     double *disc = nullptr;        // Sec. 7: discounted accumulator (n), or null
     double *ftab = nullptr;        // its discount table
+    int gb = 4;                    // log2 of one run's registers (b = gb + lruns: the row)
+    int lruns = 0;                 // log2 of the runs per row (hb_create_runs), 0 otherwise
+    uint64_t *run_seeds = nullptr; // their seeds (device)
+    std::vector<int32_t> run_last; // per run: last iteration in which it changed (-1: none)
     bool track_nf = false;         // HB_NEIGHBOURHOOD: N(t) after every iteration
     double *nf_part = nullptr;     // block partials of the estimate sum
     std::vector<double> nf;        // N(0), N(1), ... of the current run

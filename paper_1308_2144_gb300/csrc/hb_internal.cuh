@@ -99,6 +99,7 @@ struct Counters {
     int32_t converged;
     unsigned long long err;            // nonzero: a device-side check failed
     double nsum;                       // sum of the nodes' cached estimates (neighbourhood function)
+    unsigned long long run_mask;       // rows of several runs: bit r set if run r changed
 };
 
 // Everything the step kernels read, passed by value.  Buffers that
@@ -150,6 +151,9 @@ struct StepArgs {
     int32_t aps;                  // class sizing (arcs per slot) of the layout
     int32_t push_union;           // frontier iterations push changed counters along reverse arcs
     int32_t flen;                 // entries of ftab
+    int32_t gb;                   // log2 of one run's registers (= b unless rows hold several runs)
+    int32_t lruns;                // log2 of the runs sharing each row (0: one run per row)
+    const uint64_t *run_seeds;    // hash seed of each run of a row
     double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
 };
 
@@ -406,6 +410,21 @@ cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, in
 // nodes, whose replicas are the items wfirst[u] .. wfirst[u+1]-1.
 cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, bool fp32,
                         cudaStream_t s, const int64_t *wfirst = nullptr);
+// Rows of several runs (hb_create_runs): the gather with the per-run tail,
+// the pushed-union tail, initial counters, and per-run readouts.  log2row
+// is the row's log2 byte count (a.b); a.gb and a.lruns give the runs.
+cudaError_t launch_runs_step(const StepArgs &a, int log2row, bool fp32, int grid, cudaStream_t s);
+cudaError_t launch_runs_tail(const StepArgs &a, int log2row, bool fp32, int grid, cudaStream_t s);
+cudaError_t launch_runs_init(const StepArgs &a, const int32_t *perm, bool fp32, cudaStream_t s);
+cudaError_t launch_runs_centralities(const StepArgs &a, const uint8_t *regs, const int32_t *perm, bool fp32,
+                                     int run, double *closeness, double *harmonic, double *lin,
+                                     double *reachable, cudaStream_t s);
+cudaError_t launch_runs_stats(const StepArgs &a, const uint8_t *regs, const int32_t *perm, bool fp32,
+                              int which, double *mean, double *sd, cudaStream_t s);
+// out[u] = src[(inv[u] << lstride) + off] (inv may be null: identity).
+cudaError_t launch_gather_strided(const double *src, const int32_t *inv, int64_t n, int lstride, int off,
+                                  double *out, cudaStream_t s);
+int runs_step_blocks_per_sm(int log2row, bool fp32);
 // Neighbourhood function: the sum of the n cached estimates (float or
 // double) into ctr->nsum, in a fixed order (grid kNfBlocks, partials in
 // part[kNfBlocks]) so that the result does not vary between runs.

@@ -87,13 +87,6 @@ __global__ void init_rows_kernel(uint8_t *r0, uint8_t *r1, const int32_t *perm, 
     }
 }
 
-__device__ __forceinline__ void reset_counters(Counters *c) {
-    c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
-    for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
-    c->prev_changed = 0; c->prev_list_len = 0; c->prev_push_arcs = 0; c->prev_big = 0;
-    c->mode = 0; c->t = 0; c->steps_done = 0; c->converged = 0; c->err = 0;
-}
-
 template <bool F32>
 __global__ void init_nodes_kernel(StepArgs a, const int32_t *perm, uint64_t seed) {
     const int P = 1 << a.b;
@@ -256,59 +249,7 @@ __global__ void heavy_total_kernel(const int64_t *off, int64_t n, int64_t heavy,
 template <int LOG2P, bool F32>
 __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MIN_BLOCKS)
     step_kernel(StepArgs a) {
-    using C = Cfg<LOG2P>;
-    const Counters *ctr = a.ctr;
-    const int t = ctr->t;
-    const bool sparse = ctr->mode == 1;
-    const Plan *pl = sparse ? a.plan_sparse : a.plan_dense;
-    const int32_t *list = sparse ? a.slist : a.dense_list;
-    const int32_t *owner = sparse ? a.owner_sparse : a.owner_dense;
-    const int64_t *cstart = sparse ? a.cstart_sparse : a.cstart_dense;
-    const uint8_t *cur = a.regs[t & 1];
-    uint8_t *nxt = a.regs[(t + 1) & 1];
-    int32_t *clist = a.clist[t & 1];
-    int32_t *biglist = a.biglist[t & 1];
-    if (sparse && a.push_union) return;   // the pushed union does this iteration
-    const int64_t items = pl->items;
-    const int64_t hch = pl->heavy_chunks;
-    int64_t ib[C::NLIGHT + 1], cnt[C::NLIGHT];
-#pragma unroll
-    for (int j = 0; j <= C::NLIGHT; ++j) ib[j] = pl->item_begin[j];
-#pragma unroll
-    for (int j = 0; j < C::NLIGHT; ++j) cnt[j] = pl->count[j + 1];
-    __shared__ unsigned long long s_changed;
-    __shared__ unsigned long long s_pow2[64];
-    const double rdist64 = 1.0 / (double)(t + 1);
-    const float rdist32 = 1.0f / (float)(t + 1);
-    // most nodes change in the first iterations: fetch their accumulators early
-    const bool prefetch = !sparse && (t == 0 || 4 * (int64_t)ctr->prev_changed > a.n_pos);
-    if (threadIdx.x == 0) s_changed = 0;
-    if (threadIdx.x < 64) {
-        const int M = threadIdx.x, sh = 64 - a.b;
-        s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
-    }
-    __syncthreads();
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t it = gw; it < items; it += nw) {
-        if (it < hch) {
-            heavy_item<LOG2P, F32>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
-                                   &s_changed, rdist64, rdist32, s_pow2);
-        } else {
-            const int64_t li = it - hch;
-            int j = 0;
-            int64_t ibj = ib[0], cntj = cnt[0], seg0 = a.seg_begin[1];
-#pragma unroll
-            for (int q = 1; q < C::NLIGHT; ++q)
-                if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
-            const int64_t pos0 = seg0 + ((li - ibj) << j);
-            light_item<LOG2P, F32>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
-                                   clist, biglist, sparse, &s_changed, rdist64, rdist32, s_pow2,
-                                   prefetch);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && s_changed) atomicAdd(&a.ctr->n_changed, s_changed);
+    step_body<LOG2P, F32, false>(a);
 }
 
 // ------------------------------------------------ pushed frontier union --
@@ -339,30 +280,7 @@ __global__ void __launch_bounds__(kStepThreads, 4) push_union_kernel(StepArgs a)
 // The per-node tail of a pushed frontier iteration over the marked nodes.
 template <int LOG2P, bool F32>
 __global__ void __launch_bounds__(kStepThreads) union_tail_kernel(StepArgs a) {
-    using C = Cfg<LOG2P>;
-    const Counters *ctr = a.ctr;
-    if (ctr->mode != 1 || !a.push_union) return;
-    const int t = ctr->t;
-    int64_t total = 0;
-#pragma unroll
-    for (int s = 0; s < kSegs; ++s) total += (int64_t)ctr->fill[s];
-    __shared__ unsigned long long s_changed;
-    __shared__ unsigned long long s_pow2[64];
-    const double rdist64 = 1.0 / (double)(t + 1);
-    const float rdist32 = 1.0f / (float)(t + 1);
-    if (threadIdx.x == 0) s_changed = 0;
-    if (threadIdx.x < 64) {
-        const int M = threadIdx.x, sh = 64 - a.b;
-        s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
-    }
-    __syncthreads();
-    constexpr int NPW = 32 / C::L;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = gw * NPW; base < total; base += nw * NPW)
-        union_tail_item<LOG2P, F32>(a, t, base, &s_changed, rdist64, rdist32, s_pow2);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_changed) atomicAdd(&a.ctr->n_changed, s_changed);
+    tail_body<LOG2P, F32, false>(a);
 }
 
 // After a dense iteration (frontier kept): list the changed nodes, their
@@ -503,6 +421,7 @@ cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, in
 cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, bool fp32,
                         cudaStream_t s, const int64_t *wfirst) {
     const int CH = (1 << a.b) >> 4;
+    if (a.lruns) return launch_runs_init(a, perm, fp32, s);
     if (wfirst) {
         if (fp32) init_weighted_kernel<true><<<grid_for(a.n, 128), 128, 0, s>>>(a, perm, wfirst, seed);
         else init_weighted_kernel<false><<<grid_for(a.n, 128), 128, 0, s>>>(a, perm, wfirst, seed);
@@ -562,13 +481,15 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
         if (a.push_union) ++k;   // push_union in place of mark_push, plus the tail below
     }
     if (ev) cudaEventRecord(ev[0], s);
-    cudaError_t e = fp32 ? launch_step_t<true>(a, y.log2m, step_grid, s)
-                         : launch_step_t<false>(a, y.log2m, step_grid, s);
+    cudaError_t e = a.lruns ? launch_runs_step(a, y.log2m, fp32, step_grid, s)
+                  : fp32    ? launch_step_t<true>(a, y.log2m, step_grid, s)
+                            : launch_step_t<false>(a, y.log2m, step_grid, s);
     if (e != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], s);
     if (a.push_union) {
-        e = fp32 ? launch_union_tail_t<true>(a, y.log2m, step_grid, s)
-                 : launch_union_tail_t<false>(a, y.log2m, step_grid, s);
+        e = a.lruns ? launch_runs_tail(a, y.log2m, fp32, step_grid, s)
+          : fp32    ? launch_union_tail_t<true>(a, y.log2m, step_grid, s)
+                    : launch_union_tail_t<false>(a, y.log2m, step_grid, s);
         if (e != cudaSuccess) return e;
         if (ev) cudaEventRecord(ev[3], s);
     }

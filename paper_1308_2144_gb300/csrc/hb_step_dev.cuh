@@ -244,7 +244,138 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
     }
 }
 
+// Per-node tail for rows that hold 2^lruns runs of p = 2^gb registers each
+// (hb_create_runs).  Run r owns bytes [r p, (r+1) p) of the row; the
+// register-wise max never mixes bytes, so the row's union is every run's
+// union at once.  The row write, changed flag and changed lists are those
+// of node_epilogue (a node changed if any of its runs did).  Then every run
+// whose registers changed gets its own size(), delta and Sec. 5
+// accumulators at index v * runs + r, and sets bit r of the iteration's run
+// mask (s_changed[1]); s_changed[0] counts changed nodes.
 template <int LOG2P, bool F32>
+__device__ __forceinline__ void node_epilogue_wide(const StepArgs &a, const uint8_t *__restrict__ cur,
+                                                   uint8_t *__restrict__ nxt, int t, int64_t v,
+                                                   bool active, uint4 (&acc)[Cfg<LOG2P>::CPL], int cl,
+                                                   int tl, int team, int logT, int32_t *clist,
+                                                   int32_t *biglist, bool sparse,
+                                                   unsigned long long *s_changed, double rdist64,
+                                                   float rdist32, const unsigned long long *pow2) {
+    using C = Cfg<LOG2P>;
+    const int lane = threadIdx.x & 31;
+    bool cd[C::CPL];
+    bool diff = false;
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c) cd[c] = false;
+    if (active) {
+        const uint8_t *own = cur + v * C::P + cl * 16;
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) {
+            const uint4 o = ld_counter(own + c * C::L * 16);
+            const uint4 nv = vmax16(acc[c], o);
+            cd[c] = ne16(nv, o);
+            diff |= cd[c];
+            acc[c] = nv;
+        }
+    }
+    const unsigned bal = __ballot_sync(FULL, diff);
+    const unsigned tmask = logT == 5 ? FULL : (((1u << (1 << logT)) - 1u) << (team << logT));
+    const bool ch = (bal & tmask) != 0u;
+    if (active && tl < C::L) {
+        uint8_t *dst = nxt + v * C::P + cl * 16;
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) __stcs(reinterpret_cast<uint4 *>(dst + c * C::L * 16), acc[c]);
+    }
+    const bool leader = active && tl == 0;
+    if (leader) a.changed[v] = ch ? 1 : 0;
+    const unsigned lb = __ballot_sync(FULL, leader && ch);
+    if (lb == 0u) return;
+
+    // A run's Gc = p/16 chunks sit in Gc consecutive chunk lanes (Gc <= L):
+    // chunk k of lane cl is chunk cl + k L of the row.  Sum each chunk's
+    // zero count and fixed-point sum over the run's lanes; the lane holding
+    // the run's first chunk finishes the run.
+    const int lg = a.gb - 4;
+    const int P = 1 << a.gb;
+    unsigned long long rmask = 0;
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c) {
+        uint32_t V = 0;
+        unsigned long long S = 0;
+        chunk_sums_tab(acc[c], pow2, V, S);
+        unsigned g = cd[c] ? 1u : 0u;
+        for (int o = 1; o < (1 << lg); o <<= 1) {
+            V += __shfl_xor_sync(FULL, V, o);
+            S += __shfl_xor_sync(FULL, S, o);
+            g |= __shfl_xor_sync(FULL, g, o);
+        }
+        const int r = (cl + c * C::L) >> lg;
+        if (active && ch && g && tl < C::L && (cl & ((1 << lg) - 1)) == 0) {
+            const int64_t q = (v << a.lruns) + r;
+            const double s_old = a.sumd[q], h_old = a.harm[q];
+            // Sec. 5: the new layer sits at distance t+1
+            if (F32) {
+                const float e_old = static_cast<const float *>(a.ecache)[q];
+                const float E = estimate32(V, S, P, a.gb, a.c32, a.thr_x, a.lc32);
+                const float d = __fsub_rn(E, e_old);
+                static_cast<float *>(a.ecache)[q] = E;
+                a.sumd[q] = __fma_rn((double)(t + 1), (double)d, s_old);
+                a.harm[q] = __dadd_rn(h_old, (double)__fmul_rn(d, rdist32));
+            } else {
+                const double e_old = static_cast<const double *>(a.ecache)[q];
+                const double E = estimate64(V, S, P, a.gb, a.c64, a.thr_x, a.lc64);
+                const double d = __dsub_rn(E, e_old);
+                static_cast<double *>(a.ecache)[q] = E;
+                a.sumd[q] = __fma_rn((double)(t + 1), d, s_old);
+                a.harm[q] = __fma_rn(d, rdist64, h_old);
+            }
+            rmask |= 1ULL << r;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) rmask |= __shfl_xor_sync(FULL, rmask, o);
+    if (lane == 0) {
+        atomicAdd(s_changed, (unsigned long long)__popc(lb));
+        if (rmask) atomicOr(s_changed + 1, rmask);
+    }
+    if (!sparse) return;   // dense iterations: the changed list is compacted afterwards
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctr->list_len, (unsigned long long)__popc(lb));
+    base = __shfl_sync(FULL, base, 0);
+    if (leader && ch) clist[base + __popc(lb & lanemask_lt())] = (int32_t)v;
+    if (a.has_reverse) {
+        const int64_t rd = (leader && ch) ? a.roff[v + 1] - a.roff[v] : 0;
+        unsigned long long sr = (unsigned long long)rd;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) sr += __shfl_xor_sync(FULL, sr, o);
+        if (lane == 0 && sr) atomicAdd(&a.ctr->push_arcs, sr);
+        const unsigned bb = __ballot_sync(FULL, rd > kBigRdeg);
+        if (bb) {
+            unsigned long long bbase = 0;
+            if (lane == 0) bbase = atomicAdd(&a.ctr->n_big, (unsigned long long)__popc(bb));
+            bbase = __shfl_sync(FULL, bbase, 0);
+            if (rd > kBigRdeg) biglist[bbase + __popc(bb & lanemask_lt())] = (int32_t)v;
+        }
+    }
+}
+
+// The tail of one node: node_epilogue, or node_epilogue_wide for rows of
+// several runs.
+template <int LOG2P, bool F32, bool WIDE>
+__device__ __forceinline__ void node_tail(const StepArgs &a, const uint8_t *__restrict__ cur,
+                                          uint8_t *__restrict__ nxt, int t, int64_t v, bool active,
+                                          uint4 (&acc)[Cfg<LOG2P>::CPL], int cl, int tl, int team,
+                                          int logT, int32_t *clist, int32_t *biglist, bool sparse,
+                                          unsigned long long *s_changed, double rdist64, float rdist32,
+                                          const unsigned long long *pow2) {
+    if constexpr (WIDE)
+        node_epilogue_wide<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
+                                       sparse, s_changed, rdist64, rdist32, pow2);
+    else
+        node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
+                                  sparse, s_changed, rdist64, rdist32, pow2);
+}
+
+template <int LOG2P, bool F32, bool WIDE = false>
 __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t pos0,
                                            int64_t pos_end, int logS, const int32_t *list,
@@ -282,14 +413,14 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
-    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
-                              sparse, s_changed, rdist64, rdist32, pow2);
+    node_tail<LOG2P, F32, WIDE>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
+                                sparse, s_changed, rdist64, rdist32, pow2);
 }
 
 // One chunk of a heavy node, by a whole warp.  Each chunk leaves its
 // partial union in scratch; the last chunk to arrive combines them and
 // finishes the node.
-template <int LOG2P, bool F32>
+template <int LOG2P, bool F32, bool WIDE = false>
 __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t it,
                                            const int32_t *owner, const int64_t *cstart,
@@ -345,8 +476,8 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
     }
-    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
-                              s_changed, rdist64, rdist32, pow2);
+    node_tail<LOG2P, F32, WIDE>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
+                                s_changed, rdist64, rdist32, pow2);
 }
 
 // Start of an iteration for one graph: shift this iteration's counters
@@ -360,6 +491,7 @@ __device__ __forceinline__ void begin_one(const StepArgs &a) {
     c->prev_push_arcs = c->push_arcs;
     c->prev_big = c->n_big;
     c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
+    c->run_mask = 0;
     for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
     int sparse = 0;
     if (t > 0) {
@@ -515,7 +647,7 @@ __device__ __forceinline__ void push_union_big(const StepArgs &a, const uint4 *c
 // through the same tail as a gathered node (own counter folded in,
 // changed flag, estimator, accumulators, changed list).  One team of L
 // lanes per node; called by a whole warp.
-template <int LOG2P, bool F32>
+template <int LOG2P, bool F32, bool WIDE = false>
 __device__ __forceinline__ void union_tail_item(const StepArgs &a, int t, int64_t base,
                                                 unsigned long long *cnt, double rdist64, float rdist32,
                                                 const unsigned long long *pow2) {
@@ -546,8 +678,108 @@ __device__ __forceinline__ void union_tail_item(const StepArgs &a, int t, int64_
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = __ldcg(row + c * C::L);
     }
-    node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, tl, tl, team, C::LOGL, a.clist[t & 1],
-                              a.biglist[t & 1], true, cnt, rdist64, rdist32, pow2);
+    node_tail<LOG2P, F32, WIDE>(a, cur, nxt, t, v, active, acc, tl, tl, team, C::LOGL, a.clist[t & 1],
+                                a.biglist[t & 1], true, cnt, rdist64, rdist32, pow2);
+}
+
+// The gather kernel's body: every work item of the iteration's plan (heavy
+// chunks, then light items of each degree class), with the per-node tail
+// of one run per row or, WIDE, of several runs per row.
+template <int LOG2P, bool F32, bool WIDE>
+__device__ __forceinline__ void step_body(const StepArgs &a) {
+    using C = Cfg<LOG2P>;
+    const Counters *ctr = a.ctr;
+    const int t = ctr->t;
+    const bool sparse = ctr->mode == 1;
+    const Plan *pl = sparse ? a.plan_sparse : a.plan_dense;
+    const int32_t *list = sparse ? a.slist : a.dense_list;
+    const int32_t *owner = sparse ? a.owner_sparse : a.owner_dense;
+    const int64_t *cstart = sparse ? a.cstart_sparse : a.cstart_dense;
+    const uint8_t *cur = a.regs[t & 1];
+    uint8_t *nxt = a.regs[(t + 1) & 1];
+    int32_t *clist = a.clist[t & 1];
+    int32_t *biglist = a.biglist[t & 1];
+    if (sparse && a.push_union) return;   // the pushed union does this iteration
+    const int64_t items = pl->items;
+    const int64_t hch = pl->heavy_chunks;
+    int64_t ib[C::NLIGHT + 1], cnt[C::NLIGHT];
+#pragma unroll
+    for (int j = 0; j <= C::NLIGHT; ++j) ib[j] = pl->item_begin[j];
+#pragma unroll
+    for (int j = 0; j < C::NLIGHT; ++j) cnt[j] = pl->count[j + 1];
+    __shared__ unsigned long long s_changed[2];   // changed nodes; WIDE: mask of changed runs
+    __shared__ unsigned long long s_pow2[64];
+    const double rdist64 = 1.0 / (double)(t + 1);
+    const float rdist32 = 1.0f / (float)(t + 1);
+    // most nodes change in the first iterations: fetch their accumulators early
+    const bool prefetch = !sparse && (t == 0 || 4 * (int64_t)ctr->prev_changed > a.n_pos);
+    if (threadIdx.x < 2) s_changed[threadIdx.x] = 0;
+    if (threadIdx.x < 64) {
+        const int M = threadIdx.x, sh = 64 - (WIDE ? a.gb : a.b);
+        s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
+    }
+    __syncthreads();
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = gw; it < items; it += nw) {
+        if (it < hch) {
+            heavy_item<LOG2P, F32, WIDE>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
+                                         s_changed, rdist64, rdist32, s_pow2);
+        } else {
+            const int64_t li = it - hch;
+            int j = 0;
+            int64_t ibj = ib[0], cntj = cnt[0], seg0 = a.seg_begin[1];
+#pragma unroll
+            for (int q = 1; q < C::NLIGHT; ++q)
+                if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
+            const int64_t pos0 = seg0 + ((li - ibj) << j);
+            light_item<LOG2P, F32, WIDE>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
+                                         clist, biglist, sparse, s_changed, rdist64, rdist32, s_pow2,
+                                         prefetch && !WIDE);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_changed[0]) atomicAdd(&a.ctr->n_changed, s_changed[0]);
+    if (WIDE && threadIdx.x == 0 && s_changed[1]) atomicOr(&a.ctr->run_mask, s_changed[1]);
+}
+
+// The pushed-union tail kernel's body: the per-node tail over the nodes
+// marked in a pushed frontier iteration.
+template <int LOG2P, bool F32, bool WIDE>
+__device__ __forceinline__ void tail_body(const StepArgs &a) {
+    using C = Cfg<LOG2P>;
+    const Counters *ctr = a.ctr;
+    if (ctr->mode != 1 || !a.push_union) return;
+    const int t = ctr->t;
+    int64_t total = 0;
+#pragma unroll
+    for (int s = 0; s < kSegs; ++s) total += (int64_t)ctr->fill[s];
+    __shared__ unsigned long long s_changed[2];
+    __shared__ unsigned long long s_pow2[64];
+    const double rdist64 = 1.0 / (double)(t + 1);
+    const float rdist32 = 1.0f / (float)(t + 1);
+    if (threadIdx.x < 2) s_changed[threadIdx.x] = 0;
+    if (threadIdx.x < 64) {
+        const int M = threadIdx.x, sh = 64 - (WIDE ? a.gb : a.b);
+        s_pow2[M] = (M == 0 || M > sh) ? 0ULL : 1ULL << (sh - M);
+    }
+    __syncthreads();
+    constexpr int NPW = 32 / C::L;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = gw * NPW; base < total; base += nw * NPW)
+        union_tail_item<LOG2P, F32, WIDE>(a, t, base, s_changed, rdist64, rdist32, s_pow2);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_changed[0]) atomicAdd(&a.ctr->n_changed, s_changed[0]);
+    if (WIDE && threadIdx.x == 0 && s_changed[1]) atomicOr(&a.ctr->run_mask, s_changed[1]);
+}
+
+__device__ __forceinline__ void reset_counters(Counters *c) {
+    c->n_changed = 0; c->list_len = 0; c->push_arcs = 0; c->n_big = 0; c->arcs = 0;
+    for (int s = 0; s < kSegs; ++s) c->fill[s] = 0;
+    c->prev_changed = 0; c->prev_list_len = 0; c->prev_push_arcs = 0; c->prev_big = 0;
+    c->mode = 0; c->t = 0; c->steps_done = 0; c->converged = 0; c->err = 0;
+    c->nsum = 0.0; c->run_mask = 0;
 }
 
 struct PlanParams {

@@ -45,7 +45,8 @@ HB_REQ_QUEUED, HB_REQ_RUNNING, HB_REQ_DONE, HB_REQ_FAILED = 0, 1, 2, 3
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
            "hb_get_info", "hb_reset", "hb_set_weights", "hb_set_discount", "hb_get_discounted",
-           "hb_get_neighbourhood",
+           "hb_get_neighbourhood", "hb_create_runs", "hb_get_run_steps", "hb_get_run_centralities",
+           "hb_get_run_accumulators", "hb_get_run_stats",
            "hb_save", "hb_load", "hb_destroy", "hb_last_error",
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
@@ -142,6 +143,17 @@ def load():
         L.hb_get_info.argtypes = [_vp, ctypes.POINTER(Info)]
         L.hb_reset.restype = st
         L.hb_reset.argtypes = [_vp, ctypes.c_uint64]
+        L.hb_create_runs.restype = st
+        L.hb_create_runs.argtypes = [_vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(Options), ctypes.POINTER(_vp)]
+        L.hb_get_run_steps.restype = st
+        L.hb_get_run_steps.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
+        L.hb_get_run_centralities.restype = st
+        L.hb_get_run_centralities.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+        L.hb_get_run_accumulators.restype = st
+        L.hb_get_run_accumulators.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+        L.hb_get_run_stats.restype = st
+        L.hb_get_run_stats.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
         L.hb_get_neighbourhood.restype = st
         L.hb_get_neighbourhood.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.hb_set_weights.restype = st
@@ -583,6 +595,53 @@ class HyperBall:
     @classmethod
     def from_graph(cls, g, **kw):
         return cls(g.offsets, g.targets, n=g.n, **kw)
+
+    @classmethod
+    def runs(cls, offsets, targets, log2m: int, seeds, n: int | None = None, **opts) -> "HyperBall":
+        """Several runs of one graph in one handle (hb_create_runs): run r
+        uses seeds[r]; rows hold len(seeds) counters of 2^log2m registers."""
+        if offsets.dtype in (torch.int32, np.int32):   # the entry point takes int64 offsets
+            offsets = offsets.to(torch.int64) if isinstance(offsets, torch.Tensor) else offsets.astype(np.int64)
+        self = cls.__new__(cls)
+        self.n = int(offsets.shape[0] - 1) if n is None else int(n)
+        self.m = int(targets.shape[0])
+        self.log2m = log2m
+        self.nruns = len(seeds)
+        self.p = self.nruns << log2m
+        self.options = make_options(**opts)
+        self._h = _vp()
+        arr = (ctypes.c_uint64 * self.nruns)(*[int(x) & (2**64 - 1) for x in seeds])
+        _check(load().hb_create_runs(_ptr(offsets), _ptr(targets) if self.m else None, self.n, self.m,
+                                     int(log2m), self.nruns, arr, ctypes.byref(self.options),
+                                     ctypes.byref(self._h)))
+        return self
+
+    def run_steps(self) -> list:
+        arr = (ctypes.c_int32 * self.nruns)()
+        _check(load().hb_get_run_steps(self._h, arr))
+        return list(arr)
+
+    def run_centralities(self, r: int, device="cuda") -> dict:
+        out = {k: self._out(self.n, torch.float64, device)
+               for k in ("closeness", "harmonic", "lin", "reachable")}
+        _check(load().hb_get_run_centralities(self._h, int(r), _ptr(out["closeness"]), _ptr(out["harmonic"]),
+                                              _ptr(out["lin"]), _ptr(out["reachable"])))
+        return out
+
+    def run_accumulators(self, r: int, device="cuda"):
+        sumd = self._out(self.n, torch.float64, device)
+        harm = self._out(self.n, torch.float64, device)
+        _check(load().hb_get_run_accumulators(self._h, int(r), _ptr(sumd), _ptr(harm)))
+        return sumd, harm
+
+    def run_stats(self, which, device="cuda"):
+        """Per-node mean and sample standard deviation over the runs of one
+        centrality ("closeness", "harmonic", "lin", "reachable")."""
+        w = ("closeness", "harmonic", "lin", "reachable").index(which) if isinstance(which, str) else int(which)
+        mean = self._out(self.n, torch.float64, device)
+        sd = self._out(self.n, torch.float64, device)
+        _check(load().hb_get_run_stats(self._h, w, _ptr(mean), _ptr(sd)))
+        return mean, sd
 
     def step(self) -> int:
         return hb_step(self._h)

@@ -90,3 +90,100 @@ def test_same_graph_batch_and_mixed_sizes(orc):
         mixed.run_stats("lin")
     assert e.value.status == hbl.HB_ERR_INVALID
     mixed.close()
+
+
+# ------------------------------------------------- runs in one handle --
+
+def check_wide(orc, hb, off, tgt, b, seeds):
+    n = off.size - 1
+    p = 1 << b
+    regs = hb.registers().cpu().numpy()
+    assert regs.shape == (n, len(seeds) * p)
+    steps = hb.run_steps()
+    for r, s in enumerate(seeds):
+        ref = orc.run(off, tgt, b, s)
+        assert steps[r] == ref.steps, (r, steps[r], ref.steps)
+        assert np.array_equal(regs[:, r * p:(r + 1) * p], ref.regs), r
+        gs, gh = hb.run_accumulators(r)
+        close(gs.cpu().numpy(), ref.sumd)
+        close(gh.cpu().numpy(), ref.harm)
+        fin = orc.finalize(b, ref.regs, ref.sumd, ref.harm)
+        cen = hb.run_centralities(r)
+        for k in CENTRALITIES:
+            close(cen[k].cpu().numpy(), fin[k])
+    assert hb.info()["t"] == max(steps)
+    for which in CENTRALITIES:
+        mean, sd = (x.cpu().numpy() for x in hb.run_stats(which))
+        m_ref, s_ref = orc.run_stats(off, tgt, b, seeds, which)
+        close(mean, m_ref)
+        assert np.all(np.abs(sd - s_ref) <= 1e-9 * np.abs(m_ref)), which
+
+
+@pytest.mark.parametrize("b,R,frontier", [(4, 2, "auto"), (4, 16, "auto"), (4, 64, "off"), (5, 64, "push"),
+                                          (6, 4, "off"), (6, 16, "push"), (7, 32, "auto"), (9, 8, "pull")])
+def test_runs_in_one_handle_equal_solo_runs(orc, b, R, frontier):
+    """Each run of a row equals its solo run: counters, iteration count,
+    accumulators and centralities; the statistics equal the oracle's."""
+    off, tgt = graphs.rmat_graph(scale=11, edge_factor=8, seed=60 + b + R).numpy()
+    seeds = [300 + 11 * r for r in range(R)]
+    hb = hbl.HyperBall.runs(*to_dev(off, tgt), b, seeds, n=off.size - 1, frontier=frontier)
+    hb.run()
+    check_wide(orc, hb, off, tgt, b, seeds)
+    # a reset keeps the seeds and gives the same runs again
+    hb.reset(0)
+    hb.run()
+    check_wide(orc, hb, off, tgt, b, seeds)
+    hb.close()
+
+
+def test_runs_in_one_handle_every_iteration(orc):
+    """At every iteration each run's slice of the rows equals the oracle's
+    counters of that run, and a node is flagged changed exactly when one of
+    its runs changed.  Hubs above the split threshold of the wide rows."""
+    off, tgt = graphs.rmat_graph(scale=13, edge_factor=16, seed=8).numpy()
+    n = off.size - 1
+    b, seeds = 6, [5, 6, 7, 8]
+    p = 1 << b
+    hb = hbl.HyperBall.runs(*to_dev(off, tgt), b, seeds, n=n)
+    cs = [orc.init(n, b, s) for s in seeds]
+    acc = [(np.zeros(n), np.zeros(n)) for _ in seeds]
+    t = 0
+    while True:
+        outs = [orc.step(off, tgt, b, t, cs[r], *acc[r]) for r in range(len(seeds))]
+        k = hb.step()
+        regs = hb.registers().cpu().numpy()
+        changed = np.zeros(n, dtype=bool)
+        for r, (nxt, ch, _) in enumerate(outs):
+            assert np.array_equal(regs[:, r * p:(r + 1) * p], nxt), (t, r)
+            changed |= ch.astype(bool)
+            cs[r] = nxt
+        assert k == int(changed.sum())
+        assert np.array_equal(hb.frontier()[0].cpu().numpy().astype(bool), changed)
+        t += 1
+        if k == 0:
+            break
+    hb.close()
+
+
+def test_runs_in_one_handle_fp32_host_csr_and_limits(orc):
+    off, tgt = graphs.plain_graph(n=4000, seed=9).numpy()
+    n = off.size - 1
+    seeds = [21, 22, 23, 24, 25, 26, 27, 28]
+    hb = hbl.HyperBall.runs(torch.from_numpy(off), torch.from_numpy(tgt), 4, seeds, n=n, fp32=True)
+    hb.tune()
+    hb.run()
+    regs = hb.registers().cpu().numpy()
+    for r, s in enumerate(seeds):
+        assert np.array_equal(regs[:, 16 * r:16 * (r + 1)], orc.run(off, tgt, 4, s).regs)
+    for call in (lambda: hb.centralities(), lambda: hb.accumulators(),
+                 lambda: hb.set_weights(np.ones(n, dtype=np.int64)), lambda: hb.set_discount([1.0]),
+                 lambda: hb.save("/tmp/never-written.ckpt")):
+        with pytest.raises(hbl.HBError) as e:
+            call()
+        assert e.value.status == hbl.HB_ERR_STATE
+    hb.close()
+    d_off, d_tgt = to_dev(off, tgt)
+    for b, seeds in ((4, [1, 2, 3]), (10, [1, 2]), (7, list(range(64))), (4, [1])):
+        with pytest.raises(hbl.HBError) as e:
+            hbl.HyperBall.runs(d_off, d_tgt, b, seeds, n=n)
+        assert e.value.status == hbl.HB_ERR_INVALID
