@@ -87,13 +87,66 @@ __global__ void count_targets(const int32_t *tgt, int64_t m, unsigned long long 
         atomicAdd(&cnt[tgt[e]], 1ULL);
 }
 
-__global__ void scatter_transpose(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                                  unsigned long long *cursor, int32_t *ttgt) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t u = arc_source(off, n, e);
-        unsigned long long pos = atomicAdd(&cursor[tgt[e]], 1ULL);
-        ttgt[pos] = (int32_t)u;
+// Arc passes that need each arc's source node work on tiles of kArcTile
+// consecutive arcs: thread 0 finds the sources u0 of the tile's first arc
+// and u1 of its last by binary search over all offsets, the block stages
+// off[u0 .. u1] in shared memory, and every arc's source is then the last
+// staged node whose offset is <= the arc (off[u1+1] lies beyond the tile).
+// A tile whose sources span more than kStageNodes nodes (runs of empty
+// nodes) falls back to the search over all offsets.
+constexpr int kArcTile = 2048;
+constexpr int kStageNodes = 2048;
+
+struct ArcTile {
+    int64_t e0, e1, u0;
+    int cnt;   // staged offsets (0: fall back)
+};
+
+__device__ __forceinline__ ArcTile stage_arc_tile(const int64_t *off, int64_t n, int64_t m, int64_t e0,
+                                                  int64_t *s_off, int64_t *s_hdr) {
+    const int64_t e1 = e0 + kArcTile < m ? e0 + kArcTile : m;
+    __syncthreads();   // the previous tile's readers are done with s_off
+    if (threadIdx.x == 0) {
+        const int64_t u0 = arc_source(off, n, e0), u1 = arc_source(off, n, e1 - 1);
+        s_hdr[0] = u0;
+        s_hdr[1] = (u1 - u0 + 1 <= kStageNodes) ? u1 - u0 + 1 : 0;
+    }
+    __syncthreads();
+    ArcTile t{e0, e1, s_hdr[0], (int)s_hdr[1]};
+    for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) s_off[i] = off[t.u0 + i];
+    __syncthreads();
+    return t;
+}
+
+// Source node of arc e of the tile, and its first arc off[u].
+__device__ __forceinline__ int64_t tile_source(const ArcTile &t, const int64_t *s_off, const int64_t *off,
+                                               int64_t n, int64_t e, int64_t &first) {
+    if (t.cnt == 0) {
+        const int64_t u = arc_source(off, n, e);
+        first = off[u];
+        return u;
+    }
+    int lo = 0, hi = t.cnt;   // s_off[lo] <= e < off[u0 + hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_off[mid] <= e) lo = mid; else hi = mid;
+    }
+    first = s_off[lo];
+    return t.u0 + lo;
+}
+
+__global__ void __launch_bounds__(256) scatter_transpose(const int64_t *off, const int32_t *tgt, int64_t n,
+                                                         int64_t m, unsigned long long *cursor, int32_t *ttgt) {
+    __shared__ int64_t s_off[kStageNodes];
+    __shared__ int64_t s_hdr[2];
+    for (int64_t e0 = (int64_t)blockIdx.x * kArcTile; e0 < m; e0 += (int64_t)gridDim.x * kArcTile) {
+        const ArcTile t = stage_arc_tile(off, n, m, e0, s_off, s_hdr);
+        for (int64_t e = t.e0 + threadIdx.x; e < t.e1; e += blockDim.x) {
+            int64_t first;
+            const int64_t u = tile_source(t, s_off, off, n, e, first);
+            const unsigned long long pos = atomicAdd(&cursor[tgt[e]], 1ULL);
+            ttgt[pos] = (int32_t)u;
+        }
     }
 }
 
@@ -197,13 +250,18 @@ __global__ void permuted_degrees(const int64_t *off, const int32_t *perm, int64_
     if (blockIdx.x == 0 && threadIdx.x == 0) deg[n] = 0;
 }
 
-__global__ void relabel_arcs(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                             const int32_t *inv, const int64_t *noff, int32_t *ntgt) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t u = arc_source(off, n, e);
-        int64_t nu = inv[u];
-        ntgt[noff[nu] + (e - off[u])] = inv[tgt[e]];
+__global__ void __launch_bounds__(256) relabel_arcs(const int64_t *off, const int32_t *tgt, int64_t n,
+                                                    int64_t m, const int32_t *inv, const int64_t *noff,
+                                                    int32_t *ntgt) {
+    __shared__ int64_t s_off[kStageNodes];
+    __shared__ int64_t s_hdr[2];
+    for (int64_t e0 = (int64_t)blockIdx.x * kArcTile; e0 < m; e0 += (int64_t)gridDim.x * kArcTile) {
+        const ArcTile t = stage_arc_tile(off, n, m, e0, s_off, s_hdr);
+        for (int64_t e = t.e0 + threadIdx.x; e < t.e1; e += blockDim.x) {
+            int64_t first;
+            const int64_t u = tile_source(t, s_off, off, n, e, first);
+            ntgt[noff[inv[u]] + (e - first)] = inv[tgt[e]];
+        }
     }
 }
 
@@ -325,7 +383,8 @@ cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int
     e = scan_exclusive_i64(reinterpret_cast<int64_t *>(cnt), toff, n + 1, s);
     if (e == cudaSuccess && m > 0) {
         cudaMemcpyAsync(cnt, toff, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
-        scatter_transpose<<<grid_for(m, 256), 256, 0, s>>>(off, tgt, n, m, cnt, ttgt);
+        scatter_transpose<<<grid_for((m + kArcTile - 1) / kArcTile * 256, 256), 256, 0, s>>>(off, tgt, n, m, cnt,
+                                                                                           ttgt);
         e = cudaGetLastError();
     }
     cudaFreeAsync(cnt, s);
@@ -385,7 +444,8 @@ cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64
     permuted_degrees<<<grid_for(n + 1, 256), 256, 0, s>>>(off, perm, n, deg);
     e = scan_exclusive_i64(deg, noff, n + 1, s);
     if (e == cudaSuccess && m > 0) {
-        relabel_arcs<<<grid_for(m, 256), 256, 0, s>>>(off, tgt, n, m, inv, noff, ntgt);
+        relabel_arcs<<<grid_for((m + kArcTile - 1) / kArcTile * 256, 256), 256, 0, s>>>(off, tgt, n, m, inv,
+                                                                                      noff, ntgt);
         e = cudaGetLastError();
     }
     cudaFreeAsync(deg, s);
