@@ -183,6 +183,10 @@ def runs_main(args):
         g = graphs.web_graph(device="cuda")
         b, args.fp32 = 4, True
         desc = "web-like (R-MAT scale 28, 268,435,456 nodes, edge factor 16), transpose, log2m 4, FP32 estimates"
+    elif args.graph == "web25":
+        g = graphs.web_graph(scale=25, device="cuda", bucket_bits=3)
+        b, args.fp32 = 4, True
+        desc = "web-like at profiling size (R-MAT scale 25, 33,554,432 nodes, edge factor 16), transpose, log2m 4, FP32"
     else:
         g = graphs.enwiki_graph(device="cuda")
         b = 6
@@ -210,7 +214,7 @@ def runs_main(args):
     # left out on the web-like graph, where it would hold a further copy of
     # every run's state and adds nothing to the comparison
     batch = None
-    if args.graph != "web":
+    if not args.graph.startswith("web"):
         batch = hbl.HyperBallBatch.runs(g.offsets, g.targets, n, b, seeds, fp32=args.fp32)
 
     def batched():
@@ -290,7 +294,7 @@ def main():
     s.add_argument("--fp32", action="store_true")
     r = sub.add_parser("runs")
     r.add_argument("--runs", type=int, default=16)
-    r.add_argument("--graph", choices=["enwiki", "web"], default="enwiki")
+    r.add_argument("--graph", choices=["enwiki", "web", "web25"], default="enwiki")
     r.add_argument("--repeat", type=int, default=3)
     r.add_argument("--fp32", action="store_true")
     args = ap.parse_args()
