@@ -396,27 +396,35 @@ def run_e2e(args, g, opts, wl, world, cen, aps):
     """Same metric through the public API from host memory: pinned host CSR
     in, handle created (upload + setup) with the class sizing chosen above,
     run to the fixpoint, centralities back to pinned host memory, handle
-    destroyed, every step."""
+    destroyed, every step; one untimed step first."""
     from paper_1308_2144_gb300 import hyperball as hbl
     n = g.n
     off_h = g.offsets.cpu().pin_memory()
     tgt_h = g.targets.cpu().pin_memory()
     outs_h = {k: torch.empty(n, dtype=torch.float64).pin_memory() for k in cen}
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, 5))
     e2e_arcs = 0
     opts_h = dict(opts)
     opts_h.pop("profile")
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for k in range(e2e_steps):
-        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=wl["seed"] + 100 + k))
+
+    def one(seed):
+        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed))
         h.set_class_sizing(aps)
         h.run()
         hbl.hb_get_centralities(h._h, outs_h["closeness"], outs_h["harmonic"], outs_h["lin"],
                                 outs_h["reachable"])
-        e2e_arcs += h.info()["total_arcs"]
+        arcs = h.info()["total_arcs"]
         h.close()
+        return arcs
+
+    # one untimed pass first, as for the device-resident steps: the first
+    # handle of a process grows the library's memory pool
+    one(wl["seed"] + 99)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        e2e_arcs += one(wl["seed"] + 100 + k)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     e2e_val = sum_over_ranks(e2e_arcs, world) / e2e_s

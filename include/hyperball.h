@@ -26,7 +26,8 @@
  *     valid and unchanged until hb_destroy.  Outputs may be host or device
  *     memory of the stated size; the call returns when they are written.
  *   - The library owns every buffer it allocates (registers, flags,
- *     accumulators) and frees them in hb_destroy.
+ *     accumulators) and frees them in hb_destroy (into its memory pool:
+ *     see hb_trim_memory).
  *   - All device work runs on the stream in hb_options (NULL = the legacy
  *     default stream).  A handle must not be used by two threads at once;
  *     distinct handles are independent.
@@ -292,6 +293,16 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out);
 
 /* Free every resource of the handle (NULL is allowed). */
 void hb_destroy(hb_graph *g);
+
+/* Device memory: handles take their device memory from a pool of the
+ * library's own (one per device, stream-ordered on the handle's stream),
+ * and what hb_destroy frees stays in that pool for later handles, so that
+ * creating and destroying handles needs no device-wide synchronisation and
+ * no new page mappings once the pool has grown (the way a caching
+ * allocator keeps freed blocks).  hb_trim_memory returns every unused byte
+ * of the library's pools to the device; memory of live handles is kept.
+ * The process's default memory pool is not changed. */
+hb_status hb_trim_memory(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *hb_last_error(void);

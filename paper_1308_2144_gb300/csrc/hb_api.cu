@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -48,6 +49,45 @@ double hll_alpha(int p) {
 }  // namespace
 
 namespace hb {
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+bool g_pool_tried[kMaxDevices] = {};
+}  // namespace
+
+cudaMemPool_t library_pool() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool_tried[dev]) {
+        g_pool_tried[dev] = true;
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+            // keep freed memory for the next handle (hb_trim_memory returns it)
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pools[dev] = pool;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return g_pools[dev];
+}
+
+cudaError_t tmp_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = library_pool();
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, s) : cudaMallocAsync(p, bytes, s);
+}
+
 double hll_alpha_of(int p) { return hll_alpha(p); }
 void set_last_error(const char *msg) { g_err = msg ? msg : ""; }
 }  // namespace hb
@@ -278,8 +318,8 @@ hb_status retune(hb_graph *g, int aps) {
     if (a.dense_list) {
         int64_t *sb_dev = nullptr;
         unsigned long long *fill = nullptr;
-        e = cudaMallocAsync(&sb_dev, sizeof(seg_begin), s);
-        if (e == cudaSuccess) e = cudaMallocAsync(&fill, sizeof(unsigned long long) * kSegs, s);
+        e = tmp_alloc(&sb_dev, sizeof(seg_begin), s);
+        if (e == cudaSuccess) e = tmp_alloc(&fill, sizeof(unsigned long long) * kSegs, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sb_dev, seg_begin, sizeof(seg_begin), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = build_dense_list(g->off, n, g->y, sb_dev, const_cast<int32_t *>(a.dense_list), fill, s);
@@ -300,7 +340,7 @@ hb_status retune(hb_graph *g, int aps) {
 hb_status make_instance(const hb_graph *tmpl, uint64_t seed, cudaStream_t s, hb_graph **out,
                         cudaMemPool_t pool, Counters *ctr_host) {
     hb_graph *g = new hb_graph();
-    g->mem.pool = pool;
+    g->mem.pool = pool ? pool : library_pool();
     g->mem.stream = s;
     if (ctr_host) {
         g->ctr_host = ctr_host;
@@ -407,6 +447,8 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     }
     cudaStream_t s = g->s;
     DevMem &M = g->mem;
+    M.pool = library_pool();
+    M.stream = s;
     if (lruns) {
         g->run_seeds = M.alloc<uint64_t>((size_t)1 << lruns);
         if (!g->run_seeds) { delete g; return fail(HB_ERR_OOM, "out of device memory (run seeds)"); }
@@ -1107,6 +1149,8 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     g->opt = o;
     g->opt.frontier = h.frontier;
     g->s = static_cast<cudaStream_t>(o.stream);
+    g->mem.pool = library_pool();
+    g->mem.stream = g->s;
     g->fp32 = h.fp32 != 0;
     g->relabel = h.relabel != 0;
     g->track_nf = h.nf_len >= 0;
@@ -1170,6 +1214,16 @@ void hb_destroy(hb_graph *g) {
     if (g->s) cudaStreamSynchronize(g->s);
     else cudaDeviceSynchronize();
     delete g;
+}
+
+hb_status hb_trim_memory(void) {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (int d = 0; d < kMaxDevices; ++d) {
+        if (!g_pools[d]) continue;
+        const cudaError_t e = cudaMemPoolTrimTo(g_pools[d], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "trim");
+    }
+    return HB_OK;
 }
 
 const char *hb_last_error(void) { return g_err.c_str(); }

@@ -4,7 +4,7 @@
 // for the step kernel (heavy nodes first, then light degree classes).
 #include <cstdio>
 
-#include "hb_internal.cuh"
+#include "hb_handle.h"
 
 namespace hb {
 
@@ -325,7 +325,7 @@ cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t N, cudaS
         return cudaGetLastError();
     }
     int64_t *sums = nullptr;
-    cudaError_t e = cudaMallocAsync(&sums, sizeof(int64_t) * tiles * 2, s);
+    cudaError_t e = tmp_alloc(&sums, sizeof(int64_t) * tiles * 2, s);
     if (e != cudaSuccess) return e;
     scan_tile_sums<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, N, sums);
     e = scan_exclusive_i64(sums, sums + tiles, tiles, s);
@@ -360,7 +360,7 @@ __global__ void weights_in_kernel(const int64_t *w, int64_t n, int64_t *tmp, uns
 cudaError_t replica_starts(const int64_t *w, int64_t n, int64_t *wfirst, unsigned long long *err,
                            cudaStream_t s) {
     int64_t *tmp = nullptr;
-    cudaError_t e = cudaMallocAsync(&tmp, sizeof(int64_t) * (n + 1), s);
+    cudaError_t e = tmp_alloc(&tmp, sizeof(int64_t) * (n + 1), s);
     if (e != cudaSuccess) return e;
     weights_in_kernel<<<grid_for(n + 1, 256), 256, 0, s>>>(w, n, tmp, err);
     e = scan_exclusive_i64(tmp, wfirst, n + 1, s);
@@ -376,7 +376,7 @@ cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaSt
 cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                           int64_t *toff, int32_t *ttgt, cudaStream_t s) {
     unsigned long long *cnt = nullptr;
-    cudaError_t e = cudaMallocAsync(&cnt, sizeof(unsigned long long) * (n + 1), s);
+    cudaError_t e = tmp_alloc(&cnt, sizeof(unsigned long long) * (n + 1), s);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (n + 1), s);
     if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, cnt);
@@ -403,10 +403,10 @@ cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64
     unsigned long long *indeg = nullptr;
     uint8_t *keys = nullptr;
     int32_t *perm1 = nullptr;
-    cudaError_t e = cudaMallocAsync(&counts, sizeof(int64_t) * kBuckets * ntiles * 2, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&indeg, sizeof(unsigned long long) * n, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&keys, 2 * (size_t)n, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&perm1, sizeof(int32_t) * n, s);
+    cudaError_t e = tmp_alloc(&counts, sizeof(int64_t) * kBuckets * ntiles * 2, s);
+    if (e == cudaSuccess) e = tmp_alloc(&indeg, sizeof(unsigned long long) * n, s);
+    if (e == cudaSuccess) e = tmp_alloc(&keys, 2 * (size_t)n, s);
+    if (e == cudaSuccess) e = tmp_alloc(&perm1, sizeof(int32_t) * n, s);
     if (e == cudaSuccess) {
         cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * n, s);
         if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, indeg);
@@ -439,7 +439,7 @@ cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64
                         const int32_t *perm, const int32_t *inv, int64_t *noff, int32_t *ntgt,
                         cudaStream_t s) {
     int64_t *deg = nullptr;
-    cudaError_t e = cudaMallocAsync(&deg, sizeof(int64_t) * (n + 1), s);
+    cudaError_t e = tmp_alloc(&deg, sizeof(int64_t) * (n + 1), s);
     if (e != cudaSuccess) return e;
     permuted_degrees<<<grid_for(n + 1, 256), 256, 0, s>>>(off, perm, n, deg);
     e = scan_exclusive_i64(deg, noff, n + 1, s);
@@ -455,7 +455,7 @@ cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64
 cudaError_t count_degree_segments(const int64_t *off, int64_t n, const Layout &y,
                                   int64_t *seg_count_host, cudaStream_t s) {
     unsigned long long *cnt = nullptr;
-    cudaError_t e = cudaMallocAsync(&cnt, sizeof(unsigned long long) * kSegs, s);
+    cudaError_t e = tmp_alloc(&cnt, sizeof(unsigned long long) * kSegs, s);
     if (e != cudaSuccess) return e;
     cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kSegs, s);
     if (n > 0) seg_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, bounds_of(y), cnt);

@@ -45,6 +45,21 @@ struct DevMem {
     }
 };
 
+// The library's device memory pool for the current device (created on
+// first use; null if the device cannot make one, and callers then fall
+// back to cudaMalloc).  Handles allocate from it in stream order, and
+// memory they free stays in it for the next handle until
+// hb_trim_memory() returns it: creating and destroying handles costs no
+// device-wide synchronisation and no page mapping after the first time.
+cudaMemPool_t library_pool();
+// Stream-ordered temporary allocation from the library pool (the default
+// pool of the device if there is none); free with cudaFreeAsync.
+cudaError_t tmp_alloc(void **p, size_t bytes, cudaStream_t s);
+template <class T>
+cudaError_t tmp_alloc(T **p, size_t bytes, cudaStream_t s) {
+    return tmp_alloc(reinterpret_cast<void **>(p), bytes, s);
+}
+
 // Host-side services of hb_api.cu used by the other translation units.
 hb_status create_handle64(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
                           int log2m, uint64_t seed, const hb_options *opt, hb_graph **out);

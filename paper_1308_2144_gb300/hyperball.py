@@ -44,7 +44,7 @@ HB_REQ_QUEUED, HB_REQ_RUNNING, HB_REQ_DONE, HB_REQ_FAILED = 0, 1, 2, 3
 # every symbol include/hyperball.h declares
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
-           "hb_get_info", "hb_reset", "hb_set_weights", "hb_set_discount", "hb_get_discounted",
+           "hb_get_info", "hb_reset", "hb_trim_memory", "hb_set_weights", "hb_set_discount", "hb_get_discounted",
            "hb_get_neighbourhood", "hb_create_runs", "hb_get_run_steps", "hb_get_run_centralities",
            "hb_get_run_accumulators", "hb_get_run_stats",
            "hb_save", "hb_load", "hb_destroy", "hb_last_error",
@@ -174,6 +174,8 @@ def load():
         L.hb_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(Options), ctypes.POINTER(_vp)]
         L.hb_destroy.restype = None
         L.hb_destroy.argtypes = [_vp]
+        L.hb_trim_memory.restype = st
+        L.hb_trim_memory.argtypes = []
         L.hb_last_error.restype = ctypes.c_char_p
         L.hb_last_error.argtypes = []
         L.hb_version.restype = ctypes.c_char_p
@@ -378,6 +380,12 @@ def hb_load(path: str, options: Options | None = None):
 def hb_destroy(h):
     if h:
         load().hb_destroy(h)
+
+
+def hb_trim_memory():
+    """Return the device memory cached in the library's pools (freed by
+    destroyed handles) to the device."""
+    _check(load().hb_trim_memory())
 
 
 def hb_version() -> str:

@@ -203,3 +203,37 @@ def test_web_full_size_sampled(orc, web):
     info = hb.info()
     assert info["converged"] == 1 and 5 <= steps <= 64
     hb.close()
+
+
+def test_enwiki_full_size_runs_in_one_handle(orc, enwiki):
+    """Four runs of the encyclopedia-like graph in one handle (rows of
+    4 x 64 bytes): each run's counters and iteration count equal its solo
+    oracle run, accumulators and centralities within 1e-9, and the per-node
+    statistics over the runs equal the oracle's."""
+    g = enwiki
+    off, tgt = g.numpy()
+    b, seeds = 6, [42, 43, 44, 45]
+    p = 1 << b
+    hb = hbl.HyperBall.runs(g.offsets, g.targets, b, seeds, n=g.n)
+    hb.run()
+    regs = hb.registers(device="cpu").numpy()
+    steps = hb.run_steps()
+    fins = []
+    for r, s in enumerate(seeds):
+        ref = orc.run(off, tgt, b, s)
+        assert steps[r] == ref.steps
+        assert np.array_equal(regs[:, r * p:(r + 1) * p], ref.regs), r
+        gs, gh = hb.run_accumulators(r, device="cpu")
+        close(gs.numpy(), ref.sumd)
+        close(gh.numpy(), ref.harm)
+        fin = orc.finalize(b, ref.regs, ref.sumd, ref.harm)
+        cen = hb.run_centralities(r, device="cpu")
+        for k in ("closeness", "harmonic", "lin", "reachable"):
+            close(cen[k].numpy(), fin[k])
+        fins.append(fin)
+    for k in ("closeness", "harmonic", "lin", "reachable"):
+        vals = np.array([f[k] for f in fins])
+        mean, sd = (x.cpu().numpy() for x in hb.run_stats(k))
+        close(mean, vals.mean(axis=0))
+        assert np.all(np.abs(sd - vals.std(axis=0, ddof=1)) <= 1e-9 * np.abs(vals.mean(axis=0))), k
+    hb.close()
