@@ -572,6 +572,15 @@ hb_status sync_host_state(hb_graph *g) {
 
 namespace {
 
+// Temporary device buffers of a call on handle g: from the library pool, on
+// the handle's stream (freed into the pool when the call returns).
+DevMem scratch(const hb_graph *g) {
+    DevMem d;
+    d.pool = library_pool();
+    d.stream = g->s;
+    return d;
+}
+
 hb_status check(hb_graph *g) {
     if (!g) return fail(HB_ERR_INVALID, "handle is NULL");
     if (g->broken) return fail(HB_ERR_STATE, "handle unusable after a CUDA error");
@@ -688,7 +697,7 @@ hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic, 
     const int64_t n = g->n;
     double *outs[4] = {closeness, harmonic, lin, reachable};
     double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     for (int k = 0; k < 4; ++k) {
         if (!outs[k]) continue;
         dev[k] = is_device_ptr(outs[k]) ? outs[k] : tmp.alloc<double>(n);
@@ -712,7 +721,7 @@ hb_status hb_get_accumulators(hb_graph *g, double *sumd, double *harm) {
     const int64_t n = g->n;
     double *outs[2] = {sumd, harm};
     const double *src[2] = {g->a.sumd, g->a.harm};
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         if (!outs[k]) continue;
@@ -733,7 +742,7 @@ hb_status hb_get_registers(hb_graph *g, uint8_t *out) {
     const size_t bytes = (size_t)g->n << g->b;
     if (bytes == 0) return HB_OK;
     if (!out) return fail(HB_ERR_INVALID, "out is NULL");
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     uint8_t *d = is_device_ptr(out) ? out : tmp.alloc<uint8_t>(bytes);
     if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
     cudaError_t e = launch_gather_rows(current_regs(g), g->inv, g->n, 1 << g->b, d, g->s);
@@ -748,7 +757,7 @@ hb_status hb_get_frontier(hb_graph *g, uint8_t *changed, uint8_t *must_check) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
     const int64_t n = g->n;
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     uint8_t *dc = changed ? (is_device_ptr(changed) ? changed : tmp.alloc<uint8_t>(n)) : nullptr;
     uint8_t *dm = must_check ? (is_device_ptr(must_check) ? must_check : tmp.alloc<uint8_t>(n)) : nullptr;
     if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
@@ -853,7 +862,7 @@ hb_status hb_set_weights(hb_graph *g, const int64_t *weights) {
         return init_state(g, g->seed);
     }
     const int64_t n = g->n;
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     int64_t *w = nullptr;
     cudaError_t e = cudaSuccess;
     if (is_device_ptr(weights)) {
@@ -932,7 +941,7 @@ hb_status hb_get_discounted(hb_graph *g, double *out) {
     if (!g->a.disc) return fail(HB_ERR_STATE, "no discount function set (hb_set_discount)");
     if (g->n > 0 && !out) return fail(HB_ERR_INVALID, "out is NULL");
     const int64_t n = g->n;
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     double *d = is_device_ptr(out) ? out : tmp.alloc<double>(n);
     if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
     cudaError_t e = launch_gather_f64(g->a.disc, g->inv, n, d, g->s);
@@ -1001,7 +1010,7 @@ hb_status hb_get_run_centralities(hb_graph *g, int32_t run, double *closeness, d
     const int64_t n = g->n;
     double *outs[4] = {closeness, harmonic, lin, reachable};
     double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     for (int k = 0; k < 4; ++k)
         if (outs[k]) dev[k] = is_device_ptr(outs[k]) ? outs[k] : tmp.alloc<double>(n);
     if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
@@ -1022,7 +1031,7 @@ hb_status hb_get_run_accumulators(hb_graph *g, int32_t run, double *sumd, double
     const int64_t n = g->n;
     double *outs[2] = {sumd, harm};
     const double *src[2] = {g->a.sumd, g->a.harm};
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
         if (!outs[k]) continue;
@@ -1042,7 +1051,7 @@ hb_status hb_get_run_stats(hb_graph *g, int32_t which, double *mean, double *sd)
     if (st != HB_OK) return st;
     if (which < 0 || which > 3) return fail(HB_ERR_INVALID, "which must lie in [0, 3]");
     const int64_t n = g->n;
-    DevMem tmp;
+    DevMem tmp = scratch(g);
     double *dm = mean ? (is_device_ptr(mean) ? mean : tmp.alloc<double>(n)) : nullptr;
     double *ds = sd ? (is_device_ptr(sd) ? sd : tmp.alloc<double>(n)) : nullptr;
     if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
