@@ -294,7 +294,8 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out);
 /* Free every resource of the handle (NULL is allowed). */
 void hb_destroy(hb_graph *g);
 
-/* Device memory: handles take their device memory from a pool of the
+/* Device memory (no counterpart in the paper: how the library holds its
+ * buffers).  Handles take their device memory from a pool of the
  * library's own (one per device, stream-ordered on the handle's stream),
  * and what hb_destroy frees stays in that pool for later handles, so that
  * creating and destroying handles needs no device-wide synchronisation and

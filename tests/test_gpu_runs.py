@@ -187,3 +187,34 @@ def test_runs_in_one_handle_fp32_host_csr_and_limits(orc):
         with pytest.raises(hbl.HBError) as e:
             hbl.HyperBall.runs(d_off, d_tgt, b, seeds, n=n)
         assert e.value.status == hbl.HB_ERR_INVALID
+
+
+@pytest.mark.parametrize("relabel,transpose", [(False, False), (True, True)])
+def test_runs_in_one_handle_layouts(orc, relabel, transpose):
+    """Without the degree relabelling, and with the transpose taken on the
+    device (HB_TRANSPOSE): each run still equals its solo oracle run on the
+    scanned graph."""
+    g = graphs.rmat_graph(scale=11, edge_factor=8, seed=77)
+    off, tgt = g.numpy()
+    b, seeds = 5, [3, 4, 5, 6]
+    if transpose:
+        gt = graphs.transpose(g)          # hand over G^T, scan its transpose (= g)
+        d_off, d_tgt = to_dev(*gt.numpy())
+    else:
+        d_off, d_tgt = to_dev(off, tgt)
+    hb = hbl.HyperBall.runs(d_off, d_tgt, b, seeds, n=off.size - 1, relabel=relabel, transpose=transpose)
+    hb.run()
+    check_wide(orc, hb, off, tgt, b, seeds)
+    hb.close()
+
+
+def test_runs_in_one_handle_empty_and_edgeless():
+    for n in (0, 5):
+        off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+        tgt = torch.zeros(0, dtype=torch.int32, device="cuda")
+        hb = hbl.HyperBall.runs(off, tgt, 4, [1, 2], n=n)
+        assert hb.run() == 1
+        assert hb.run_steps() == [1, 1]
+        mean, sd = hb.run_stats("closeness")
+        assert mean.numel() == n and not mean.any() and not sd.any()
+        hb.close()
