@@ -1011,6 +1011,7 @@ void serve_loop(hb_server *S) {
         {
             std::unique_lock<std::mutex> lk(S->mu);
             // admission: FIFO, into free slots, while device memory allows
+            bool trimmed = false;
             for (int slot = 0; slot < k && !S->queue.empty(); ++slot) {
                 if (S->slot_req[slot] >= 0) continue;
                 const int64_t id = S->queue.front();
@@ -1024,7 +1025,23 @@ void serve_loop(hb_server *S) {
                 cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrUsedMemCurrent, &used);
                 const int64_t avail = (int64_t)free_b + (int64_t)(reserved - used);
                 const int64_t need = (int64_t)run_bytes(tmpl) + 32 * tmpl->n + 4096;
-                if (avail < need + S->opt.reserve_bytes) break;
+                if (avail < need + S->opt.reserve_bytes) {
+                    // memory cached by the library's own pool (freed by
+                    // handles destroyed earlier) goes back to the device first
+                    cudaMemPool_t lib = library_pool();
+                    size_t lres = 0, lused = 0;
+                    if (!trimmed && lib &&
+                        cudaMemPoolGetAttribute(lib, cudaMemPoolAttrReservedMemCurrent, &lres) == cudaSuccess &&
+                        cudaMemPoolGetAttribute(lib, cudaMemPoolAttrUsedMemCurrent, &lused) == cudaSuccess &&
+                        lres > lused && avail + (int64_t)(lres - lused) >= need + S->opt.reserve_bytes) {
+                        cudaStreamSynchronize(b->s);
+                        cudaMemPoolTrimTo(lib, lused);
+                        trimmed = true;   // once per admission pass
+                        --slot;
+                        continue;
+                    }
+                    break;
+                }
                 S->queue.pop_front();
                 lk.unlock();
                 hb_graph *inst = nullptr;
