@@ -202,15 +202,10 @@ hb_status setup_shared(hb_graph *g) {
     e = launch_dense_plan(a, g->y, g->seg_count, const_cast<Plan *>(a.plan_dense),
                           const_cast<int32_t *>(a.owner_dense), const_cast<int64_t *>(a.cstart_dense), s);
     if (e != cudaSuccess) return cuda_fail(e, "dense plan");
-    int dev = 0, sms = 0, l2 = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     g->step_grid = sms * (g->lruns ? runs_step_blocks_per_sm(g->b, g->fp32) : step_blocks_per_sm(g->b, g->fp32));
-    // counters of the most gathered nodes (lowest ids after the degree sort)
-    // that fit in half of L2, for the optional eviction hints
-    const int64_t hot = g->relabel ? ((int64_t)l2 / 2) / P : 0;
-    a.hot_nodes = (int32_t)(hot < n ? hot : n);
     return HB_OK;
 }
 

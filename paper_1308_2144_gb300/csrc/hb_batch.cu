@@ -373,13 +373,6 @@ __global__ void batch_end_kernel(BatchArrays B) {
     }
 }
 
-int grid_for(int64_t work, int threads) {
-    int64_t g = (work + threads - 1) / threads;
-    if (g < 1) g = 1;
-    if (g > 152 * 32) g = 152 * 32;
-    return (int)g;
-}
-
 // Sec. 5 (multiple runs): per node u of the caller's order, the mean and
 // the empirical (sample, k-1) standard deviation over the k graphs of the
 // batch of one centrality (which: 0 closeness, 1 harmonic, 2 Lin,

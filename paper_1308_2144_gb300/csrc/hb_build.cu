@@ -302,13 +302,6 @@ __global__ void dense_list_kernel(const int64_t *off, int64_t n, SegBounds sb, c
     }
 }
 
-int grid_for(int64_t work, int threads) {
-    int64_t g = (work + threads - 1) / threads;
-    if (g < 1) g = 1;
-    if (g > 152 * 32) g = 152 * 32;
-    return (int)g;
-}
-
 SegBounds bounds_of(const Layout &y) {
     SegBounds sb;
     for (int s = 0; s < kSegs; ++s) { sb.lo[s] = y.lo[s]; sb.hi[s] = y.hi[s]; }

@@ -147,7 +147,6 @@ struct StepArgs {
     int32_t b;
     int32_t frontier;             // HB_FRONTIER_* policy
     int32_t has_reverse;          // roff/rtgt present
-    int32_t hot_nodes;            // counters of nodes below this id are kept in L2
     int32_t aps;                  // class sizing (arcs per slot) of the layout
     int32_t push_union;           // frontier iterations push changed counters along reverse arcs
     int32_t flen;                 // entries of ftab
@@ -158,6 +157,15 @@ struct StepArgs {
 };
 
 // ------------------------------------------------------------ helpers --
+
+// Blocks for a grid-stride loop over `work` items: enough to cover it, at
+// most 32 resident blocks' worth per SM of the 152.
+inline int grid_for(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;
+    return (int)g;
+}
 
 // Byte-wise maximum of two words whose bytes are all below 128.  Register
 // values never exceed 64 - b <= 60, so in t = a + 0x80808080 - b every byte
@@ -209,29 +217,6 @@ __device__ __forceinline__ uint4 shfl_xor16(uint4 a, int o) {
 // Counter loads: the read buffer does not change during a step.
 __device__ __forceinline__ uint4 ld_counter(const uint8_t *p) {
     return __ldg(reinterpret_cast<const uint4 *>(p));
-}
-
-// Counter loads with an L2 eviction policy (from createpolicy): counters of
-// the most gathered nodes (low ids after the degree sort) are kept with
-// evict_last, the rest use evict_first so they do not displace them.
-__device__ __forceinline__ uint4 ld_counter_policy(const uint8_t *p, uint64_t pol) {
-    uint4 r;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
-                 : "l"(p), "l"(pol));
-    return r;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
 }
 
 // Targets are streamed once per step.

@@ -149,13 +149,6 @@ __global__ void gather_strided_kernel(const double *src, const int32_t *inv, int
     }
 }
 
-int grid_for(int64_t work, int threads) {
-    int64_t g = (work + threads - 1) / threads;
-    if (g < 1) g = 1;
-    if (g > 152 * 32) g = 152 * 32;
-    return (int)g;
-}
-
 template <bool F32>
 const void *runs_step_ptr(int log2row) {
     switch (log2row) {

@@ -342,13 +342,6 @@ __global__ void frontier_out_kernel(StepArgs a, const int32_t *inv, uint8_t *cha
     }
 }
 
-int grid_for(int64_t work, int threads) {
-    int64_t g = (work + threads - 1) / threads;
-    if (g < 1) g = 1;
-    if (g > 152 * 32) g = 152 * 32;
-    return (int)g;
-}
-
 template <bool F32>
 cudaError_t launch_step_t(const StepArgs &a, int log2m, int grid, cudaStream_t s) {
     switch (log2m) {

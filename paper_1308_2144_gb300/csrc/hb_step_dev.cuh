@@ -15,11 +15,8 @@
 #ifndef HB_MIN_BLOCKS
 #define HB_MIN_BLOCKS 5
 #endif
-// L2 eviction hints on counter gathers, and streaming stores for data the
-// next iteration reads only after it has left L2.
-#ifndef HB_CACHE_HINTS
-#define HB_CACHE_HINTS 0
-#endif
+// Streaming stores for data the next iteration reads only after it has
+// left L2.
 #ifndef HB_STREAM_STORES
 #define HB_STREAM_STORES 1
 #endif
@@ -71,7 +68,7 @@ template <int LOG2P, int UMAX>
 __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
                                             const uint8_t *__restrict__ cur, int64_t e,
                                             int64_t eend, int logS, int cl,
-                                            uint4 (&acc)[Cfg<LOG2P>::CPL], uint32_t hot) {
+                                            uint4 (&acc)[Cfg<LOG2P>::CPL]) {
     using C = Cfg<LOG2P>;
     constexpr int U0 = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
     constexpr int U = U0 < UMAX ? U0 : UMAX;
@@ -79,12 +76,6 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
     const int cnt = (int)((eend - e + (1LL << logS) - 1) >> logS);
     const int32_t *tp = tgt + e;
     const uint8_t *base = cur + cl * 16;
-#if HB_CACHE_HINTS
-    const uint64_t pol_last = policy_evict_last(), pol_first = policy_evict_first();
-#define HB_GATHER(addr, w) ld_counter_policy((addr), (uint32_t)(w) < hot ? pol_last : pol_first)
-#else
-#define HB_GATHER(addr, w) ld_counter(addr)
-#endif
     int j = 0;
     for (; j + U <= cnt; j += U) {
         int32_t w[U];
@@ -95,7 +86,7 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c)
-                g[u][c] = HB_GATHER(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, w[u]);
+                g[u][c] = ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16);
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -111,13 +102,12 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c)
-                g[u][c] = w[u] >= 0 ? HB_GATHER(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, w[u]) : z;
+                g[u][c] = w[u] >= 0 ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16) : z;
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
     }
-#undef HB_GATHER
 }
 
 // Pull the node's accumulators and cached estimate into L2 while its
@@ -403,13 +393,13 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
     if (logS == C::LOGSMAX)
-        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
+        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
     else if (a.aps <= 2)
-        gather_arcs<LOG2P, 2>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
+        gather_arcs<LOG2P, 2>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
     else if (a.aps <= 4)
-        gather_arcs<LOG2P, 4>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
+        gather_arcs<LOG2P, 4>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
     else
-        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, (uint32_t)a.hot_nodes);
+        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
@@ -444,7 +434,7 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, (uint32_t)a.hot_nodes);
+    gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc);
 #pragma unroll
     for (int o = C::L; o < 32; o <<= 1)
 #pragma unroll
