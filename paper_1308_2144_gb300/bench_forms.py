@@ -154,9 +154,18 @@ def serve_run(pool, args, slots, label):
     L = np.array([lat[j] for j in sel])
     arcs = sum(infos[j]["arcs"] for j in sel)
     window = max(done_wall[j] for j in sel) - args.warm
+    # latency by request size: graphs in the top quarter of the pool by arcs
+    big_m = np.quantile([g.m for g in pool], 0.75)
+    big = np.array([pool[jobs[j][1]].m >= big_m for j in sel])
+    by_size = {}
+    for key, mask in (("large_quarter", big), ("rest", ~big)):
+        if mask.any():
+            by_size[key] = {"requests": int(mask.sum()), "p50_s": float(np.percentile(L[mask], 50)),
+                            "p99_s": float(np.percentile(L[mask], 99))}
     return {"form": "served", "server": label, "slots": slots, "rate_per_s": args.rate,
             "requests": len(sel), "p50_latency_s": float(np.percentile(L, 50)),
             "p99_latency_s": float(np.percentile(L, 99)), "mean_latency_s": float(L.mean()),
+            "latency_by_size": by_size,
             "arc_updates_per_s": arcs / window, "drain_s": round(end - total, 2),
             "estimate": "fp32" if args.fp32 else "fp64", "pool_graphs": len(pool),
             "pool_arcs": int(sum(g.m for g in pool))}
