@@ -16,6 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhyperball.so")
+# the same library with every arc target range-checked in the gather (HB_DEBUG)
+LIB_DEBUG = os.path.join(HERE, "libhyperball_debug.so")
 SOURCES = ["hb_build.cu", "hb_step.cu", "hb_runs.cu", "hb_api.cu", "hb_noalloc.cu", "hb_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -34,16 +36,23 @@ def _deps():
         os.path.join(ROOT, "include", "hyperball.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=(), out: str | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra=(), out: str | None = None,
+          debug: bool = False) -> str:
     """Compile and link; ``extra`` nvcc flags (e.g. -D tuning macros) and a
-    different output path serve tuning sweeps."""
+    different output path serve tuning sweeps.  ``debug`` builds
+    libhyperball_debug.so, whose gather checks every arc target."""
+    if debug:
+        if not force and up_to_date(LIB_DEBUG):
+            return LIB_DEBUG
+        extra = tuple(extra) + ("-DHB_DEBUG=1",)
+        out = out or LIB_DEBUG
     lib = out or LIB
     if not force and not extra and out is None and up_to_date():
         return LIB
@@ -74,5 +83,5 @@ def build(force: bool = False, verbose: bool = False, extra=(), out: str | None 
 
 if __name__ == "__main__":
     import sys
-    build(force=True, verbose="-v" in sys.argv, extra=("-Xptxas", "-v") if "-v" in sys.argv else ())
-    print(LIB)
+    print(build(force=True, verbose="-v" in sys.argv, extra=("-Xptxas", "-v") if "-v" in sys.argv else (),
+                debug="--debug" in sys.argv))

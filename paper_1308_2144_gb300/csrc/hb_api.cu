@@ -373,6 +373,7 @@ hb_status finish_setup(hb_graph *g) {
 }
 
 hb_status init_state(hb_graph *g, uint64_t seed) {
+    NvtxRange nv("init");
     g->seed = seed;
     cudaError_t e = launch_init(g->a, g->perm, seed, g->fp32, g->s, g->wfirst);
     g->launches += g->n > 0 ? 2 : 1;
@@ -451,6 +452,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         if (e != cudaSuccess) { delete g; return cuda_fail(e, "run seeds"); }
     }
 
+    NvtxRange nv_create("hb_create");
     // 1. input CSR on the device (int64 offsets)
     const bool borrow = (o.flags & HB_BORROW_DEVICE_PTRS) != 0;
     const bool off_dev = is_device_ptr(offsets), tgt_dev = m == 0 || is_device_ptr(targets);
@@ -489,9 +491,12 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     unsigned long long err_host = 0;
     if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory"); }
     cudaMemsetAsync(err_dev, 0, sizeof(unsigned long long), s);
-    e = validate_csr(in_off, in_tgt, n, m, err_dev, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&err_host, err_dev, sizeof(err_host), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    {
+        NvtxRange nv("validate");
+        e = validate_csr(in_off, in_tgt, n, m, err_dev, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&err_host, err_dev, sizeof(err_host), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     M.release(err_dev);
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "validation"); }
     if (err_host) {
@@ -519,6 +524,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
 
     // 4. degree-sorted relabelling
     if (g->relabel) {
+        NvtxRange nv("relabel");
         g->perm = M.alloc<int32_t>(n);
         g->inv = M.alloc<int32_t>(n);
         int64_t *noff = M.alloc<int64_t>(n + 1);
@@ -537,7 +543,11 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         g->tgt = in_tgt;
     }
 
-    hb_status st = finish_setup(g);
+    hb_status st;
+    {
+        NvtxRange nv("setup");
+        st = finish_setup(g);
+    }
     if (st == HB_OK) st = init_state(g, seed);
     if (st != HB_OK) { delete g; return st; }
     *out = g;
@@ -607,6 +617,7 @@ hb_status hb_create32(const int32_t *offsets, const int32_t *targets, int64_t n,
 hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    NvtxRange nv("hb_step");
     cudaError_t e = launch_iteration(g->a, g->y, g->fp32, g->step_grid, g->s, g->profile ? g->ev : nullptr,
                                      &g->launches);
     if (e == cudaSuccess && g->track_nf) {
@@ -623,7 +634,10 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     const Counters &c = *g->ctr_host;
     if (c.err) {
         g->broken = true;
-        return fail(HB_ERR_STATE, "a device-side check failed during the step");
+        std::string why = "a device-side check failed during the step:";
+        if (c.err & kErrCasBound) why += " the pushed union's compare-and-swap loop reached its bound;";
+        if (c.err & kErrTarget) why += " an arc target lies outside [0, n) (debug build check);";
+        return fail(HB_ERR_STATE, why);
     }
     g->t = c.steps_done;
     g->last_changed = (int64_t)c.n_changed;
@@ -675,6 +689,7 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
 hb_status hb_run_to_fixpoint(hb_graph *g, int32_t *steps) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    NvtxRange nv("hb_run_to_fixpoint");
     while (!g->converged && g->t < g->opt.max_steps) {
         st = hb_step(g, nullptr);
         if (st != HB_OK) return st;
@@ -689,6 +704,7 @@ hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic, 
     hb_status st = check(g);
     if (st != HB_OK) return st;
     if (g->lruns) return fail(HB_ERR_STATE, "a handle of several runs: use hb_get_run_centralities");
+    NvtxRange nv("hb_get_centralities");
     const int64_t n = g->n;
     double *outs[4] = {closeness, harmonic, lin, reachable};
     double *dev[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -740,6 +740,7 @@ hb_status hb_batch_get_run_stats(hb_batch *b, int32_t which, double *mean, doubl
 
 hb_status hb_batch_step(hb_batch *b, int32_t *n_active) {
     if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    NvtxRange nv("hb_batch_step");
     cudaError_t e = cudaGraphLaunch(b->step_exec, b->s);
     if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
     hb_status st = read_ctl(b);
@@ -750,6 +751,7 @@ hb_status hb_batch_step(hb_batch *b, int32_t *n_active) {
 
 hb_status hb_batch_run(hb_batch *b, int32_t *iterations) {
     if (!b) return bfail(HB_ERR_INVALID, "batch is NULL");
+    NvtxRange nv("hb_batch_run");
     cudaError_t e = cudaGraphLaunch(b->run_exec, b->s);
     if (e != cudaSuccess) return bfail(HB_ERR_CUDA, std::string("batch run: ") + cudaGetErrorString(e));
     hb_status st = read_ctl(b);
@@ -1067,6 +1069,7 @@ void serve_loop(hb_server *S) {
             }
         }
         const double t_start = S->now();
+        NvtxRange nv("serve iteration");
         cudaError_t e = cudaSuccess;
         if (changed) {
             e = publish_slots(S);

@@ -5,10 +5,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hb_internal.cuh"
 #include "hyperball.h"
 
 namespace hb {
+
+// A named range on the host timeline of NVIDIA's profilers (NVTX), for the
+// life of the object; costs a check and nothing else when no profiler is
+// attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Device allocations owned by a handle, freed together.
 struct DevMem {

@@ -14,6 +14,10 @@ constexpr int kSegs = 7;          // segment 0: heavy nodes; 1..6: light classes
 constexpr int kArcsPerSlot = 16;  // default class sizing: about this many arcs per lane slot
 constexpr int kStepThreads = 256;
 constexpr int kBigRdeg = 1024;    // changed nodes with more predecessors are pushed grid-wide
+// Bits of Counters::err, the device-side error word the host reads after
+// every iteration (and turns into HB_ERR_STATE).
+constexpr unsigned long long kErrCasBound = 2;  // the pushed union's CAS loop hit its bound
+constexpr unsigned long long kErrTarget = 4;    // debug builds: an arc target outside [0, n)
 
 // Per-p layout of a counter across the lanes of a warp.  A counter of P
 // bytes is CH 16-byte chunks; L lanes ("chunk lanes") hold one arc's
@@ -192,7 +196,7 @@ __device__ __forceinline__ void atomic_bmax4(uint32_t *addr, uint32_t v, unsigne
         old = seen;
         nv = bmax4(old, v);
         if (guard == 1024) {
-            atomicOr(err, 2ull);
+            atomicOr(err, kErrCasBound);
             return;
         }
     }

@@ -20,6 +20,12 @@
 #ifndef HB_STREAM_STORES
 #define HB_STREAM_STORES 1
 #endif
+// Debug builds (libhyperball_debug.so, HB_DEBUG=1) check every arc target
+// against [0, n) before its counter is read: a target outside sets
+// kErrTarget in the device error word and its arc is skipped.
+#ifndef HB_DEBUG
+#define HB_DEBUG 0
+#endif
 
 namespace hb {
 namespace dev {
@@ -61,14 +67,28 @@ __device__ __forceinline__ void mark_append(const StepArgs &a, int32_t u, int la
     if (lane == 0 && dd) atomicAdd(&a.ctr->arcs, dd);
 }
 
+// An arc's target, checked against [0, n) in debug builds (-1 if outside).
+__device__ __forceinline__ int32_t arc_target(const int32_t *p, int64_t n, unsigned long long *err) {
+    const int32_t w = ld_stream(p);
+#if HB_DEBUG
+    if ((uint64_t)(uint32_t)w >= (uint64_t)n) {
+        atomicOr(err, kErrTarget);
+        return -1;
+    }
+#endif
+    return w;
+}
+
 // Gather the counters of arcs e, e+S, ... < eend (S = 2^logS) into acc
 // (this lane's chunks), U arcs in flight per lane; full groups of U arcs
-// run without bounds checks.
+// run without bounds checks (targets were validated at creation; debug
+// builds check them here).  n and err serve the debug check only.
 template <int LOG2P, int UMAX>
 __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
                                             const uint8_t *__restrict__ cur, int64_t e,
                                             int64_t eend, int logS, int cl,
-                                            uint4 (&acc)[Cfg<LOG2P>::CPL]) {
+                                            uint4 (&acc)[Cfg<LOG2P>::CPL], int64_t n,
+                                            unsigned long long *err) {
     using C = Cfg<LOG2P>;
     constexpr int U0 = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
     constexpr int U = U0 < UMAX ? U0 : UMAX;
@@ -80,13 +100,18 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
     for (; j + U <= cnt; j += U) {
         int32_t w[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) w[u] = ld_stream(tp + ((j + u) << logS));
+        for (int u = 0; u < U; ++u) w[u] = arc_target(tp + ((j + u) << logS), n, err);
         uint4 g[U][C::CPL];
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c)
+#if HB_DEBUG
+                g[u][c] = w[u] >= 0 ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                                    : make_uint4(0u, 0u, 0u, 0u);
+#else
                 g[u][c] = ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16);
+#endif
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -96,7 +121,7 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
         int32_t w[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) w[u] = j + u < cnt ? ld_stream(tp + ((j + u) << logS)) : -1;
+        for (int u = 0; u < U; ++u) w[u] = j + u < cnt ? arc_target(tp + ((j + u) << logS), n, err) : -1;
         uint4 g[U][C::CPL];
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -393,13 +418,13 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
     if (logS == C::LOGSMAX)
-        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
+        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
     else if (a.aps <= 2)
-        gather_arcs<LOG2P, 2>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
+        gather_arcs<LOG2P, 2>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
     else if (a.aps <= 4)
-        gather_arcs<LOG2P, 4>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
+        gather_arcs<LOG2P, 4>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
     else
-        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc);
+        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
@@ -434,7 +459,7 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc);
+    gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err);
 #pragma unroll
     for (int o = C::L; o < 32; o <<= 1)
 #pragma unroll
