@@ -400,6 +400,7 @@ void hb_batch_destroy(hb_batch *b);
 #define HB_REQ_RUNNING 1
 #define HB_REQ_DONE    2
 #define HB_REQ_FAILED  3
+#define HB_REQ_CANCELLED 4
 
 typedef struct {
     int32_t slots;            /* requests on the device at once, 1..4096 (1 = FIFO one at a time) */
@@ -428,10 +429,20 @@ hb_status hb_server_add_graph(hb_server *s, const int64_t *offsets, const int32_
 hb_status hb_server_submit(hb_server *s, int32_t graph_id, int32_t log2m, uint64_t seed,
                            int64_t *request_id);
 /* Wait until the request is done (timeout_s < 0: no limit; HB_ERR_TIMEOUT
- * if it ran out).  info may be NULL. */
+ * if it ran out).  info may be NULL.  A failed request returns its error:
+ * HB_ERR_OOM when it was refused (its device memory plus reserve_bytes
+ * exceeds the device, or it does not fit while none of the server's
+ * requests is running); a cancelled one returns HB_ERR_STATE with
+ * info->state = HB_REQ_CANCELLED. */
 hb_status hb_server_wait(hb_server *s, int64_t request_id, double timeout_s, hb_request_info *info);
+/* Cancel a request: a queued one leaves the queue at once; a running one is
+ * retired at the next iteration boundary (its slot and device memory are
+ * freed, the other requests are untouched).  HB_ERR_STATE if it has
+ * already finished. */
+hb_status hb_server_cancel(hb_server *s, int64_t request_id);
 /* Copy a finished request's centralities (n doubles each, host memory, any
- * may be NULL) and forget the request. */
+ * may be NULL) and forget the request; a failed or cancelled request is
+ * forgotten with HB_ERR_STATE. */
 hb_status hb_server_take(hb_server *s, int64_t request_id, double *closeness, double *harmonic,
                          double *lin, double *reachable);
 /* Completed requests, batched iterations, arc-updates, seconds with work on

@@ -909,6 +909,7 @@ struct ServeReq {
     hb_status err = HB_OK;
     int64_t n = 0;
     double *dres = nullptr;   // device: closeness, harmonic, lin, reachable (n each)
+    bool cancel = false;      // running: retire at the next iteration boundary
 };
 
 struct PoolGraph {
@@ -1020,6 +1021,20 @@ void serve_loop(hb_server *S) {
                 cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrUsedMemCurrent, &used);
                 const int64_t avail = (int64_t)free_b + (int64_t)(reserved - used);
                 const int64_t need = (int64_t)run_bytes(tmpl) + 32 * tmpl->n + 4096;
+                bool any_running = false;
+                for (int q = 0; q < k; ++q) any_running |= S->slot_req[q] >= 0;
+                if (need + S->opt.reserve_bytes > (int64_t)total_b ||
+                    (trimmed && !any_running && avail < need + S->opt.reserve_bytes)) {
+                    // can never fit, or does not fit while none of the
+                    // server's requests holds memory: refuse it
+                    S->queue.pop_front();
+                    r.state = HB_REQ_FAILED;
+                    r.err = HB_ERR_OOM;
+                    r.t_done = S->now();
+                    S->done_cv.notify_all();
+                    --slot;
+                    continue;
+                }
                 if (avail < need + S->opt.reserve_bytes) {
                     // memory cached by the library's own pool (freed by
                     // handles destroyed earlier) goes back to the device first
@@ -1032,6 +1047,11 @@ void serve_loop(hb_server *S) {
                         cudaStreamSynchronize(b->s);
                         cudaMemPoolTrimTo(lib, lused);
                         trimmed = true;   // once per admission pass
+                        --slot;
+                        continue;
+                    }
+                    if (!trimmed && !any_running) {   // refused above on the next look
+                        trimmed = true;
                         --slot;
                         continue;
                     }
@@ -1101,6 +1121,27 @@ void serve_loop(hb_server *S) {
             ServeReq &r = *running_req[slot];
             r.steps += 1;
             const bool capped = r.steps >= S->opt.max_steps;
+            bool cancel;
+            {
+                std::lock_guard<std::mutex> lk(S->mu);
+                cancel = r.cancel;
+            }
+            if (cancel) {
+                // retired without results; the other slots are untouched
+                hb_destroy(r.inst);
+                std::lock_guard<std::mutex> lk(S->mu);
+                r.inst = nullptr;
+                r.slot = -1;
+                r.err = HB_ERR_STATE;
+                r.state = HB_REQ_CANCELLED;
+                r.t_done = S->now();
+                S->slot_req[slot] = -1;
+                S->slot_args[slot] = null_slot(S, slot);
+                running_req[slot] = nullptr;
+                freed = true;
+                S->done_cv.notify_all();
+                continue;
+            }
             if (!done[slot] && !capped) continue;
             hb_graph *inst = r.inst;
             hb_status st = sync_host_state(inst);
@@ -1291,8 +1332,33 @@ hb_status hb_server_wait(hb_server *S, int64_t request_id, double timeout_s, hb_
         info->done_s = r.t_done;
     }
     if (r.state == HB_REQ_QUEUED || r.state == HB_REQ_RUNNING) return sfail(HB_ERR_TIMEOUT, "request not finished");
-    if (r.state == HB_REQ_FAILED) return sfail(r.err, "request failed");
+    if (r.state == HB_REQ_CANCELLED) return sfail(HB_ERR_STATE, "request cancelled");
+    if (r.state == HB_REQ_FAILED)
+        return sfail(r.err, r.err == HB_ERR_OOM ? "request refused: its device memory cannot be had"
+                                                : "request failed");
     return HB_OK;
+}
+
+hb_status hb_server_cancel(hb_server *S, int64_t request_id) {
+    if (!S) return sfail(HB_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request_id);
+    if (it == S->reqs.end()) return sfail(HB_ERR_INVALID, "unknown request");
+    ServeReq &r = it->second;
+    if (r.state == HB_REQ_QUEUED) {
+        for (auto q = S->queue.begin(); q != S->queue.end(); ++q)
+            if (*q == request_id) { S->queue.erase(q); break; }
+        r.state = HB_REQ_CANCELLED;
+        r.err = HB_ERR_STATE;
+        r.t_done = S->now();
+        S->done_cv.notify_all();
+        return HB_OK;
+    }
+    if (r.state == HB_REQ_RUNNING) {
+        r.cancel = true;
+        return HB_OK;
+    }
+    return sfail(HB_ERR_STATE, "request already finished");
 }
 
 hb_status hb_server_take(hb_server *S, int64_t request_id, double *closeness, double *harmonic, double *lin,
@@ -1305,6 +1371,11 @@ hb_status hb_server_take(hb_server *S, int64_t request_id, double *closeness, do
         auto it = S->reqs.find(request_id);
         if (it == S->reqs.end()) return sfail(HB_ERR_INVALID, "unknown request");
         ServeReq &r = it->second;
+        if (r.state == HB_REQ_FAILED || r.state == HB_REQ_CANCELLED) {
+            if (r.dres) cudaFreeAsync(r.dres, S->copy_stream);
+            S->reqs.erase(it);
+            return sfail(HB_ERR_STATE, "request failed or cancelled; forgotten");
+        }
         if (r.state != HB_REQ_DONE) return sfail(HB_ERR_STATE, "request not done");
         dres = r.dres;
         n = r.n;

@@ -39,7 +39,7 @@ HB_NEIGHBOURHOOD = 0x40
 
 FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
 
-HB_REQ_QUEUED, HB_REQ_RUNNING, HB_REQ_DONE, HB_REQ_FAILED = 0, 1, 2, 3
+HB_REQ_QUEUED, HB_REQ_RUNNING, HB_REQ_DONE, HB_REQ_FAILED, HB_REQ_CANCELLED = 0, 1, 2, 3, 4
 
 # every symbol include/hyperball.h declares
 EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_to_fixpoint",
@@ -52,7 +52,7 @@ EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
            "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
            "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
-           "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_take",
+           "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_cancel", "hb_server_take",
            "hb_server_stats", "hb_server_destroy"]
 
 
@@ -221,6 +221,8 @@ def load():
                                        ctypes.POINTER(ctypes.c_int64)]
         L.hb_server_wait.restype = st
         L.hb_server_wait.argtypes = [_vp, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(RequestInfo)]
+        L.hb_server_cancel.restype = st
+        L.hb_server_cancel.argtypes = [_vp, ctypes.c_int64]
         L.hb_server_take.restype = st
         L.hb_server_take.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
         L.hb_server_stats.restype = st
@@ -550,6 +552,9 @@ class HyperBallServer:
         info = RequestInfo()
         _check(load().hb_server_wait(self._h, int(request_id), float(timeout), ctypes.byref(info)))
         return info.as_dict()
+
+    def cancel(self, request_id):
+        _check(load().hb_server_cancel(self._h, int(request_id)))
 
     def take(self, request_id, n, out=None) -> dict:
         """Copy a finished request's centralities into `out` (a dict of

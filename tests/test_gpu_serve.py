@@ -80,3 +80,74 @@ def test_server_rejects_unknown_graph_and_log2m():
     with pytest.raises(hbl.HBError):
         srv.submit(gid, 6, 1)
     srv.close()
+
+
+def _state(srv, rid):
+    info = hbl.RequestInfo()
+    st = hbl.load().hb_server_wait(srv._h, int(rid), 0.0, hbl.ctypes.byref(info))
+    return st, info.state
+
+
+def test_cancel_queued_and_running_requests():
+    pool = _pool()
+    big = graphs.rmat_graph(scale=18, edge_factor=16, seed=6)
+    srv = hbl.HyperBallServer(slots=1, reserve_bytes=0)
+    gids = [srv.add_graph(g.offsets.cuda(), g.targets.cuda(), g.n, log2ms=(4, 6)) for g in pool]
+    gbig = srv.add_graph(big.offsets.cuda(), big.targets.cuda(), big.n, log2ms=(6,))
+    # one slot: the first request runs, the next two wait in the queue
+    r0 = srv.submit(gbig, 6, 1)
+    r1 = srv.submit(gids[0], 4, 2)
+    r2 = srv.submit(gids[2], 4, 3)
+    srv.cancel(r1)                       # queued: leaves the queue at once
+    with pytest.raises(hbl.HBError) as e:
+        srv.wait(r1, timeout=10)
+    assert e.value.status == hbl.HB_ERR_STATE
+    assert _state(srv, r1)[1] == hbl.HB_REQ_CANCELLED
+    for rid, g, b, seed in ((r0, big, 6, 1), (r2, pool[2], 4, 3)):
+        info = srv.wait(rid, timeout=120)
+        steps, solo = _solo(g, b, seed)
+        assert info["steps"] == steps
+        res = srv.take(rid, g.n)
+        for key in solo:
+            assert np.array_equal(res[key], solo[key]), key
+    with pytest.raises(hbl.HBError) as e:
+        srv.cancel(r0)                   # taken: unknown now
+    with pytest.raises(hbl.HBError) as e:
+        srv.take(r1, pool[0].n)          # a cancelled request is forgotten
+    assert e.value.status == hbl.HB_ERR_STATE
+    # a running request: retired at an iteration boundary, its slot reused
+    r3 = srv.submit(gbig, 6, 9)
+    for _ in range(2000):
+        if _state(srv, r3)[1] != hbl.HB_REQ_QUEUED:
+            break
+        time.sleep(0.001)
+    try:
+        srv.cancel(r3)
+        cancelled = True
+    except hbl.HBError:                  # it finished before the cancel arrived
+        cancelled = False
+    st, state = _state(srv, r3)
+    if cancelled:
+        with pytest.raises(hbl.HBError):
+            srv.wait(r3, timeout=60)
+        assert _state(srv, r3)[1] == hbl.HB_REQ_CANCELLED
+    r4 = srv.submit(gids[1], 6, 4)
+    info = srv.wait(r4, timeout=120)
+    steps, solo = _solo(pool[1], 6, 4)
+    assert info["steps"] == steps
+    res = srv.take(r4, pool[1].n)
+    for key in solo:
+        assert np.array_equal(res[key], solo[key]), key
+    srv.close()
+
+
+def test_request_that_cannot_fit_is_refused():
+    g = graphs.plain_graph(n=2000, seed=1)
+    srv = hbl.HyperBallServer(slots=2, reserve_bytes=1 << 50)   # more than any device has
+    gid = srv.add_graph(g.offsets.cuda(), g.targets.cuda(), g.n, log2ms=(4,))
+    rid = srv.submit(gid, 4, 1)
+    with pytest.raises(hbl.HBError) as e:
+        srv.wait(rid, timeout=30)
+    assert e.value.status == hbl.HB_ERR_OOM
+    assert _state(srv, rid)[1] == hbl.HB_REQ_FAILED
+    srv.close()
