@@ -45,3 +45,21 @@ def test_repeated_handles_and_trim(orc):
     freed = torch.cuda.mem_get_info()[0] - kept
     # the pool held at least the handle's own allocations until the trim
     assert device_bytes > 0 and freed >= device_bytes // 2, (freed, device_bytes)
+
+
+def test_state_beyond_device_memory_is_refused(orc):
+    """A handle whose counters alone (2 x n x 4096 bytes at log2m 12) exceed
+    the device: hb_create returns HB_ERR_OOM and the library keeps working."""
+    free_b, total_b = torch.cuda.mem_get_info()
+    n = min(2**31 - 2, int(total_b // (2 * 4096)) + (1 << 20))
+    off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    tgt = torch.zeros(0, dtype=torch.int32, device="cuda")
+    with pytest.raises(hbl.HBError) as e:
+        hbl.hb_create(off, tgt, n, 0, 12, 1)
+    assert e.value.status == hbl.HB_ERR_OOM
+    del off
+    hbl.hb_trim_memory()
+    g_off, g_tgt = graphs.plain_graph(n=2000, seed=2).numpy()
+    hb = hbl.HyperBall(*to_dev(g_off, g_tgt), log2m=5, seed=3, n=g_off.size - 1)
+    assert hb.run() == orc.run(g_off, g_tgt, 5, 3).steps
+    hb.close()
