@@ -213,7 +213,8 @@ hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot);
  * The computation restarts from t = 0 with the handle's current seed.
  * Initialisation costs one hash per replica, w(u) of them in one thread.
  * HB_ERR_INVALID (handle unchanged) if a weight is out of range.
- * Single-graph handles only (not the batched or served forms). */
+ * Single-graph handles, of one run or several (hb_create_runs: each run
+ * hashes the replicas with its own seed); not the batched or served forms. */
 hb_status hb_set_weights(hb_graph *g, const int64_t *weights);
 
 /* Discount function (Sec. 7): a further per-node accumulator
@@ -222,11 +223,13 @@ hb_status hb_set_weights(hb_graph *g, const int64_t *weights);
  * weighted by w(y) under hb_set_weights.  f(d) = f[d-1] for d = 1..len and
  * 0 for longer distances; f is host or device memory, copied.  len = 0 (f
  * may then be NULL) removes the accumulator.  The computation restarts from
- * t = 0 with the handle's current seed.  Single-graph handles only. */
+ * t = 0 with the handle's current seed.  Single-graph handles, of one run
+ * or several (one accumulator per run: hb_get_run_discounted). */
 hb_status hb_set_discount(hb_graph *g, const double *f, int32_t len);
 
 /* The discounted accumulator, n doubles in the caller's node order (host or
- * device).  HB_ERR_STATE if no discount is set. */
+ * device).  HB_ERR_STATE if no discount is set or the handle holds several
+ * runs (hb_get_run_discounted). */
 hb_status hb_get_discounted(hb_graph *g, double *out);
 
 /* The neighbourhood function (the aggregate that ANF and HyperANF compute
@@ -259,10 +262,12 @@ hb_status hb_get_neighbourhood(hb_graph *g, double *out, int32_t cap, int32_t *l
  * hb_step, hb_run_to_fixpoint, hb_reset (the seeds are kept; the argument
  * is ignored), hb_tune, hb_set_class_sizing, hb_get_frontier, hb_get_info
  * and hb_destroy work as for one run; hb_get_registers returns rows of
- * runs * p bytes.  Results come from the hb_get_run_* calls below;
- * hb_get_centralities, hb_get_accumulators, weights, discounts and
- * checkpoints return HB_ERR_STATE on such a handle.  Device memory: two
- * rows of runs * p bytes and about 20 * runs + 20 bytes per node. */
+ * runs * p bytes.  hb_set_weights and hb_set_discount apply to every run.
+ * Results come from the hb_get_run_* calls below; hb_get_centralities,
+ * hb_get_accumulators, hb_get_discounted and checkpoints return
+ * HB_ERR_STATE on such a handle.  Device memory: two rows of runs * p
+ * bytes and about 20 * runs + 20 bytes per node (8 * runs more with a
+ * discount). */
 hb_status hb_create_runs(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
                          int log2m, int32_t runs, const uint64_t *seeds, const hb_options *opt,
                          hb_graph **out);
@@ -277,11 +282,15 @@ hb_status hb_get_run_steps(hb_graph *g, int32_t *steps);
 hb_status hb_get_run_centralities(hb_graph *g, int32_t run, double *closeness, double *harmonic,
                                   double *lin, double *reachable);
 hb_status hb_get_run_accumulators(hb_graph *g, int32_t run, double *sumd, double *harm);
+/* Run r's Sec. 7 discounted accumulator (n doubles, host or device);
+ * HB_ERR_STATE without hb_set_discount. */
+hb_status hb_get_run_discounted(hb_graph *g, int32_t run, double *out);
 
 /* Per-node mean and empirical standard deviation (sample form, divisor
  * runs - 1) over the runs of one centrality (which = 0 closeness,
- * 1 harmonic, 2 Lin, 3 reachable), n doubles each in the caller's order,
- * host or device; either may be NULL. */
+ * 1 harmonic, 2 Lin, 3 reachable, 4 the discounted accumulator), n
+ * doubles each in the caller's order, host or device; either may be NULL.
+ * which = 4 without hb_set_discount gives HB_ERR_STATE. */
 hb_status hb_get_run_stats(hb_graph *g, int32_t which, double *mean, double *sd);
 
 /* Checkpoint: write t, counters, last frontier and accumulators (and the

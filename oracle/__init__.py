@@ -304,14 +304,15 @@ def exact_centralities(offsets, targets, sources=None):
     return out
 
 
-def run_stats(offsets, targets, b: int, seeds, which: str, weights=None):
+def run_stats(offsets, targets, b: int, seeds, which: str, weights=None, discount=None):
     """Sec. 5, multiple runs: per node, the mean and the empirical (sample,
     divisor R-1) standard deviation of one centrality over independent runs
-    of Algorithm 2 with the given hash seeds (numpy's mean and std)."""
+    of Algorithm 2 with the given hash seeds (numpy's mean and std).
+    ``which`` = "discounted" takes the Sec. 7 accumulator of ``discount``."""
     vals = []
     for s in seeds:
-        res = run(offsets, targets, b, s, weights=weights)
-        vals.append(finalize(b, res.regs, res.sumd, res.harm)[which])
+        res = run(offsets, targets, b, s, weights=weights, discount=discount)
+        vals.append(res.disc if which == "discounted" else finalize(b, res.regs, res.sumd, res.harm)[which])
     vals = np.array(vals)
     sd = vals.std(axis=0, ddof=1) if len(seeds) > 1 else np.zeros(vals.shape[1])
     return vals.mean(axis=0), sd

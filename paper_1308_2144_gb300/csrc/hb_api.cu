@@ -865,7 +865,6 @@ hb_status hb_reset(hb_graph *g, uint64_t seed) {
 hb_status hb_set_weights(hb_graph *g, const int64_t *weights) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
-    if (g->lruns) return fail(HB_ERR_STATE, "weights need a handle of one run");
     DevMem &M = g->mem;
     if (!weights) {
         if (g->wfirst) M.release(g->wfirst);
@@ -911,7 +910,6 @@ hb_status hb_set_weights(hb_graph *g, const int64_t *weights) {
 hb_status hb_set_discount(hb_graph *g, const double *f, int32_t len) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
-    if (g->lruns) return fail(HB_ERR_STATE, "discounts need a handle of one run");
     if (len < 0) return fail(HB_ERR_INVALID, "len must be >= 0");
     if (len > 0 && !f) return fail(HB_ERR_INVALID, "f is NULL");
     DevMem &M = g->mem;
@@ -926,7 +924,7 @@ hb_status hb_set_discount(hb_graph *g, const double *f, int32_t len) {
         a.flen = 0;
         return init_state(g, g->seed);
     }
-    if (!g->disc) g->disc = M.alloc<double>(g->n);
+    if (!g->disc) g->disc = M.alloc<double>(g->n << g->lruns);   // one per (node, run)
     g->ftab = M.alloc<double>(len);
     if (!g->disc || !g->ftab) {
         if (g->disc) M.release(g->disc);
@@ -950,6 +948,7 @@ hb_status hb_get_discounted(hb_graph *g, double *out) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
     if (!g->a.disc) return fail(HB_ERR_STATE, "no discount function set (hb_set_discount)");
+    if (g->lruns) return fail(HB_ERR_STATE, "a handle of several runs: use hb_get_run_discounted");
     if (g->n > 0 && !out) return fail(HB_ERR_INVALID, "out is NULL");
     const int64_t n = g->n;
     DevMem tmp = scratch(g);
@@ -1057,10 +1056,29 @@ hb_status hb_get_run_accumulators(hb_graph *g, int32_t run, double *sumd, double
     return HB_OK;
 }
 
+hb_status hb_get_run_discounted(hb_graph *g, int32_t run, double *out) {
+    hb_status st = check_runs(g);
+    if (st != HB_OK) return st;
+    if (run < 0 || run >= (1 << g->lruns)) return fail(HB_ERR_INVALID, "run out of range");
+    if (!g->a.disc) return fail(HB_ERR_STATE, "no discount function set (hb_set_discount)");
+    if (g->n > 0 && !out) return fail(HB_ERR_INVALID, "out is NULL");
+    const int64_t n = g->n;
+    DevMem tmp = scratch(g);
+    double *d = is_device_ptr(out) ? out : tmp.alloc<double>(n);
+    if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaError_t e = launch_gather_strided(g->a.disc, g->inv, n, g->lruns, run, d, g->s);
+    if (e == cudaSuccess && d != out) e = to_caller(out, d, sizeof(double) * n, g->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+    tmp.free_all();
+    if (e != cudaSuccess) return cuda_fail(e, "run discounted accumulator");
+    return HB_OK;
+}
+
 hb_status hb_get_run_stats(hb_graph *g, int32_t which, double *mean, double *sd) {
     hb_status st = check_runs(g);
     if (st != HB_OK) return st;
-    if (which < 0 || which > 3) return fail(HB_ERR_INVALID, "which must lie in [0, 3]");
+    if (which < 0 || which > 4) return fail(HB_ERR_INVALID, "which must lie in [0, 4]");
+    if (which == 4 && !g->a.disc) return fail(HB_ERR_STATE, "no discount function set (hb_set_discount)");
     const int64_t n = g->n;
     DevMem tmp = scratch(g);
     double *dm = mean ? (is_device_ptr(mean) ? mean : tmp.alloc<double>(n)) : nullptr;

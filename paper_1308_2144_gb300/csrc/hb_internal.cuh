@@ -404,7 +404,8 @@ cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, b
 // is the row's log2 byte count (a.b); a.gb and a.lruns give the runs.
 cudaError_t launch_runs_step(const StepArgs &a, int log2row, bool fp32, int grid, cudaStream_t s);
 cudaError_t launch_runs_tail(const StepArgs &a, int log2row, bool fp32, int grid, cudaStream_t s);
-cudaError_t launch_runs_init(const StepArgs &a, const int32_t *perm, bool fp32, cudaStream_t s);
+cudaError_t launch_runs_init(const StepArgs &a, const int32_t *perm, bool fp32, cudaStream_t s,
+                             const int64_t *wfirst = nullptr);
 cudaError_t launch_runs_centralities(const StepArgs &a, const uint8_t *regs, const int32_t *perm, bool fp32,
                                      int run, double *closeness, double *harmonic, double *lin,
                                      double *reachable, cudaStream_t s);

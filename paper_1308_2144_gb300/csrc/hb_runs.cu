@@ -71,6 +71,47 @@ __global__ void runs_init_nodes_kernel(StepArgs a, const int32_t *perm) {
         else static_cast<double *>(a.ecache)[q] = estimate64(V, S, P, a.gb, a.c64, a.thr_x, a.lc64);
         a.sumd[q] = 0.0;
         a.harm[q] = 0.0;
+        if (a.disc) a.disc[q] = 0.0;
+        if (r == 0) a.changed[v] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) reset_counters(a.ctr);
+}
+
+// Sec. 6 for rows of several runs: run r of the caller's node u starts from
+// the replicas wfirst[u] .. wfirst[u+1]-1 hashed with run r's seed.  One
+// thread per (node, run) writes that run's p bytes of the row, in both
+// buffers, and its cached estimate and zero accumulators.
+template <bool F32>
+__global__ void runs_init_weighted_kernel(StepArgs a, const int32_t *perm, const int64_t *wfirst) {
+    const int P = 1 << a.gb;
+    const int CH = P >> 4;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    const int64_t total = a.n << a.lruns;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = q >> a.lruns;
+        const int r = (int)(q & ((1 << a.lruns) - 1));
+        const int64_t u = perm ? (int64_t)perm[v] : v;
+        uint8_t *g0 = a.regs[0] + (v << a.b) + (int64_t)r * P;
+        uint4 *g1 = reinterpret_cast<uint4 *>(a.regs[1] + (v << a.b) + (int64_t)r * P);
+        for (int c = 0; c < CH; ++c) reinterpret_cast<uint4 *>(g0)[c] = z;
+        for (int64_t item = wfirst[u]; item < wfirst[u + 1]; ++item) {
+            uint32_t idx, rho;
+            hash_to_register(splitmix64(a.run_seeds[r], (uint64_t)item), a.gb, idx, rho);
+            if (g0[idx] < rho) g0[idx] = (uint8_t)rho;
+        }
+        uint32_t V = 0;
+        unsigned long long S = 0;
+        for (int c = 0; c < CH; ++c) {
+            const uint4 x = reinterpret_cast<const uint4 *>(g0)[c];
+            g1[c] = x;
+            chunk_sums(x, a.gb, V, S);
+        }
+        if (F32) static_cast<float *>(a.ecache)[q] = estimate32(V, S, P, a.gb, a.c32, a.thr_x, a.lc32);
+        else static_cast<double *>(a.ecache)[q] = estimate64(V, S, P, a.gb, a.c64, a.thr_x, a.lc64);
+        a.sumd[q] = 0.0;
+        a.harm[q] = 0.0;
+        if (a.disc) a.disc[q] = 0.0;
         if (r == 0) a.changed[v] = 0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) reset_counters(a.ctr);
@@ -115,7 +156,8 @@ __global__ void runs_centralities_kernel(StepArgs a, const uint8_t *regs, const 
 }
 
 // Sec. 5: per node, the mean and the empirical (sample, R-1) standard
-// deviation over the R runs of one centrality, in two passes.
+// deviation over the R runs of one centrality (which = 4: the Sec. 7
+// discounted accumulator), in two passes.
 template <bool F32>
 __global__ void runs_stats_kernel(StepArgs a, const uint8_t *regs, const int32_t *perm, int which,
                                   double *mean, double *sd) {
@@ -124,14 +166,14 @@ __global__ void runs_stats_kernel(StepArgs a, const uint8_t *regs, const int32_t
          v += (int64_t)gridDim.x * blockDim.x) {
         double c[4], sum = 0.0;
         for (int r = 0; r < R; ++r) {
-            run_centralities<F32>(a, regs, v, r, c);
-            sum += c[which];
+            if (which < 4) run_centralities<F32>(a, regs, v, r, c);
+            sum += which < 4 ? c[which] : a.disc[(v << a.lruns) + r];
         }
         const double mu = sum / (double)R;
         double q = 0.0;
         for (int r = 0; r < R; ++r) {
-            run_centralities<F32>(a, regs, v, r, c);
-            const double d = c[which] - mu;
+            if (which < 4) run_centralities<F32>(a, regs, v, r, c);
+            const double d = (which < 4 ? c[which] : a.disc[(v << a.lruns) + r]) - mu;
             q += d * d;
         }
         const int64_t o = perm ? (int64_t)perm[v] : v;
@@ -199,7 +241,14 @@ cudaError_t launch_runs_tail(const StepArgs &a, int log2row, bool fp32, int grid
     return fp32 ? runs_tail_t<true>(a, log2row, grid, s) : runs_tail_t<false>(a, log2row, grid, s);
 }
 
-cudaError_t launch_runs_init(const StepArgs &a, const int32_t *perm, bool fp32, cudaStream_t s) {
+cudaError_t launch_runs_init(const StepArgs &a, const int32_t *perm, bool fp32, cudaStream_t s,
+                             const int64_t *wfirst) {
+    if (wfirst) {
+        const int64_t q = a.n << a.lruns;
+        if (fp32) runs_init_weighted_kernel<true><<<grid_for(q, 128), 128, 0, s>>>(a, perm, wfirst);
+        else runs_init_weighted_kernel<false><<<grid_for(q, 128), 128, 0, s>>>(a, perm, wfirst);
+        return cudaGetLastError();
+    }
     const int64_t chunks = a.n * ((1 << a.b) >> 4);
     if (a.n > 0) runs_init_rows_kernel<<<grid_for(chunks, 256), 256, 0, s>>>(a, perm);
     const int64_t q = a.n << a.lruns;

@@ -414,7 +414,7 @@ cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, in
 cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, bool fp32,
                         cudaStream_t s, const int64_t *wfirst) {
     const int CH = (1 << a.b) >> 4;
-    if (a.lruns) return launch_runs_init(a, perm, fp32, s);
+    if (a.lruns) return launch_runs_init(a, perm, fp32, s, wfirst);
     if (wfirst) {
         if (fp32) init_weighted_kernel<true><<<grid_for(a.n, 128), 128, 0, s>>>(a, perm, wfirst, seed);
         else init_weighted_kernel<false><<<grid_for(a.n, 128), 128, 0, s>>>(a, perm, wfirst, seed);

@@ -327,6 +327,7 @@ __device__ __forceinline__ void node_epilogue_wide(const StepArgs &a, const uint
         if (active && ch && g && tl < C::L && (cl & ((1 << lg) - 1)) == 0) {
             const int64_t q = (v << a.lruns) + r;
             const double s_old = a.sumd[q], h_old = a.harm[q];
+            const double q_old = a.disc ? a.disc[q] : 0.0;
             // Sec. 5: the new layer sits at distance t+1
             if (F32) {
                 const float e_old = static_cast<const float *>(a.ecache)[q];
@@ -335,6 +336,7 @@ __device__ __forceinline__ void node_epilogue_wide(const StepArgs &a, const uint
                 static_cast<float *>(a.ecache)[q] = E;
                 a.sumd[q] = __fma_rn((double)(t + 1), (double)d, s_old);
                 a.harm[q] = __dadd_rn(h_old, (double)__fmul_rn(d, rdist32));
+                if (a.disc) a.disc[q] = __fma_rn(discount_of(a, t), (double)d, q_old);
             } else {
                 const double e_old = static_cast<const double *>(a.ecache)[q];
                 const double E = estimate64(V, S, P, a.gb, a.c64, a.thr_x, a.lc64);
@@ -342,6 +344,7 @@ __device__ __forceinline__ void node_epilogue_wide(const StepArgs &a, const uint
                 static_cast<double *>(a.ecache)[q] = E;
                 a.sumd[q] = __fma_rn((double)(t + 1), d, s_old);
                 a.harm[q] = __fma_rn(d, rdist64, h_old);
+                if (a.disc) a.disc[q] = __fma_rn(discount_of(a, t), d, q_old);
             }
             rmask |= 1ULL << r;
         }

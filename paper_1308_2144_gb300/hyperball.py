@@ -46,7 +46,7 @@ EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_
            "hb_get_centralities", "hb_get_accumulators", "hb_get_registers", "hb_get_frontier",
            "hb_get_info", "hb_reset", "hb_trim_memory", "hb_set_weights", "hb_set_discount", "hb_get_discounted",
            "hb_get_neighbourhood", "hb_create_runs", "hb_get_run_steps", "hb_get_run_centralities",
-           "hb_get_run_accumulators", "hb_get_run_stats",
+           "hb_get_run_accumulators", "hb_get_run_discounted", "hb_get_run_stats",
            "hb_save", "hb_load", "hb_destroy", "hb_last_error",
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
@@ -152,6 +152,8 @@ def load():
         L.hb_get_run_centralities.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
         L.hb_get_run_accumulators.restype = st
         L.hb_get_run_accumulators.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+        L.hb_get_run_discounted.restype = st
+        L.hb_get_run_discounted.argtypes = [_vp, ctypes.c_int32, _vp]
         L.hb_get_run_stats.restype = st
         L.hb_get_run_stats.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
         L.hb_get_neighbourhood.restype = st
@@ -647,10 +649,17 @@ class HyperBall:
         _check(load().hb_get_run_accumulators(self._h, int(r), _ptr(sumd), _ptr(harm)))
         return sumd, harm
 
+    def run_discounted(self, r: int, device="cuda") -> torch.Tensor:
+        out = self._out(self.n, torch.float64, device)
+        _check(load().hb_get_run_discounted(self._h, int(r), _ptr(out)))
+        return out
+
     def run_stats(self, which, device="cuda"):
         """Per-node mean and sample standard deviation over the runs of one
-        centrality ("closeness", "harmonic", "lin", "reachable")."""
-        w = ("closeness", "harmonic", "lin", "reachable").index(which) if isinstance(which, str) else int(which)
+        centrality ("closeness", "harmonic", "lin", "reachable") or of the
+        discounted accumulator ("discounted")."""
+        names = ("closeness", "harmonic", "lin", "reachable", "discounted")
+        w = names.index(which) if isinstance(which, str) else int(which)
         mean = self._out(self.n, torch.float64, device)
         sd = self._out(self.n, torch.float64, device)
         _check(load().hb_get_run_stats(self._h, w, _ptr(mean), _ptr(sd)))

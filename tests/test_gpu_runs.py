@@ -3,6 +3,8 @@ each run equals its solo run with the same seed (registers and iteration
 counts bit-exact, accumulators within 1e-9), and the per-node mean and
 empirical standard deviation of every centrality equal the oracle's over
 the same seeds within 1e-9 of the mean."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -94,27 +96,29 @@ def test_same_graph_batch_and_mixed_sizes(orc):
 
 # ------------------------------------------------- runs in one handle --
 
-def check_wide(orc, hb, off, tgt, b, seeds):
+def check_wide(orc, hb, off, tgt, b, seeds, weights=None, discount=None):
     n = off.size - 1
     p = 1 << b
     regs = hb.registers().cpu().numpy()
     assert regs.shape == (n, len(seeds) * p)
     steps = hb.run_steps()
     for r, s in enumerate(seeds):
-        ref = orc.run(off, tgt, b, s)
+        ref = orc.run(off, tgt, b, s, weights=weights, discount=discount)
         assert steps[r] == ref.steps, (r, steps[r], ref.steps)
         assert np.array_equal(regs[:, r * p:(r + 1) * p], ref.regs), r
         gs, gh = hb.run_accumulators(r)
         close(gs.cpu().numpy(), ref.sumd)
         close(gh.cpu().numpy(), ref.harm)
+        if discount is not None:
+            close(hb.run_discounted(r).cpu().numpy(), ref.disc)
         fin = orc.finalize(b, ref.regs, ref.sumd, ref.harm)
         cen = hb.run_centralities(r)
         for k in CENTRALITIES:
             close(cen[k].cpu().numpy(), fin[k])
     assert hb.info()["t"] == max(steps)
-    for which in CENTRALITIES:
+    for which in CENTRALITIES + (("discounted",) if discount is not None else ()):
         mean, sd = (x.cpu().numpy() for x in hb.run_stats(which))
-        m_ref, s_ref = orc.run_stats(off, tgt, b, seeds, which)
+        m_ref, s_ref = orc.run_stats(off, tgt, b, seeds, which, weights=weights, discount=discount)
         close(mean, m_ref)
         assert np.all(np.abs(sd - s_ref) <= 1e-9 * np.abs(m_ref)), which
 
@@ -175,18 +179,50 @@ def test_runs_in_one_handle_fp32_host_csr_and_limits(orc):
     regs = hb.registers().cpu().numpy()
     for r, s in enumerate(seeds):
         assert np.array_equal(regs[:, 16 * r:16 * (r + 1)], orc.run(off, tgt, 4, s).regs)
-    for call in (lambda: hb.centralities(), lambda: hb.accumulators(),
-                 lambda: hb.set_weights(np.ones(n, dtype=np.int64)), lambda: hb.set_discount([1.0]),
-                 lambda: hb.save("/tmp/never-written.ckpt")):
+    for call in (lambda: hb.centralities(), lambda: hb.accumulators(), lambda: hb.run_discounted(0),
+                 lambda: hb.run_stats("discounted"), lambda: hb.save("/tmp/never-written.ckpt")):
         with pytest.raises(hbl.HBError) as e:
             call()
         assert e.value.status == hbl.HB_ERR_STATE
+    hb.set_discount([1.0])
+    with pytest.raises(hbl.HBError) as e:   # one accumulator per run: hb_get_run_discounted
+        hb.discounted()
+    assert e.value.status == hbl.HB_ERR_STATE
     hb.close()
     d_off, d_tgt = to_dev(off, tgt)
     for b, seeds in ((4, [1, 2, 3]), (10, [1, 2]), (7, list(range(64))), (4, [1])):
         with pytest.raises(hbl.HBError) as e:
             hbl.HyperBall.runs(d_off, d_tgt, b, seeds, n=n)
         assert e.value.status == hbl.HB_ERR_INVALID
+
+
+@pytest.mark.parametrize("b,R,frontier", [(4, 8, "auto"), (6, 4, "off"), (5, 16, "push")])
+def test_runs_in_one_handle_weighted_discounted(orc, b, R, frontier):
+    """Sec. 6 weights and a Sec. 7 discount on rows of several runs: each run
+    hashes the replicas with its own seed and keeps its own discounted
+    accumulator; every run equals the weighted, discounted oracle run of its
+    seed, and the statistics (the discounted one included) the oracle's."""
+    off, tgt = graphs.rmat_graph(scale=11, edge_factor=8, seed=90 + b).numpy()
+    n = off.size - 1
+    w = np.random.default_rng(b + R).integers(0, 7, size=n).astype(np.int64)
+    table = [1.0 / math.log(d + 1) for d in range(1, 65)]
+    seeds = [500 + 13 * r for r in range(R)]
+    hb = hbl.HyperBall.runs(*to_dev(off, tgt), b, seeds, n=n, frontier=frontier)
+    hb.set_weights(torch.from_numpy(w).cuda())
+    hb.set_discount(table)
+    hb.run()
+    check_wide(orc, hb, off, tgt, b, seeds, weights=w, discount=table)
+    # a short table: distances beyond it contribute nothing; reset keeps both
+    hb.set_discount([1.0, 0.5, 0.25])
+    hb.reset(0)
+    hb.run()
+    check_wide(orc, hb, off, tgt, b, seeds, weights=w, discount=[1.0, 0.5, 0.25])
+    # unit weights give the unweighted runs
+    hb.set_weights(np.ones(n, dtype=np.int64))
+    hb.set_discount([])
+    hb.run()
+    check_wide(orc, hb, off, tgt, b, seeds)
+    hb.close()
 
 
 @pytest.mark.parametrize("relabel,transpose", [(False, False), (True, True)])
