@@ -140,7 +140,8 @@ hb_status setup_shared(hb_graph *g) {
         g->roff = M.alloc<int64_t>(n + 1);
         g->rtgt = M.alloc<int32_t>(m);
         if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (reverse CSR)");
-        e = transpose_csr(g->off, g->tgt, n, m, g->roff, g->rtgt, s);
+        e = g->indeg ? transpose_csr_counted(g->off, g->tgt, n, m, g->indeg, g->perm, g->roff, g->rtgt, s)
+                     : transpose_csr(g->off, g->tgt, n, m, g->roff, g->rtgt, s);
         if (e != cudaSuccess) return cuda_fail(e, "reverse CSR");
     }
     StepArgs &a = g->a;
@@ -529,8 +530,9 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         g->inv = M.alloc<int32_t>(n);
         int64_t *noff = M.alloc<int64_t>(n + 1);
         int32_t *ntgt = M.alloc<int32_t>(m);
+        g->indeg = M.alloc<unsigned long long>(n);
         if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory (relabel)"); }
-        e = degree_sort(in_off, in_tgt, n, m, g->perm, g->inv, s);
+        e = degree_sort_counted(in_off, in_tgt, n, m, g->perm, g->inv, g->indeg, s);
         if (e == cudaSuccess) e = relabel_csr(in_off, in_tgt, n, m, g->perm, g->inv, noff, ntgt, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { delete g; return cuda_fail(e, "relabel"); }
@@ -548,6 +550,8 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         NvtxRange nv("setup");
         st = finish_setup(g);
     }
+    if (g->indeg) M.release(g->indeg);
+    g->indeg = nullptr;
     if (st == HB_OK) st = init_state(g, seed);
     if (st != HB_OK) { delete g; return st; }
     *out = g;

@@ -88,34 +88,43 @@ __global__ void count_targets(const int32_t *tgt, int64_t m, unsigned long long 
 }
 
 // Arc passes that need each arc's source node work on tiles of kArcTile
-// consecutive arcs: thread 0 finds the sources u0 of the tile's first arc
-// and u1 of its last by binary search over all offsets, the block stages
-// off[u0 .. u1] in shared memory, and every arc's source is then the last
-// staged node whose offset is <= the arc (off[u1+1] lies beyond the tile).
-// A tile whose sources span more than kStageNodes nodes (runs of empty
-// nodes) falls back to the search over all offsets.
+// consecutive arcs.  tile_ends_kernel finds, for all tiles in parallel, the
+// sources u0 of a tile's first arc and u1 of its last (a binary search over
+// the offsets each); a block stages off[u0 .. u1] in shared memory, and
+// every arc's source is then the last staged node whose offset is <= the
+// arc (off[u1+1] lies beyond the tile).  A tile whose sources span more
+// than kStageNodes nodes (runs of empty nodes) falls back to the search
+// over all offsets.  Each thread takes kArcPer arcs of a tile and runs
+// their dependent loads (and atomics) stage by stage, so that the loads of
+// all its arcs are in flight together.
 constexpr int kArcTile = 2048;
 constexpr int kStageNodes = 2048;
+constexpr int kArcThreads = 256;
+constexpr int kArcPer = kArcTile / kArcThreads;
 
 struct ArcTile {
     int64_t e0, e1, u0;
     int cnt;   // staged offsets (0: fall back)
 };
 
-__device__ __forceinline__ ArcTile stage_arc_tile(const int64_t *off, int64_t n, int64_t m, int64_t e0,
-                                                  int64_t *s_off, int64_t *s_hdr) {
-    const int64_t e1 = e0 + kArcTile < m ? e0 + kArcTile : m;
-    __syncthreads();   // the previous tile's readers are done with s_off
-    if (threadIdx.x == 0) {
-        const int64_t u0 = arc_source(off, n, e0), u1 = arc_source(off, n, e1 - 1);
-        s_hdr[0] = u0;
-        s_hdr[1] = (u1 - u0 + 1 <= kStageNodes) ? u1 - u0 + 1 : 0;
+__global__ void tile_ends_kernel(const int64_t *off, int64_t n, int64_t m, int64_t ntiles, int64_t *ends) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ntiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e0 = t * kArcTile, e1 = e0 + kArcTile < m ? e0 + kArcTile : m;
+        ends[2 * t] = arc_source(off, n, e0);
+        ends[2 * t + 1] = arc_source(off, n, e1 - 1);
     }
+}
+
+__device__ __forceinline__ ArcTile stage_arc_tile(const int64_t *off, int64_t m, int64_t tile, const int64_t *ends,
+                                                  int64_t *s_off) {
+    const int64_t e0 = tile * kArcTile, e1 = e0 + kArcTile < m ? e0 + kArcTile : m;
+    const int64_t u0 = ends[2 * tile], u1 = ends[2 * tile + 1];
+    const int cnt = u1 - u0 + 1 <= kStageNodes ? (int)(u1 - u0 + 1) : 0;
+    __syncthreads();   // the previous tile's readers are done with s_off
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_off[i] = off[u0 + i];
     __syncthreads();
-    ArcTile t{e0, e1, s_hdr[0], (int)s_hdr[1]};
-    for (int i = threadIdx.x; i < t.cnt; i += blockDim.x) s_off[i] = off[t.u0 + i];
-    __syncthreads();
-    return t;
+    return ArcTile{e0, e1, u0, cnt};
 }
 
 // Source node of arc e of the tile, and its first arc off[u].
@@ -135,19 +144,41 @@ __device__ __forceinline__ int64_t tile_source(const ArcTile &t, const int64_t *
     return t.u0 + lo;
 }
 
-__global__ void __launch_bounds__(256) scatter_transpose(const int64_t *off, const int32_t *tgt, int64_t n,
-                                                         int64_t m, unsigned long long *cursor, int32_t *ttgt) {
+__global__ void __launch_bounds__(kArcThreads) scatter_transpose(const int64_t *off, const int32_t *tgt, int64_t n,
+                                                                 int64_t m, const int64_t *ends,
+                                                                 unsigned long long *cursor, int32_t *ttgt) {
     __shared__ int64_t s_off[kStageNodes];
-    __shared__ int64_t s_hdr[2];
-    for (int64_t e0 = (int64_t)blockIdx.x * kArcTile; e0 < m; e0 += (int64_t)gridDim.x * kArcTile) {
-        const ArcTile t = stage_arc_tile(off, n, m, e0, s_off, s_hdr);
-        for (int64_t e = t.e0 + threadIdx.x; e < t.e1; e += blockDim.x) {
-            int64_t first;
-            const int64_t u = tile_source(t, s_off, off, n, e, first);
-            const unsigned long long pos = atomicAdd(&cursor[tgt[e]], 1ULL);
-            ttgt[pos] = (int32_t)u;
+    const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const ArcTile t = stage_arc_tile(off, m, tile, ends, s_off);
+        int32_t w[kArcPer], u[kArcPer];
+        unsigned long long pos[kArcPer];
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q) {
+            const int64_t e = t.e0 + threadIdx.x + q * kArcThreads;
+            if (e < t.e1) {
+                int64_t first;
+                w[q] = tgt[e];
+                u[q] = (int32_t)tile_source(t, s_off, off, n, e, first);
+            }
         }
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q)
+            if (t.e0 + threadIdx.x + q * kArcThreads < t.e1) pos[q] = atomicAdd(&cursor[w[q]], 1ULL);
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q)
+            if (t.e0 + threadIdx.x + q * kArcThreads < t.e1) ttgt[pos[q]] = u[q];
     }
+}
+
+// In-arc counts of the relabelled graph from the in-degrees of the
+// caller's nodes: node v of the relabelled graph is the caller's perm[v].
+__global__ void permuted_counts(const unsigned long long *indeg, const int32_t *perm, int64_t n,
+                                unsigned long long *cnt) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        cnt[v] = indeg[perm ? perm[v] : v];
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[n] = 0;
 }
 
 // -------------------------------------------------------- degree sort --
@@ -250,17 +281,37 @@ __global__ void permuted_degrees(const int64_t *off, const int32_t *perm, int64_
     if (blockIdx.x == 0 && threadIdx.x == 0) deg[n] = 0;
 }
 
-__global__ void __launch_bounds__(256) relabel_arcs(const int64_t *off, const int32_t *tgt, int64_t n,
-                                                    int64_t m, const int32_t *inv, const int64_t *noff,
-                                                    int32_t *ntgt) {
+// Arcs of the relabelled CSR in their own order: arc e of new node v (the
+// caller's u = perm[v]) is u's arc e - noff[v], its target mapped by inv.
+// The writes are sequential and each node's targets are read as one run.
+__global__ void __launch_bounds__(kArcThreads) relabel_arcs(const int64_t *off, const int32_t *tgt, int64_t n,
+                                                            int64_t m, const int32_t *perm, const int32_t *inv,
+                                                            const int64_t *noff, const int64_t *ends, int32_t *ntgt) {
     __shared__ int64_t s_off[kStageNodes];
-    __shared__ int64_t s_hdr[2];
-    for (int64_t e0 = (int64_t)blockIdx.x * kArcTile; e0 < m; e0 += (int64_t)gridDim.x * kArcTile) {
-        const ArcTile t = stage_arc_tile(off, n, m, e0, s_off, s_hdr);
-        for (int64_t e = t.e0 + threadIdx.x; e < t.e1; e += blockDim.x) {
-            int64_t first;
-            const int64_t u = tile_source(t, s_off, off, n, e, first);
-            ntgt[noff[inv[u]] + (e - first)] = inv[tgt[e]];
+    const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const ArcTile t = stage_arc_tile(noff, m, tile, ends, s_off);
+        int64_t v[kArcPer], at[kArcPer];
+        int32_t x[kArcPer];
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q) {
+            const int64_t e = t.e0 + threadIdx.x + q * kArcThreads;
+            int64_t first = e;
+            v[q] = e < t.e1 ? tile_source(t, s_off, noff, n, e, first) : 0;
+            at[q] = e - first;   // the arc's rank in its node's list
+        }
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q) v[q] = perm[v[q]];
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q)
+            if (t.e0 + threadIdx.x + q * kArcThreads < t.e1) at[q] += off[v[q]];
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q)
+            if (t.e0 + threadIdx.x + q * kArcThreads < t.e1) x[q] = __ldcs(tgt + at[q]);
+#pragma unroll
+        for (int q = 0; q < kArcPer; ++q) {
+            const int64_t e = t.e0 + threadIdx.x + q * kArcThreads;
+            if (e < t.e1) ntgt[e] = inv[x[q]];
         }
     }
 }
@@ -366,43 +417,67 @@ cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                          int64_t *toff, int32_t *ttgt, cudaStream_t s) {
+// Source nodes of the first and last arc of every kArcTile tile of the
+// CSR (off, m arcs): 2 entries per tile, freed by the caller.
+static cudaError_t tile_ends(const int64_t *off, int64_t n, int64_t m, int64_t **ends, cudaStream_t s) {
+    const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
+    cudaError_t e = tmp_alloc(ends, sizeof(int64_t) * 2 * ntiles, s);
+    if (e != cudaSuccess) return e;
+    tile_ends_kernel<<<grid_for(ntiles, 256), 256, 0, s>>>(off, n, m, ntiles, *ends);
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_csr_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                                  const unsigned long long *indeg, const int32_t *perm, int64_t *toff,
+                                  int32_t *ttgt, cudaStream_t s) {
     unsigned long long *cnt = nullptr;
     cudaError_t e = tmp_alloc(&cnt, sizeof(unsigned long long) * (n + 1), s);
     if (e != cudaSuccess) return e;
-    cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (n + 1), s);
-    if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, cnt);
+    if (indeg) {
+        permuted_counts<<<grid_for(n + 1, 256), 256, 0, s>>>(indeg, perm, n, cnt);
+    } else {
+        cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (n + 1), s);
+        if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, cnt);
+    }
     e = scan_exclusive_i64(reinterpret_cast<int64_t *>(cnt), toff, n + 1, s);
+    int64_t *ends = nullptr;
+    if (e == cudaSuccess && m > 0) e = tile_ends(off, n, m, &ends, s);
     if (e == cudaSuccess && m > 0) {
         cudaMemcpyAsync(cnt, toff, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
-        scatter_transpose<<<grid_for((m + kArcTile - 1) / kArcTile * 256, 256), 256, 0, s>>>(off, tgt, n, m, cnt,
-                                                                                           ttgt);
+        const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
+        scatter_transpose<<<grid_for(ntiles * kArcThreads, kArcThreads), kArcThreads, 0, s>>>(off, tgt, n, m, ends,
+                                                                                          cnt, ttgt);
         e = cudaGetLastError();
     }
     cudaFreeAsync(cnt, s);
+    if (ends) cudaFreeAsync(ends, s);
     return e;
+}
+
+cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                          int64_t *toff, int32_t *ttgt, cudaStream_t s) {
+    return transpose_csr_counted(off, tgt, n, m, nullptr, nullptr, toff, ttgt, s);
 }
 
 // Node order for the step kernel: out-degree buckets descending (so every
 // degree class is a contiguous id range), and within a bucket in-degree
 // buckets descending (the most gathered counters share L2 lines); two
 // stable partitions, least significant key first.
-cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
-                        int32_t *inv, cudaStream_t s) {
+cudaError_t degree_sort_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
+                                int32_t *inv, unsigned long long *indeg, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
     int64_t *counts = nullptr;
-    unsigned long long *indeg = nullptr;
     uint8_t *keys = nullptr;
     int32_t *perm1 = nullptr;
     cudaError_t e = tmp_alloc(&counts, sizeof(int64_t) * kBuckets * ntiles * 2, s);
-    if (e == cudaSuccess) e = tmp_alloc(&indeg, sizeof(unsigned long long) * n, s);
     if (e == cudaSuccess) e = tmp_alloc(&keys, 2 * (size_t)n, s);
     if (e == cudaSuccess) e = tmp_alloc(&perm1, sizeof(int32_t) * n, s);
     if (e == cudaSuccess) {
         cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * n, s);
         if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, indeg);
+    }
+    if (e == cudaSuccess) {
         key_in_kernel<<<grid_for(n, 256), 256, 0, s>>>(indeg, n, keys);
         key_out_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, keys + n);
         const int g = (int)(ntiles < 152 * 8 ? ntiles : 152 * 8);
@@ -422,9 +497,18 @@ cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64
         }
     }
     cudaFreeAsync(counts, s);
-    cudaFreeAsync(indeg, s);
     cudaFreeAsync(keys, s);
     cudaFreeAsync(perm1, s);
+    return e;
+}
+
+cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
+                        int32_t *inv, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    unsigned long long *indeg = nullptr;
+    cudaError_t e = tmp_alloc(&indeg, sizeof(unsigned long long) * n, s);
+    if (e == cudaSuccess) e = degree_sort_counted(off, tgt, n, m, perm, inv, indeg, s);
+    if (indeg) cudaFreeAsync(indeg, s);
     return e;
 }
 
@@ -436,12 +520,16 @@ cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64
     if (e != cudaSuccess) return e;
     permuted_degrees<<<grid_for(n + 1, 256), 256, 0, s>>>(off, perm, n, deg);
     e = scan_exclusive_i64(deg, noff, n + 1, s);
+    int64_t *ends = nullptr;
+    if (e == cudaSuccess && m > 0) e = tile_ends(noff, n, m, &ends, s);
     if (e == cudaSuccess && m > 0) {
-        relabel_arcs<<<grid_for((m + kArcTile - 1) / kArcTile * 256, 256), 256, 0, s>>>(off, tgt, n, m, inv,
-                                                                                      noff, ntgt);
+        const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
+        relabel_arcs<<<grid_for(ntiles * kArcThreads, kArcThreads), kArcThreads, 0, s>>>(off, tgt, n, m, perm, inv,
+                                                                                     noff, ends, ntgt);
         e = cudaGetLastError();
     }
     cudaFreeAsync(deg, s);
+    if (ends) cudaFreeAsync(ends, s);
     return e;
 }
 

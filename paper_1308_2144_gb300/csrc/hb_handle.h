@@ -72,6 +72,19 @@ cudaError_t tmp_alloc(T **p, size_t bytes, cudaStream_t s) {
     return tmp_alloc(reinterpret_cast<void **>(p), bytes, s);
 }
 
+// Create-time graph passes that share one in-degree histogram (the step
+// kernel's node order needs it, and so do the reverse lists).
+// degree_sort_counted: degree_sort that leaves the in-degree of each of the
+// caller's nodes in indeg (n entries, device, owned by the caller).
+cudaError_t degree_sort_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
+                                int32_t *inv, unsigned long long *indeg, cudaStream_t s);
+// transpose_csr of a relabelled graph whose node v is the caller's perm[v]
+// (perm null: the identity) and has in-degree indeg[perm[v]]; indeg null
+// counts the in-arcs instead.
+cudaError_t transpose_csr_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                                  const unsigned long long *indeg, const int32_t *perm, int64_t *toff,
+                                  int32_t *ttgt, cudaStream_t s);
+
 // Host-side services of hb_api.cu used by the other translation units.
 hb_status create_handle64(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
                           int log2m, uint64_t seed, const hb_options *opt, hb_graph **out);
@@ -117,6 +130,7 @@ struct hb_graph {
     int64_t *roff = nullptr;
     int32_t *rtgt = nullptr;
     int32_t *perm = nullptr, *inv = nullptr;
+    unsigned long long *indeg = nullptr;   // create time only: in-degree of each caller node
     int64_t *wfirst = nullptr;     // Sec. 6: first replica item of each caller node (n+1), or null
     double *disc = nullptr;        // Sec. 7: discounted accumulator (n), or null
     double *ftab = nullptr;        // its discount table
