@@ -394,7 +394,8 @@ def trace_run(hb, seed, log2m):
 
 def run_e2e(args, g, opts, wl, world, cen, aps):
     """Same metric through the public API from host memory: pinned host CSR
-    in, handle created (upload + setup) with the class sizing chosen above,
+    in, handle created (upload + setup) with the class sizing chosen above
+    given at creation (hb_options.arcs_per_slot),
     run to the fixpoint, centralities back to pinned host memory, handle
     destroyed, every step; one untimed step first."""
     from paper_1308_2144_gb300 import hyperball as hbl
@@ -408,8 +409,7 @@ def run_e2e(args, g, opts, wl, world, cen, aps):
     opts_h.pop("profile")
 
     def one(seed):
-        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed))
-        h.set_class_sizing(aps)
+        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed, arcs_per_slot=aps))
         h.run()
         hbl.hb_get_centralities(h._h, outs_h["closeness"], outs_h["harmonic"], outs_h["lin"],
                                 outs_h["reachable"])

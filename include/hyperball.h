@@ -80,6 +80,9 @@ typedef struct {
     int32_t frontier;    /* HB_FRONTIER_* */
     int32_t max_steps;   /* iteration cap for hb_run_to_fixpoint; <= 0 means 1<<20 */
     void *stream;        /* cudaStream_t, or NULL */
+    int32_t arcs_per_slot; /* class sizing of the gather from creation (as hb_set_class_sizing:
+                              a power of two from 1 to 128), for callers who know it from an
+                              earlier hb_tune; 0 = the default, 16.  Results never depend on it. */
 } hb_options;
 
 typedef struct hb_graph hb_graph;   /* opaque handle */
@@ -123,7 +126,7 @@ typedef struct {
  * In a pushed iteration last_arcs (the arc-updates) counts the P arcs. */
 
 /* Fill *opt with the defaults: flags 0, HB_FRONTIER_AUTO, max_steps 1<<20,
- * stream NULL. */
+ * stream NULL, arcs_per_slot 0. */
 void hb_default_options(hb_options *opt);
 
 /* Build a handle for the CSR graph (offsets: n+1 int64, targets: m int32)

@@ -99,6 +99,16 @@ void default_opts(hb_options *o) {
     o->frontier = HB_FRONTIER_AUTO;
     o->max_steps = 1 << 20;
     o->stream = nullptr;
+    o->arcs_per_slot = 0;
+}
+
+// The class sizing an options block asks for (0: the default); false if it
+// is not one of the candidates.
+bool sizing_of(const hb_options &o, int *aps) {
+    *aps = o.arcs_per_slot ? o.arcs_per_slot : kArcsPerSlot;
+    for (int c : kTuneAps)
+        if (c == *aps) return true;
+    return false;
 }
 
 // Copy `bytes` from a host or device source into device memory.
@@ -107,6 +117,39 @@ cudaError_t to_device(void *dst, const void *src, size_t bytes, cudaStream_t s) 
     return cudaMemcpyAsync(dst, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice
                                                                : cudaMemcpyHostToDevice, s);
 }
+
+// Host targets to the device in chunks on s, each chunk checked against
+// [0, n) (and its in-arcs counted into indeg, when not null) on a second
+// stream as soon as it has arrived, so that the checks run under the copy;
+// s waits for the checks at the end.
+cudaError_t upload_checked(int32_t *dst, const int32_t *src, int64_t m, int64_t n, unsigned long long *err,
+                           unsigned long long *indeg, cudaStream_t s) {
+    constexpr int K = 8;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[K + 1] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+    for (int k = 0; e == cudaSuccess && k <= K; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[K], s);   // the buffers' allocation and clearing
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev[K], 0);
+    const int64_t step = (m + K - 1) / K;
+    for (int k = 0; e == cudaSuccess && k < K; ++k) {
+        const int64_t c0 = k * step, c1 = c0 + step < m ? c0 + step : m;
+        if (c0 >= c1) break;
+        e = cudaMemcpyAsync(dst + c0, src + c0, sizeof(int32_t) * (c1 - c0), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[k], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev[k], 0);
+        if (e == cudaSuccess) e = check_targets(dst + c0, c1 - c0, n, err, indeg, side);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[K], side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[K], 0);
+    if (e != cudaSuccess && side) cudaStreamSynchronize(side);   // nothing of it outlives the buffers
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (side) cudaStreamDestroy(side);
+    return e;
+}
+// Targets from host memory at least this long are uploaded by upload_checked.
+constexpr int64_t kCheckedUploadMin = (int64_t)1 << 23;
 
 // Deliver a device result into a caller buffer (host or device).
 cudaError_t to_caller(void *dst, const void *src, size_t bytes, cudaStream_t s) {
@@ -419,6 +462,8 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     if (o.max_steps <= 0) o.max_steps = 1 << 20;
     if (o.frontier < HB_FRONTIER_AUTO || o.frontier > HB_FRONTIER_OFF)
         return fail(HB_ERR_INVALID, "unknown frontier policy");
+    int aps = 0;
+    if (!sizing_of(o, &aps)) return fail(HB_ERR_INVALID, "arcs_per_slot must be 0 or a power of two from 1 to 128");
     cudaError_t e = cudaFree(nullptr);   // make sure a context exists
     if (e != cudaSuccess) return cuda_fail(e, "CUDA context");
 
@@ -428,7 +473,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     g->b = log2m + lruns;
     g->gb = log2m;
     g->lruns = lruns;
-    g->y = make_layout(g->b);
+    g->y = make_layout(g->b, aps);
     g->opt = o;
     g->s = static_cast<cudaStream_t>(o.stream);
     g->fp32 = (o.flags & HB_FP32_ESTIMATE) != 0;
@@ -454,9 +499,18 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     }
 
     NvtxRange nv_create("hb_create");
-    // 1. input CSR on the device (int64 offsets)
+    // 1. input CSR on the device (int64 offsets), the targets checked as
+    // they arrive; when the graph given is the one scanned, the degree
+    // sort's key (every node's in-degree) is counted by the same pass
     const bool borrow = (o.flags & HB_BORROW_DEVICE_PTRS) != 0;
     const bool off_dev = is_device_ptr(offsets), tgt_dev = m == 0 || is_device_ptr(targets);
+    const bool pre_count = g->relabel && (o.flags & HB_TRANSPOSE) == 0 && n > 0 && m > 0;
+    unsigned long long *err_dev = M.alloc<unsigned long long>(1);
+    if (pre_count) g->indeg = M.alloc<unsigned long long>(n);
+    if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory"); }
+    cudaMemsetAsync(err_dev, 0, sizeof(unsigned long long), s);
+    if (pre_count) cudaMemsetAsync(g->indeg, 0, sizeof(unsigned long long) * n, s);
+    bool checked = false;
     int64_t *in_off = nullptr;
     int32_t *in_tgt = nullptr;
     bool own_in_off = true, own_in_tgt = true;
@@ -470,7 +524,6 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
             if (M.err == cudaSuccess) {
                 e = to_device(tmp, offsets, sizeof(int32_t) * (n + 1), s);
                 if (e == cudaSuccess) e = widen_offsets(tmp, in_off, n + 1, s);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
                 M.release(tmp);
             }
         } else if (M.err == cudaSuccess) {
@@ -482,19 +535,24 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         own_in_tgt = false;
     } else {
         in_tgt = M.alloc<int32_t>(m);
-        if (M.err == cudaSuccess) e = to_device(in_tgt, targets, sizeof(int32_t) * m, s);
+        if (M.err == cudaSuccess && e == cudaSuccess) {
+            if (!tgt_dev && m >= kCheckedUploadMin) {
+                e = upload_checked(in_tgt, targets, m, n, err_dev, g->indeg, s);
+                checked = true;
+            } else {
+                e = to_device(in_tgt, targets, sizeof(int32_t) * m, s);
+            }
+        }
     }
     if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory (graph)"); }
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "graph upload"); }
 
     // 2. validation
-    unsigned long long *err_dev = M.alloc<unsigned long long>(1);
     unsigned long long err_host = 0;
-    if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory"); }
-    cudaMemsetAsync(err_dev, 0, sizeof(unsigned long long), s);
     {
         NvtxRange nv("validate");
-        e = validate_csr(in_off, in_tgt, n, m, err_dev, s);
+        e = validate_offsets(in_off, n, m, err_dev, s);
+        if (e == cudaSuccess && !checked) e = check_targets(in_tgt, m, n, err_dev, g->indeg, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&err_host, err_dev, sizeof(err_host), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
@@ -530,9 +588,9 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         g->inv = M.alloc<int32_t>(n);
         int64_t *noff = M.alloc<int64_t>(n + 1);
         int32_t *ntgt = M.alloc<int32_t>(m);
-        g->indeg = M.alloc<unsigned long long>(n);
+        if (!g->indeg) g->indeg = M.alloc<unsigned long long>(n);
         if (M.err != cudaSuccess) { delete g; return fail(HB_ERR_OOM, "out of device memory (relabel)"); }
-        e = degree_sort_counted(in_off, in_tgt, n, m, g->perm, g->inv, g->indeg, s);
+        e = degree_sort_counted(in_off, in_tgt, n, m, g->perm, g->inv, g->indeg, pre_count, s);
         if (e == cudaSuccess) e = relabel_csr(in_off, in_tgt, n, m, g->perm, g->inv, noff, ntgt, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { delete g; return cuda_fail(e, "relabel"); }
@@ -1185,9 +1243,14 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     hb_options o;
     if (opt) o = *opt; else default_opts(&o);
     if (o.max_steps <= 0) o.max_steps = 1 << 20;
+    int aps = 0;
+    if (!sizing_of(o, &aps)) {
+        fclose(f);
+        return fail(HB_ERR_INVALID, "arcs_per_slot must be 0 or a power of two from 1 to 128");
+    }
     cudaFree(nullptr);
     hb_graph *g = new hb_graph();
-    g->n = h.n; g->m = h.m; g->b = h.b; g->gb = h.b; g->y = make_layout(h.b);
+    g->n = h.n; g->m = h.m; g->b = h.b; g->gb = h.b; g->y = make_layout(h.b, aps);
     g->opt = o;
     g->opt.frontier = h.frontier;
     g->s = static_cast<cudaStream_t>(o.stream);

@@ -47,19 +47,27 @@ __global__ void scan_tile_apply(const int64_t *in, int64_t *out, int64_t N, cons
 
 // ------------------------------------------------------------ validate --
 
-__global__ void validate_kernel(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                                unsigned long long *err) {
+// Error bits: 1 offsets[0] != 0, 2 offsets[n] != m, 4 offsets decrease,
+// 8 a target outside [0, n).
+__global__ void validate_offsets_kernel(const int64_t *off, int64_t n, int64_t m, unsigned long long *err) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (tid == 0) {
         if (off[0] != 0) atomicOr(err, 1ULL);
         if (off[n] != m) atomicOr(err, 2ULL);
     }
-    for (int64_t v = tid; v < n; v += stride)
+    for (int64_t v = tid; v < n; v += (int64_t)gridDim.x * blockDim.x)
         if (off[v + 1] < off[v]) { atomicOr(err, 4ULL); break; }
-    for (int64_t e = tid; e < m; e += stride) {
-        int32_t w = tgt[e];
+}
+
+// Targets tgt[0 .. len) against [0, n); with indeg, every target in range
+// also adds one to its node's in-degree.
+__global__ void check_targets_kernel(const int32_t *tgt, int64_t len, int64_t n, unsigned long long *err,
+                                     unsigned long long *indeg) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t w = tgt[e];
         if (w < 0 || (int64_t)w >= n) { atomicOr(err, 8ULL); break; }
+        if (indeg) atomicAdd(&indeg[w], 1ULL);
     }
 }
 
@@ -381,10 +389,22 @@ cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t N, cudaS
     return e;
 }
 
+cudaError_t validate_offsets(const int64_t *off, int64_t n, int64_t m, unsigned long long *err_dev,
+                             cudaStream_t s) {
+    validate_offsets_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, m, err_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t check_targets(const int32_t *tgt, int64_t len, int64_t n, unsigned long long *err_dev,
+                          unsigned long long *indeg, cudaStream_t s) {
+    if (len > 0) check_targets_kernel<<<grid_for(len, 256), 256, 0, s>>>(tgt, len, n, err_dev, indeg);
+    return cudaGetLastError();
+}
+
 cudaError_t validate_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                          unsigned long long *err_dev, cudaStream_t s) {
-    validate_kernel<<<grid_for(n > m ? n : m, 256), 256, 0, s>>>(off, tgt, n, m, err_dev);
-    return cudaGetLastError();
+    cudaError_t e = validate_offsets(off, n, m, err_dev, s);
+    return e == cudaSuccess ? check_targets(tgt, m, n, err_dev, nullptr, s) : e;
 }
 
 namespace {
@@ -464,7 +484,7 @@ cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int
 // buckets descending (the most gathered counters share L2 lines); two
 // stable partitions, least significant key first.
 cudaError_t degree_sort_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
-                                int32_t *inv, unsigned long long *indeg, cudaStream_t s) {
+                                int32_t *inv, unsigned long long *indeg, bool counted, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
     int64_t *counts = nullptr;
@@ -473,7 +493,7 @@ cudaError_t degree_sort_counted(const int64_t *off, const int32_t *tgt, int64_t 
     cudaError_t e = tmp_alloc(&counts, sizeof(int64_t) * kBuckets * ntiles * 2, s);
     if (e == cudaSuccess) e = tmp_alloc(&keys, 2 * (size_t)n, s);
     if (e == cudaSuccess) e = tmp_alloc(&perm1, sizeof(int32_t) * n, s);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !counted) {
         cudaMemsetAsync(indeg, 0, sizeof(unsigned long long) * n, s);
         if (m > 0) count_targets<<<grid_for(m, 256), 256, 0, s>>>(tgt, m, indeg);
     }
@@ -507,7 +527,7 @@ cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64
     if (n == 0) return cudaSuccess;
     unsigned long long *indeg = nullptr;
     cudaError_t e = tmp_alloc(&indeg, sizeof(unsigned long long) * n, s);
-    if (e == cudaSuccess) e = degree_sort_counted(off, tgt, n, m, perm, inv, indeg, s);
+    if (e == cudaSuccess) e = degree_sort_counted(off, tgt, n, m, perm, inv, indeg, false, s);
     if (indeg) cudaFreeAsync(indeg, s);
     return e;
 }

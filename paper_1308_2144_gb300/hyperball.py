@@ -68,7 +68,7 @@ class HBNotConverged(HBError):
 
 class Options(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("frontier", ctypes.c_int32),
-                ("max_steps", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("max_steps", ctypes.c_int32), ("stream", ctypes.c_void_p), ("arcs_per_slot", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -273,7 +273,7 @@ def _stream_ptr(stream):
 
 def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
                  max_steps=1 << 20, stream=None, profile=False, pull_gather=False,
-                 neighbourhood=False) -> Options:
+                 neighbourhood=False, arcs_per_slot=0) -> Options:
     o = Options()
     load().hb_default_options(ctypes.byref(o))
     o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
@@ -283,6 +283,7 @@ def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, fro
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
     o.max_steps = int(max_steps)
     o.stream = _stream_ptr(stream)
+    o.arcs_per_slot = int(arcs_per_slot)
     return o
 
 

@@ -91,3 +91,31 @@ def test_large_device_transpose(orc):
                        frontier="push")
     walk(orc, hb, off, tgt, 4, 12)
     hb.close()
+
+
+def test_large_host_upload_checked_by_chunks(orc):
+    """Targets from host memory (2^23 arcs and more) are uploaded in chunks,
+    each checked and counted as it arrives: pageable and pinned host CSRs
+    give the oracle's run, and a target out of range in the last chunk is
+    refused with HB_ERR_INVALID while the library stays usable."""
+    off, tgt = graphs.rmat_graph(scale=21, edge_factor=6, seed=21).numpy()
+    n = off.size - 1
+    assert tgt.size >= 1 << 23
+    ref = orc.run(off, tgt, 4, 5)
+    for pinned in (False, True):
+        o, t = torch.from_numpy(off), torch.from_numpy(tgt)
+        if pinned:
+            o, t = o.pin_memory(), t.pin_memory()
+        hb = hbl.HyperBall(o, t, log2m=4, seed=5, n=n)
+        assert hb.run() == ref.steps
+        assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+        hb.close()
+    bad = tgt.copy()
+    bad[-3] = n
+    with pytest.raises(hbl.HBError) as e:
+        hbl.HyperBall(torch.from_numpy(off), torch.from_numpy(bad), log2m=4, seed=5, n=n)
+    assert e.value.status == hbl.HB_ERR_INVALID
+    assert "outside" in str(e.value)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=5, n=n)
+    assert hb.run() == ref.steps
+    hb.close()

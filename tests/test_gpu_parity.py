@@ -380,3 +380,12 @@ def test_every_class_sizing_gives_the_same_result(orc, b, relabel):
     with pytest.raises(hbl.HBError):
         hb.set_class_sizing(3)
     hb.close()
+    # the sizing given at creation (hb_options.arcs_per_slot) is the same
+    for aps in (1, 128):
+        hb = hbl.HyperBall(*to_dev(off, tgt), log2m=b, seed=3, n=off.size - 1, relabel=relabel, arcs_per_slot=aps)
+        assert hb.run() == ref.steps
+        assert np.array_equal(hb.registers().cpu().numpy(), ref.regs)
+        hb.close()
+    with pytest.raises(hbl.HBError) as e:
+        hbl.HyperBall(*to_dev(off, tgt), log2m=b, seed=3, n=off.size - 1, arcs_per_slot=3)
+    assert e.value.status == hbl.HB_ERR_INVALID
