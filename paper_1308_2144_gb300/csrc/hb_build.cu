@@ -401,11 +401,6 @@ cudaError_t check_targets(const int32_t *tgt, int64_t len, int64_t n, unsigned l
     return cudaGetLastError();
 }
 
-cudaError_t validate_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                         unsigned long long *err_dev, cudaStream_t s) {
-    cudaError_t e = validate_offsets(off, n, m, err_dev, s);
-    return e == cudaSuccess ? check_targets(tgt, m, n, err_dev, nullptr, s) : e;
-}
 
 namespace {
 __global__ void weights_in_kernel(const int64_t *w, int64_t n, int64_t *tmp, unsigned long long *err) {
@@ -522,15 +517,6 @@ cudaError_t degree_sort_counted(const int64_t *off, const int32_t *tgt, int64_t 
     return e;
 }
 
-cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
-                        int32_t *inv, cudaStream_t s) {
-    if (n == 0) return cudaSuccess;
-    unsigned long long *indeg = nullptr;
-    cudaError_t e = tmp_alloc(&indeg, sizeof(unsigned long long) * n, s);
-    if (e == cudaSuccess) e = degree_sort_counted(off, tgt, n, m, perm, inv, indeg, false, s);
-    if (indeg) cudaFreeAsync(indeg, s);
-    return e;
-}
 
 cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                         const int32_t *perm, const int32_t *inv, int64_t *noff, int32_t *ntgt,

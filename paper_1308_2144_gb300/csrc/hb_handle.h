@@ -72,27 +72,6 @@ cudaError_t tmp_alloc(T **p, size_t bytes, cudaStream_t s) {
     return tmp_alloc(reinterpret_cast<void **>(p), bytes, s);
 }
 
-// Create-time graph passes that share one in-degree histogram (the step
-// kernel's node order needs it, and so do the reverse lists).
-// degree_sort_counted: degree_sort that leaves the in-degree of each of the
-// caller's nodes in indeg (n entries, device, owned by the caller), or
-// takes them from there when counted is true.
-cudaError_t degree_sort_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
-                                int32_t *inv, unsigned long long *indeg, bool counted, cudaStream_t s);
-// The CSR checks of validate_csr in two parts, so that the target checks
-// can follow an upload chunk by chunk: the offsets, and targets [0, len),
-// which with indeg not null also add each target's in-arc to indeg.
-cudaError_t validate_offsets(const int64_t *off, int64_t n, int64_t m, unsigned long long *err_dev,
-                             cudaStream_t s);
-cudaError_t check_targets(const int32_t *tgt, int64_t len, int64_t n, unsigned long long *err_dev,
-                          unsigned long long *indeg, cudaStream_t s);
-// transpose_csr of a relabelled graph whose node v is the caller's perm[v]
-// (perm null: the identity) and has in-degree indeg[perm[v]]; indeg null
-// counts the in-arcs instead.
-cudaError_t transpose_csr_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                                  const unsigned long long *indeg, const int32_t *perm, int64_t *toff,
-                                  int32_t *ttgt, cudaStream_t s);
-
 // Host-side services of hb_api.cu used by the other translation units.
 hb_status create_handle64(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
                           int log2m, uint64_t seed, const hb_options *opt, hb_graph **out);

@@ -377,13 +377,28 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t x, int64_t &excl) {
 // (defined in hb_build.cu / hb_step.cu; all take the stream last)
 
 cudaError_t scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t N, cudaStream_t s);
-cudaError_t validate_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                         unsigned long long *err_dev, cudaStream_t s);
+// CSR checks (error bits 1 offsets[0] != 0, 2 offsets[n] != m, 4 offsets
+// decrease, 8 a target outside [0, n)) in two parts, so that the target
+// checks can follow an upload chunk by chunk: the offsets, and targets
+// [0, len), which with indeg not null also add each target's in-arc there.
+cudaError_t validate_offsets(const int64_t *off, int64_t n, int64_t m, unsigned long long *err_dev,
+                             cudaStream_t s);
+cudaError_t check_targets(const int32_t *tgt, int64_t len, int64_t n, unsigned long long *err_dev,
+                          unsigned long long *indeg, cudaStream_t s);
 cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaStream_t s);
 cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                           int64_t *toff, int32_t *ttgt, cudaStream_t s);
-cudaError_t degree_sort(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
-                        int32_t *inv, cudaStream_t s);
+// transpose_csr of a relabelled graph whose node v is the caller's perm[v]
+// (perm null: the identity) and has in-degree indeg[perm[v]]; indeg null
+// counts the in-arcs instead.
+cudaError_t transpose_csr_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
+                                  const unsigned long long *indeg, const int32_t *perm, int64_t *toff,
+                                  int32_t *ttgt, cudaStream_t s);
+// Node order for the step kernel (perm: new -> caller's id, inv: its
+// inverse).  indeg (n entries) holds the in-degree of each of the caller's
+// nodes when counted is true, and receives it otherwise.
+cudaError_t degree_sort_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m, int32_t *perm,
+                                int32_t *inv, unsigned long long *indeg, bool counted, cudaStream_t s);
 cudaError_t relabel_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                         const int32_t *perm, const int32_t *inv, int64_t *noff, int32_t *ntgt,
                         cudaStream_t s);

@@ -47,6 +47,33 @@ def test_default_options(lib):
     o = hbl.Options()
     lib.hb_default_options(ctypes.byref(o))
     assert o.flags == 0 and o.frontier == 0 and o.max_steps == 1 << 20 and not o.stream
+    assert o.arcs_per_slot == 0
+
+
+STRUCTS = {"hb_options": hbl.Options, "hb_info": hbl.Info, "hb_graph_desc": hbl.GraphDesc,
+           "hb_server_options": hbl.ServerOptions, "hb_request_info": hbl.RequestInfo}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the header's size and field
+    offsets (a C program built against include/hyperball.h prints them)."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hyperball.h"', "int main(void) {"]
+    for cname, cls in STRUCTS.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                          check=True).stdout.splitlines())
+    for cname, cls in STRUCTS.items():
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert int(got[f"{cname} {field}"]) == getattr(cls, field).offset, (cname, field)
 
 
 @pytest.mark.parametrize("log2m", [0, 3, 13, 20])
