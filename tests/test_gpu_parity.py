@@ -286,7 +286,11 @@ def test_checkpoint_resume_is_bit_identical(tmp_path, plain, frontier):
     path = str(tmp_path / "hb.ckpt")
     a.save(path)
     a.close()
-    h = hbl.hb_load(path, hbl.make_options(frontier=frontier))
+    with pytest.raises(hbl.HBError) as e:   # a class sizing that is no candidate
+        hbl.hb_load(path, hbl.make_options(frontier=frontier, arcs_per_slot=3))
+    assert e.value.status == hbl.HB_ERR_INVALID
+    # the loaded handle takes its class sizing from the options (results never depend on it)
+    h = hbl.hb_load(path, hbl.make_options(frontier=frontier, arcs_per_slot=64 if frontier == "auto" else 0))
     b = hbl.HyperBall.__new__(hbl.HyperBall)
     b._h, b.n, b.p, b.log2m = h, off.size - 1, 16, 4
     b.run()
@@ -299,7 +303,8 @@ def test_checkpoint_resume_is_bit_identical(tmp_path, plain, frontier):
 
 
 @pytest.mark.parametrize("bad", ["first", "last", "decrease", "target_high", "target_neg"])
-def test_malformed_csr_is_rejected(bad):
+@pytest.mark.parametrize("where", ["device", "host"])
+def test_malformed_csr_is_rejected(bad, where):
     off = np.array([0, 2, 3, 5, 6], dtype=np.int64)
     tgt = np.array([1, 2, 0, 3, 1, 2], dtype=np.int32)
     n, m = 4, 6
@@ -313,8 +318,11 @@ def test_malformed_csr_is_rejected(bad):
         tgt[3] = 4
     else:
         tgt[0] = -1
+    o, t = torch.from_numpy(off), torch.from_numpy(tgt)
+    if where == "device":
+        o, t = o.cuda(), t.cuda()
     with pytest.raises(hbl.HBError) as e:
-        hbl.hb_create(torch.from_numpy(off).cuda(), torch.from_numpy(tgt).cuda(), n, m, 4, 1)
+        hbl.hb_create(o, t, n, m, 4, 1)
     assert e.value.status == hbl.HB_ERR_INVALID
 
 
@@ -389,3 +397,42 @@ def test_every_class_sizing_gives_the_same_result(orc, b, relabel):
     with pytest.raises(hbl.HBError) as e:
         hbl.HyperBall(*to_dev(off, tgt), log2m=b, seed=3, n=off.size - 1, arcs_per_slot=3)
     assert e.value.status == hbl.HB_ERR_INVALID
+
+
+def test_pinned_host_outputs(orc, plain):
+    """Outputs in pinned host memory (as the end-to-end path delivers them)
+    equal the device outputs and the oracle, for the centralities,
+    accumulators, registers, frontier and a runs handle's statistics."""
+    off, tgt = plain
+    n = off.size - 1
+    ref = orc.run(off, tgt, 4, 42)
+    hb = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=42, n=n)
+    hb.run()
+
+    def pinned(shape, dtype):
+        return torch.full(shape if isinstance(shape, tuple) else (shape,), 7, dtype=dtype).pin_memory()
+
+    cen = {k: pinned(n, torch.float64) for k in ("closeness", "harmonic", "lin", "reachable")}
+    hbl.hb_get_centralities(hb._h, cen["closeness"], cen["harmonic"], cen["lin"], cen["reachable"])
+    dev = hb.centralities()
+    for k in cen:
+        assert torch.equal(cen[k], dev[k].cpu()), k
+    s, h = pinned(n, torch.float64), pinned(n, torch.float64)
+    hbl.hb_get_accumulators(hb._h, s, h)
+    close(s.numpy(), ref.sumd)
+    close(h.numpy(), ref.harm)
+    regs = pinned((n, 16), torch.uint8)
+    hbl.hb_get_registers(hb._h, regs)
+    assert np.array_equal(regs.numpy(), ref.regs)
+    ch, mk = pinned(n, torch.uint8), pinned(n, torch.uint8)
+    hbl.hb_get_frontier(hb._h, ch, mk)
+    d_ch, d_mk = hb.frontier()
+    assert torch.equal(ch, d_ch.cpu()) and torch.equal(mk, d_mk.cpu())
+    hb.close()
+    runs = hbl.HyperBall.runs(*to_dev(off, tgt), 4, [1, 2, 3, 4], n=n)
+    runs.run()
+    mean, sd = pinned(n, torch.float64), pinned(n, torch.float64)
+    hbl._check(hbl.load().hb_get_run_stats(runs._h, 1, hbl._ptr(mean), hbl._ptr(sd)))
+    d_mean, d_sd = runs.run_stats("harmonic")
+    assert torch.equal(mean, d_mean.cpu()) and torch.equal(sd, d_sd.cpu())
+    runs.close()
