@@ -336,14 +336,19 @@ __device__ __forceinline__ int segment_of(int64_t d, const SegBounds &sb) {
     return -1;   // degree 0
 }
 
+// Nodes per degree segment.  After the degree relabelling a warp's 32
+// nodes nearly always share a segment, so each warp adds its count with one
+// shared-memory atomic per segment present (not 32 on one address).
 __global__ void seg_count_kernel(const int64_t *off, int64_t n, SegBounds sb, unsigned long long *cnt) {
     __shared__ unsigned long long c[kSegs];
     if (threadIdx.x < kSegs) c[threadIdx.x] = 0;
     __syncthreads();
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        int s = segment_of(off[v + 1] - off[v], sb);
-        if (s >= 0) atomicAdd(&c[s], 1ULL);
+    const int lane = threadIdx.x & 31;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = v0 + threadIdx.x;
+        const int s = v < n ? segment_of(off[v + 1] - off[v], sb) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, s);
+        if (s >= 0 && lane == __ffs(peers) - 1) atomicAdd(&c[s], (unsigned long long)__popc(peers));
     }
     __syncthreads();
     if (threadIdx.x < kSegs && c[threadIdx.x]) atomicAdd(&cnt[threadIdx.x], c[threadIdx.x]);
