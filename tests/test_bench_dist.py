@@ -48,3 +48,22 @@ def test_single_rank_is_identity():
     import bench
     assert bench.replica_throughput(500.0, 10.0, 1) == pytest.approx(50000.0)
     assert bench.max_over_ranks(3.0, 1) == 3.0
+
+
+def test_reference_arm_reports_the_oracle():
+    """bench.py --impl reference times the CPU oracle (no GPU) on the same
+    metric and prints one JSON line with the reference arm's keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                        "plain", "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600,
+                       cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 1
+    assert line["unit"] == "arc-updates/s" and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["n"] == 10_000
