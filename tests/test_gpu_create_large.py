@@ -119,3 +119,19 @@ def test_large_host_upload_checked_by_chunks(orc):
     hb = hbl.HyperBall(*to_dev(off, tgt), log2m=4, seed=5, n=n)
     assert hb.run() == ref.steps
     hb.close()
+
+
+@pytest.mark.parametrize("relabel,transpose", [(False, False), (False, True), (True, True)])
+def test_sparse_graph_with_long_empty_runs(orc, relabel, transpose):
+    """3,000 arcs over 60,000 nodes: a 2048-arc tile's sources span far more
+    than 2048 nodes, so the arc passes (reverse lists of the graph in the
+    caller's order, the device transpose) search all offsets per arc."""
+    n = 60_000
+    rng = np.random.default_rng(12)
+    edges = list(zip(rng.integers(0, n, 3000).tolist(), rng.integers(0, n, 3000).tolist()))
+    off, tgt = graphs.from_edges(n, edges, keep_all=True).numpy()
+    given = transpose_np(off, tgt) if transpose else (off, tgt)
+    hb = hbl.HyperBall(*to_dev(*given), log2m=4, seed=3, n=n, frontier="push", relabel=relabel,
+                       transpose=transpose)
+    assert walk(orc, hb, off, tgt, 4, 3) >= 2
+    hb.close()
