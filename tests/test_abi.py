@@ -104,3 +104,23 @@ def test_null_handle_is_rejected(lib):
     assert lib.hb_step(None, None) == hbl.HB_ERR_INVALID
     assert lib.hb_get_registers(None, None) == hbl.HB_ERR_INVALID
     lib.hb_destroy(None)
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """The status codes, flags, frontier policies and request states the
+    binding defines have the header's values."""
+    import subprocess
+    names = sorted(k for k, v in vars(hbl).items() if k.startswith("HB_") and isinstance(v, int))
+    names += [f"HB_FRONTIER_{k.upper()}" for k in hbl.FRONTIER]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(['#include <stdio.h>', '#include "hyperball.h"', "int main(void) {"]
+                             + [f'printf("{nm} %lld\\n", (long long)({nm}));' for nm in names]
+                             + ["return 0;", "}"]))
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    assert len(names) >= 20
+    for nm in names:
+        want = hbl.FRONTIER[nm[len("HB_FRONTIER_"):].lower()] if nm.startswith("HB_FRONTIER_") else getattr(hbl, nm)
+        assert int(got[nm]) == want, nm
