@@ -91,6 +91,18 @@ def test_run_statistics_definition(orc):
     mean, sd = orc.run_stats(off, tgt, b, [7, 7, 7], "harmonic")
     np.testing.assert_allclose(mean, x[0], rtol=1e-15)     # (3x)/3 may round by an ulp
     assert np.all(sd <= 1e-14 * np.abs(x[0]))
+    # the Sec. 7 accumulator, weighted (Sec. 6): the same definition over
+    # the weighted, discounted runs, and an unweighted, undiscounted call
+    # is unaffected by the new arguments
+    w = np.random.default_rng(4).integers(0, 5, size=off.size - 1).astype(np.int64)
+    f = [1.0 / (d * d) for d in range(1, 20)]
+    y = [orc.run(off, tgt, b, s, weights=w, discount=f).disc for s in (7, 8)]
+    mean, sd = orc.run_stats(off, tgt, b, [7, 8], "discounted", weights=w, discount=f)
+    np.testing.assert_allclose(mean, (y[0] + y[1]) / 2, rtol=1e-15)
+    np.testing.assert_allclose(sd, np.abs(y[0] - y[1]) / math.sqrt(2), rtol=1e-12, atol=1e-12)
+    assert np.any(y[0] != y[1])
+    mean, _ = orc.run_stats(off, tgt, b, [7, 8], "harmonic", weights=None, discount=f)
+    np.testing.assert_allclose(mean, (x[0] + x[1]) / 2, rtol=1e-15)
 
 
 def test_run_spread_matches_counter_rsd(orc, plain):
