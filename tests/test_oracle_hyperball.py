@@ -187,3 +187,42 @@ def test_thread_count_does_not_change_results(orc):
         assert r.steps == outs[0].steps
         assert np.array_equal(r.regs, outs[0].regs)
         assert np.array_equal(r.sumd, outs[0].sumd) and np.array_equal(r.harm, outs[0].harm)
+
+
+def _exact_by_brute_force(off, tgt, sources):
+    """Sum of distances, sum of reciprocal distances over y != x, number of
+    nodes at finite distance (x included) and eccentricity, from the
+    brute-force breadth-first distances along the scanned graph's arcs
+    (Sec. 3's definitions of closeness, harmonic and Lin centrality)."""
+    adj = brute.adjacency(off, tgt)
+    out = {"sumd": [], "harm": [], "reach": [], "ecc": []}
+    for x in sources:
+        d = brute.bfs_dist(adj, int(x))
+        out["sumd"].append(float(sum(d.values())))
+        out["harm"].append(sum(1.0 / k for k in d.values() if k > 0))
+        out["reach"].append(float(len(d)))
+        out["ecc"].append(max(d.values()))
+    return {k: np.array(v) for k, v in out.items()}
+
+
+@pytest.mark.parametrize("name", sorted(SMALL))
+@pytest.mark.parametrize("with_sources", [False, True])
+def test_exact_centralities_equal_brute_force_bfs(orc, name, with_sources):
+    """The exact-BFS checker behind the accuracy pins, against breadth-first
+    distances computed independently, on every small graph: all nodes, and
+    a shuffled subset of sources with a repeat."""
+    off, tgt = SMALL[name]
+    n = off.size - 1
+    if with_sources:
+        rng = np.random.default_rng(n + 1)
+        src = rng.permutation(n)[: max(1, (2 * n) // 3)] if n else np.zeros(0, dtype=np.int64)
+        if n:
+            src = np.concatenate([src, src[:1]])
+    else:
+        src = np.arange(n)
+    got = orc.exact_centralities(off, tgt, src if with_sources else None)
+    exp = _exact_by_brute_force(off, tgt, src)
+    assert np.array_equal(got["reach"], exp["reach"]), name
+    assert np.array_equal(got["ecc"], exp["ecc"]), name
+    assert np.array_equal(got["sumd"], exp["sumd"]), name
+    np.testing.assert_allclose(got["harm"], exp["harm"], rtol=1e-12, atol=0)

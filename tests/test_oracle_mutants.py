@@ -51,6 +51,10 @@ MUTANTS = {
                                "return (d >= 0 && d < len) ? table[d] : 0.0;"),
     "discount_not_accumulated": ("if (disc) disc[v] = disc[v] + fdist * delta;",
                                  "if (disc) disc[v] = fdist * delta;"),
+    "exact_reach_excludes_source": ("reach[k] = (double)tail;", "reach[k] = (double)(tail - 1);"),
+    "exact_harmonic_counts_source": ("if (du > 0) { s += (double)du; h += 1.0 / (double)du; }",
+                                     "if (du > 0) { s += (double)du; } h += 1.0 / (double)(du + 1);"),
+    "exact_ecc_off_by_one": ("if (du > e_max) e_max = du;", "if (du + 1 > e_max) e_max = du + 1;"),
     "neighbourhood_skips_a_node": ("for (int64_t v = 0; v < n; ++v) N = N + orc_size(c + v * p, b);",
                                    "for (int64_t v = 1; v < n; ++v) N = N + orc_size(c + v * p, b);"),
 }
@@ -76,6 +80,8 @@ def _checks(orc):
     yield lambda: tw.test_weighted_discounted_accumulators_closed_form(orc, "log", 10, 8, 1)
     yield lambda: tw.test_discounts_that_reduce_to_the_accumulators(orc, "dag")
     yield lambda: tw.test_neighbourhood_function_closed_form(orc)
+    for name in ("dag", "star_in"):
+        yield lambda name=name: th.test_exact_centralities_equal_brute_force_bfs(orc, name, True)
 
 
 def test_unmutated_oracle_passes_every_check(orc):
