@@ -93,6 +93,13 @@ bool on_device(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// True when the byte ranges [p, p + a) and [q, q + b) share a byte.
+bool overlaps(const void *p, size_t a, const void *q, size_t b) {
+    if (!p || !q || a == 0 || b == 0) return false;
+    const uintptr_t x = reinterpret_cast<uintptr_t>(p), y = reinterpret_cast<uintptr_t>(q);
+    return x < y + b && y < x + a;
+}
+
 // Device address of the scratch array on the current device, looked up
 // once per device (with that device current).
 cudaError_t scratch_of(unsigned char **out) {
@@ -133,6 +140,29 @@ extern "C" hb_status hb_step_noalloc(const int64_t *offsets, const int32_t *targ
     for (const void *p : ptrs)
         if (p && !on_device(p))
             return fail(HB_ERR_INVALID, "hb_step_noalloc takes device pointers only");
+    {
+        // Buffers the iteration writes may share no byte with any other
+        // buffer: next must not alias cur (the gather would read counters
+        // this iteration already raised), and a write into offsets, targets
+        // or the other outputs would corrupt what the kernels still read.
+        const int P0 = 1 << log2m;
+        const size_t rb = (size_t)n * (size_t)P0;
+        const struct { const void *p; size_t bytes; bool written; const char *name; } buf[] = {
+            {offsets, sizeof(int64_t) * (size_t)(n + 1), false, "offsets"},
+            {targets, sizeof(int32_t) * (size_t)m, false, "targets"},
+            {cur, rb, false, "cur"},
+            {next, rb, true, "next"},
+            {sumd, sizeof(double) * (size_t)n, true, "sumd"},
+            {harm, sizeof(double) * (size_t)n, true, "harm"},
+            {changed, (size_t)n, true, "changed"}};
+        const int nb = (int)(sizeof(buf) / sizeof(buf[0]));
+        for (int i = 0; i < nb; ++i)
+            for (int j = i + 1; j < nb; ++j)
+                if ((buf[i].written || buf[j].written) &&
+                    overlaps(buf[i].p, buf[i].bytes, buf[j].p, buf[j].bytes))
+                    return fail(HB_ERR_INVALID, std::string("hb_step_noalloc: ") + buf[i].name + " and " +
+                                                    buf[j].name + " overlap");
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char *base = nullptr;
     cudaError_t e = scratch_of(&base);
@@ -140,13 +170,21 @@ extern "C" hb_status hb_step_noalloc(const int64_t *offsets, const int32_t *targ
 
     const Layout y = make_layout(log2m);
     const int P = 1 << log2m;
-    // 1. degree segments and heavy chunks of the caller's CSR
+    // 1. the CSR checks of hb_create (offsets[0] = 0, offsets[n] = m,
+    //    offsets never decrease, every target in [0, n)) into the word after
+    //    the counts, and the degree segments and heavy chunks of the
+    //    caller's CSR; both come back in one copy, before any gather runs.
+    //    The count kernel reads only offsets[0 .. n], so it is safe on a
+    //    malformed CSR too.
     unsigned long long *cnt = reinterpret_cast<unsigned long long *>(base);
-    const size_t cnt_bytes = up256(sizeof(unsigned long long) * (kSegs + 1));
+    unsigned long long *csr_err = cnt + kSegs + 1;
+    const size_t cnt_bytes = up256(sizeof(unsigned long long) * (kSegs + 2));
     Bounds sb;
     for (int k = 0; k < kSegs; ++k) { sb.lo[k] = y.lo[k]; sb.hi[k] = y.hi[k]; }
-    unsigned long long hcnt[kSegs + 1];
+    unsigned long long hcnt[kSegs + 2];
     e = cudaMemsetAsync(cnt, 0, sizeof(hcnt), s);
+    if (e == cudaSuccess) e = validate_offsets(offsets, n, m, csr_err, s);
+    if (e == cudaSuccess) e = check_targets(targets, m, n, csr_err, nullptr, s);
     if (e == cudaSuccess && n > 0) {
         na_count_kernel<<<grid_of(n), 256, 0, s>>>(offsets, n, sb, y.heavy, y.chunk, cnt);
         e = cudaGetLastError();
@@ -154,6 +192,14 @@ extern "C" hb_status hb_step_noalloc(const int64_t *offsets, const int32_t *targ
     if (e == cudaSuccess) e = cudaMemcpyAsync(hcnt, cnt, sizeof(hcnt), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("hb_step_noalloc: ") + cudaGetErrorString(e));
+    if (const unsigned long long bad = hcnt[kSegs + 1]) {
+        std::string why;
+        if (bad & 1) why += " offsets[0] != 0;";
+        if (bad & 2) why += " offsets[n] != m;";
+        if (bad & 4) why += " offsets decrease;";
+        if (bad & 8) why += " a target lies outside [0, n);";
+        return fail(HB_ERR_INVALID, "malformed CSR:" + why);
+    }
     int64_t seg_count[kSegs], seg_begin[kSegs], n_pos = 0;
     for (int k = 0; k < kSegs; ++k) { seg_count[k] = (int64_t)hcnt[k]; seg_begin[k] = n_pos; n_pos += seg_count[k]; }
     const int64_t heavy_nodes = seg_count[0];
@@ -239,11 +285,17 @@ extern "C" hb_status hb_step_noalloc(const int64_t *offsets, const int32_t *targ
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = launch_step_kernel(a, log2m, false, sms * step_blocks_per_sm(log2m, false), s);
-    unsigned long long changed_count = 0;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&changed_count, &ctr->n_changed, sizeof(changed_count), cudaMemcpyDeviceToHost, s);
+    Counters done;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&done, ctr, sizeof(done), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(HB_ERR_CUDA, std::string("hb_step_noalloc: ") + cudaGetErrorString(e));
-    if (n_changed) *n_changed = (int64_t)changed_count;
+    if (done.err) {
+        // the same device-side checks, and the same report, as hb_step
+        std::string why = "a device-side check failed during the step:";
+        if (done.err & kErrCasBound) why += " the pushed union's compare-and-swap loop reached its bound;";
+        if (done.err & kErrTarget) why += " an arc target lies outside [0, n) (debug build check);";
+        return fail(HB_ERR_STATE, why);
+    }
+    if (n_changed) *n_changed = (int64_t)done.n_changed;
     return HB_OK;
 }
