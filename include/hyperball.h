@@ -83,6 +83,9 @@ typedef struct {
     int32_t arcs_per_slot; /* class sizing of the gather from creation (as hb_set_class_sizing:
                               a power of two from 1 to 128), for callers who know it from an
                               earlier hb_tune; 0 = the default, 16.  Results never depend on it. */
+    int32_t hot_nodes;   /* hot range of the two-phase gather from creation (as
+                            hb_set_hot_nodes), for callers who know it from an earlier
+                            hb_tune; 0 = one pass.  Results never depend on it. */
 } hb_options;
 
 typedef struct hb_graph hb_graph;   /* opaque handle */
@@ -106,6 +109,9 @@ typedef struct {
     int64_t push_launches;       /* HB_PROFILE: pushed frontier iterations timed since the last reset */
     double push_ms;              /* HB_PROFILE: their summed duration (push + per-node tail) */
     double push_bytes;           /* HB_PROFILE: their summed algorithmic bytes (see below) */
+    int32_t arcs_per_slot;       /* the gather's class sizing (hb_set_class_sizing, hb_tune) */
+    int32_t hot_nodes;           /* hot range of the two-phase gather, 0 = one pass
+                                    (hb_set_hot_nodes, hb_tune) */
 } hb_info;
 
 /* Algorithmic bytes of one gather-kernel launch, counted from the nodes it
@@ -192,15 +198,34 @@ hb_status hb_reset(hb_graph *g, uint64_t seed);
  * kernel gets (the class sizing: about *arcs_per_slot arcs per lane slot;
  * candidates the powers of two from 1 to 128) by timing the first eight
  * iterations (or all, if the fixpoint comes sooner) with each candidate,
- * twice (ascending, then descending order; the faster time counts), then
- * re-initialise the counters with the handle's seed.
- * Results never depend on the choice.  *arcs_per_slot (may be NULL)
- * receives the choice. */
+ * twice (ascending, then descending order; the faster time counts).  Then,
+ * with that sizing and the same timing, the hot range of the two-phase
+ * gather (hb_set_hot_nodes): one pass, or hot counters of 16, 32, 48, 64 or
+ * 96 MiB, tried when the handle holds one run per row and its counters
+ * exceed the device's L2 cache.  Finally the counters are re-initialised
+ * with the handle's seed.  Results never depend on either choice.
+ * *arcs_per_slot (may be NULL) receives the sizing; hb_get_info reports
+ * both. */
 hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
 
 /* Set the class sizing directly (a power of two from 1 to 128) and
  * re-initialise. */
 hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot);
+
+/* The two-phase gather of dense iterations.  With hot_nodes > 0 (clipped to
+ * n), each dense iteration reads its successors' counters in two passes:
+ * first only arcs whose target is one of the nodes [0, hot_nodes) of the
+ * handle's internal order, then the others.  The register-wise maximum does
+ * not depend on the order in which counters are read, so results are
+ * identical to one pass; what changes is that while the first pass runs,
+ * the random reads fall on hot_nodes * p bytes of counters.  After the
+ * degree relabelling the lowest ids are the nodes of highest out-degree,
+ * and, on graphs whose in- and out-degrees go together (the R-MAT graphs
+ * here), also the most gathered counters, which then stay in L2.  Costs a
+ * second read of the targets and p bytes written and read per node.  0 (the
+ * default) gathers in one pass; handles of several runs per row take only
+ * 0 (HB_ERR_INVALID otherwise).  Takes effect at the next iteration. */
+hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes);
 
 /* Node weights (Sec. 6).  The paper simulates an integer weight w(v) by
  * replicas: the ball of radius 0 around v holds w(v) distinct items, and
@@ -471,16 +496,27 @@ void hb_server_destroy(hb_server *s);
  * start-up so that no request can stall in, or fail on, the allocator; and
  * hosts that hand the library device buffers but no allocator.
  *
- * hb_step_noalloc runs one iteration of Algorithm 2 at loop index t on the
- * CSR graph (offsets: n+1 int64, targets: m int32), reading the counters
- * `cur` (n*p bytes) and writing all of `next` (n*p bytes), exactly as
- * hb_step does for a handle, in the caller's node order: `changed` (n
- * bytes) receives 1 for every node whose counter changed, and for those
- * nodes sumd[v] += (t+1)*d and harm[v] += d/(t+1) (n doubles each, updated
- * in place) with d the change of the FP64 size estimate (Sec. 5).
- * *n_changed (host memory, may be NULL) receives the number of changed
- * nodes; the call returns once every output is written.  Every pointer
- * but n_changed must be device memory; stream may be NULL.
+ * hb_step_noalloc runs one iteration at loop index t on the CSR graph
+ * (offsets: n+1 int64, targets: m int32), in the caller's node order: every
+ * node's new counter is the register-wise maximum of its own counter in
+ * `cur` (n*p bytes) and the counters of its successors, written to `next`
+ * (all n*p bytes).  `changed` (n bytes) receives 1 for every node whose
+ * counter grew, and for those nodes sumd[v] += (t+1)*d and harm[v] +=
+ * d/(t+1) (n doubles each, updated in place), d being the growth of the
+ * counter's FP64 size estimate; other nodes keep sumd and harm.  This is
+ * the iteration hb_step runs on a handle.  *n_changed (host memory, may be
+ * NULL) receives the number of changed nodes.  Every pointer but n_changed
+ * must be device memory; stream may be NULL.  Each call synchronises
+ * `stream` (it reads sizes and the changed count back to the host) and
+ * returns once every output is written.
+ *
+ * Checks, each answered with HB_ERR_INVALID before any kernel reads a
+ * counter: log2m in [4, 12]; the CSR is well formed (offsets[0] = 0,
+ * offsets[n] = m, offsets never decrease, every target in [0, n)); and
+ * next, sumd, harm and changed share no byte with each other nor with
+ * offsets, targets or cur (in particular next may not be cur).  A failed
+ * device-side check during the iteration (the debug build's arc-target
+ * check) returns HB_ERR_STATE with the same message as hb_step.
  *
  * It allocates nothing: its temporary data (degree lists, work plan,
  * partial counters of split nodes, cached estimates, counters) lives in

@@ -100,6 +100,7 @@ void default_opts(hb_options *o) {
     o->max_steps = 1 << 20;
     o->stream = nullptr;
     o->arcs_per_slot = 0;
+    o->hot_nodes = 0;
 }
 
 // The class sizing an options block asks for (0: the default); false if it
@@ -109,6 +110,14 @@ bool sizing_of(const hb_options &o, int *aps) {
     for (int c : kTuneAps)
         if (c == *aps) return true;
     return false;
+}
+
+// The hot range of the two-phase gather for a request of hot_nodes (0:
+// one pass): clipped to n; handles of several runs per row gather in one
+// pass.
+uint32_t hot_window(const hb_graph *g, int64_t hot_nodes) {
+    if (g->lruns || hot_nodes <= 0) return 0u;
+    return (uint32_t)(hot_nodes < g->n ? hot_nodes : g->n);
 }
 
 // Copy `bytes` from a host or device source into device memory.
@@ -229,6 +238,7 @@ hb_status setup_shared(hb_graph *g) {
     a.aps = g->y.aps;
     a.frontier = g->opt.frontier;
     a.sparse_frac = 0.25;
+    a.hot = hot_window(g, g->opt.hot_nodes);
     if (dense_list) {
         int64_t *sb_dev = M.alloc<int64_t>(kSegs);
         unsigned long long *fill = M.alloc<unsigned long long>(kSegs);
@@ -464,6 +474,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         return fail(HB_ERR_INVALID, "unknown frontier policy");
     int aps = 0;
     if (!sizing_of(o, &aps)) return fail(HB_ERR_INVALID, "arcs_per_slot must be 0 or a power of two from 1 to 128");
+    if (o.hot_nodes < 0) return fail(HB_ERR_INVALID, "hot_nodes must be >= 0");
     cudaError_t e = cudaFree(nullptr);   // make sure a context exists
     if (e != cudaSuccess) return cuda_fail(e, "CUDA context");
 
@@ -863,6 +874,8 @@ hb_status hb_get_info(hb_graph *g, hb_info *info) {
     info->push_launches = g->push_launches;
     info->push_ms = g->push_ms;
     info->push_bytes = g->push_bytes;
+    info->arcs_per_slot = g->y.aps;
+    info->hot_nodes = (int32_t)g->a.hot;
     return HB_OK;
 }
 
@@ -909,13 +922,60 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
             best_ms = cand_ms[ci];
             best = kTuneAps[ci];
         }
+    if (st == HB_OK) st = retune(g, best);
+    // then the hot range of the two-phase gather, with that sizing: one
+    // pass, or hot counters filling each candidate share of L2 (single-run
+    // handles whose counters do not fit in L2 alone)
+    uint32_t best_hot = g->a.hot;
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const int64_t row = (int64_t)1 << g->b;
+    if (st == HB_OK && !g->lruns && g->n * row > (int64_t)l2) {
+        std::vector<uint32_t> cands{0u};
+        for (int64_t mb : kTuneHotMiB) {
+            const int64_t h = (mb << 20) / row;
+            if (h < g->n) cands.push_back((uint32_t)h);
+        }
+        const int nh = (int)cands.size();
+        std::vector<float> hot_ms(nh, 1e30f);
+        for (int pass = 0; pass < 2 * nh && st == HB_OK; ++pass) {
+            const int ci = pass < nh ? pass : 2 * nh - 1 - pass;
+            g->a.hot = cands[ci];
+            st = init_state(g, seed);
+            if (st != HB_OK) break;
+            cudaEventRecord(e0, g->s);
+            for (int i = 0; i < kTuneIters && st == HB_OK && !g->converged; ++i) st = hb_step(g, nullptr);
+            cudaEventRecord(e1, g->s);
+            float ms = 0.f;
+            if (st == HB_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < hot_ms[ci])
+                hot_ms[ci] = ms;
+        }
+        float bh = 1e30f;
+        for (int ci = 0; ci < nh; ++ci)
+            if (hot_ms[ci] < bh) {
+                bh = hot_ms[ci];
+                best_hot = cands[ci];
+            }
+        g->a.hot = best_hot;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != HB_OK) return st;
-    st = retune(g, best);
-    if (st == HB_OK) st = init_state(g, seed);
+    st = init_state(g, seed);
     if (st == HB_OK && arcs_per_slot) *arcs_per_slot = best;
     return st;
+}
+
+hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    if (hot_nodes < 0) return fail(HB_ERR_INVALID, "hot_nodes must be >= 0");
+    if (g->lruns && hot_nodes > 0)
+        return fail(HB_ERR_INVALID, "handles of several runs per row gather in one pass");
+    g->a.hot = hot_window(g, hot_nodes);
+    return HB_OK;
 }
 
 hb_status hb_reset(hb_graph *g, uint64_t seed) {

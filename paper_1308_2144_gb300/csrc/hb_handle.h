@@ -96,6 +96,9 @@ constexpr int kTuneAps[] = {1, 2, 4, 8, 16, 32, 64, 128};
 // The autotuner times each candidate over the first iterations (most of a
 // run's work: the dense ones), up to the fixpoint.
 constexpr int kTuneIters = 8;
+// Candidate sizes (MiB of counters) of the hot range of the two-phase
+// gather the autotuner tries, beside one pass.
+constexpr int64_t kTuneHotMiB[] = {16, 32, 48, 64, 96};
 
 }  // namespace hb
 

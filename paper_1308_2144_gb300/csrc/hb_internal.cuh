@@ -158,6 +158,10 @@ struct StepArgs {
     int32_t lruns;                // log2 of the runs sharing each row (0: one run per row)
     const uint64_t *run_seeds;    // hash seed of each run of a row
     double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
+    uint32_t hot;                 // > 0: dense iterations gather in two passes, arcs into
+                                  // counters [0, hot) first (the most gathered ones after the
+                                  // degree relabelling), then the others
+    int32_t pass;                 // which launch of the two-phase gather this is (1 or 2)
 };
 
 // ------------------------------------------------------------ helpers --

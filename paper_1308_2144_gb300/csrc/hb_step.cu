@@ -252,6 +252,14 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
     step_body<LOG2P, F32, false>(a);
 }
 
+// The same gather in two passes (a.pass = 1, then 2): dense iterations
+// first gather the arcs into the hot counters [0, a.hot), then the others.
+template <int LOG2P, bool F32>
+__global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MIN_BLOCKS)
+    step_kernel_two_pass(StepArgs a) {
+    step_body<LOG2P, F32, false, true>(a);
+}
+
 // ------------------------------------------------ pushed frontier union --
 
 // Frontier iteration with the reverse CSR: the counter of every node that
@@ -344,6 +352,24 @@ __global__ void frontier_out_kernel(StepArgs a, const int32_t *inv, uint8_t *cha
 
 template <bool F32>
 cudaError_t launch_step_t(const StepArgs &a, int log2m, int grid, cudaStream_t s) {
+    if (a.hot > 0) {
+        // two launches: pass 1 (hot counters; dense iterations only), pass 2
+        StepArgs a1 = a, a2 = a;
+        a1.pass = 1;
+        a2.pass = 2;
+        switch (log2m) {
+#define HB_CASE(B)                                                        \
+    case B:                                                               \
+        step_kernel_two_pass<B, F32><<<grid, kStepThreads, 0, s>>>(a1);   \
+        step_kernel_two_pass<B, F32><<<grid, kStepThreads, 0, s>>>(a2);   \
+        break;
+            HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+            HB_CASE(12)
+#undef HB_CASE
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (log2m) {
 #define HB_CASE(B) case B: step_kernel<B, F32><<<grid, kStepThreads, 0, s>>>(a); break;
         HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
@@ -478,6 +504,7 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
                   : fp32    ? launch_step_t<true>(a, y.log2m, step_grid, s)
                             : launch_step_t<false>(a, y.log2m, step_grid, s);
     if (e != cudaSuccess) return e;
+    if (a.hot > 0 && !a.lruns) ++k;   // the two-phase gather's second launch
     if (ev) cudaEventRecord(ev[1], s);
     if (a.push_union) {
         e = a.lruns ? launch_runs_tail(a, y.log2m, fp32, step_grid, s)

@@ -82,13 +82,16 @@ __device__ __forceinline__ int32_t arc_target(const int32_t *p, int64_t n, unsig
 // Gather the counters of arcs e, e+S, ... < eend (S = 2^logS) into acc
 // (this lane's chunks), U arcs in flight per lane; full groups of U arcs
 // run without bounds checks (targets were validated at creation; debug
-// builds check them here).  n and err serve the debug check only.
-template <int LOG2P, int UMAX>
+// builds check them here).  n and err serve the debug check only.  WIN:
+// only targets w with w - wlo < wspan (unsigned) are gathered, the others
+// are skipped (the two-phase gather below).
+template <int LOG2P, int UMAX, bool WIN = false>
 __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
                                             const uint8_t *__restrict__ cur, int64_t e,
                                             int64_t eend, int logS, int cl,
                                             uint4 (&acc)[Cfg<LOG2P>::CPL], int64_t n,
-                                            unsigned long long *err) {
+                                            unsigned long long *err, uint32_t wlo = 0u,
+                                            uint32_t wspan = 0u) {
     using C = Cfg<LOG2P>;
     constexpr int U0 = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
     constexpr int U = U0 < UMAX ? U0 : UMAX;
@@ -107,10 +110,13 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c)
 #if HB_DEBUG
-                g[u][c] = w[u] >= 0 ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
-                                    : make_uint4(0u, 0u, 0u, 0u);
+                g[u][c] = (w[u] >= 0 && (!WIN || (uint32_t)w[u] - wlo < wspan))
+                              ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                              : make_uint4(0u, 0u, 0u, 0u);
 #else
-                g[u][c] = ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16);
+                g[u][c] = (!WIN || (uint32_t)w[u] - wlo < wspan)
+                              ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                              : make_uint4(0u, 0u, 0u, 0u);
 #endif
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -127,7 +133,9 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c)
-                g[u][c] = w[u] >= 0 ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16) : z;
+                g[u][c] = (w[u] >= 0 && (!WIN || (uint32_t)w[u] - wlo < wspan))
+                              ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                              : z;
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -393,14 +401,48 @@ __device__ __forceinline__ void node_tail(const StepArgs &a, const uint8_t *__re
                                   sparse, s_changed, rdist64, rdist32, pow2);
 }
 
-template <int LOG2P, bool F32, bool WIDE = false>
+// The two-phase gather of a dense iteration (StepArgs::hot > 0): a first
+// launch (pass 1) gathers only the arcs into the hot counters [0, hot) and
+// leaves each node's partial union in its write-buffer row; a second
+// launch (pass 2) gathers the other arcs, folds that partial in and runs the
+// per-node tail.  The register-wise max is associative and commutative, so
+// the union is the same as one pass over all arcs; only the order in which
+// the counters are read changes, so that while pass 1 runs the random
+// reads touch a set of counters small enough to stay in L2.
+struct Window {
+    uint32_t lo, span;   // targets w with w - lo < span (unsigned) are gathered
+    int pass;            // 0: one pass over all arcs; 1, 2: the passes above
+};
+
+// Pass 1: the partial union of a node goes to its write-buffer row.
+template <int LOG2P>
+__device__ __forceinline__ void store_partial(uint8_t *__restrict__ nxt, int64_t v, int cl,
+                                              const uint4 (&acc)[Cfg<LOG2P>::CPL]) {
+    using C = Cfg<LOG2P>;
+    uint8_t *dst = nxt + v * C::P + cl * 16;
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c) __stcs(reinterpret_cast<uint4 *>(dst + c * C::L * 16), acc[c]);
+}
+
+// Pass 2: fold in the partial union pass 1 left in the write-buffer row.
+template <int LOG2P>
+__device__ __forceinline__ void fold_partial(const uint8_t *__restrict__ nxt, int64_t v, int cl,
+                                             uint4 (&acc)[Cfg<LOG2P>::CPL]) {
+    using C = Cfg<LOG2P>;
+    const uint8_t *src = nxt + v * C::P + cl * 16;
+#pragma unroll
+    for (int c = 0; c < C::CPL; ++c)
+        acc[c] = vmax16(acc[c], __ldcs(reinterpret_cast<const uint4 *>(src + c * C::L * 16)));
+}
+
+template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false>
 __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t pos0,
                                            int64_t pos_end, int logS, const int32_t *list,
                                            int32_t *clist, int32_t *biglist, bool sparse,
                                            unsigned long long *s_changed, double rdist64,
                                            float rdist32, const unsigned long long *pow2,
-                                           bool prefetch) {
+                                           bool prefetch, Window win = Window{0u, 0u, 0}) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int logT = C::LOGL + logS;
@@ -420,17 +462,23 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t wlo = win.lo, wspan = win.span;
     if (logS == C::LOGSMAX)
-        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
+        gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
     else if (a.aps <= 2)
-        gather_arcs<LOG2P, 2>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
+        gather_arcs<LOG2P, 2, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
     else if (a.aps <= 4)
-        gather_arcs<LOG2P, 4>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
+        gather_arcs<LOG2P, 4, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
     else
-        gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err);
+        gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
+    if (WIN && win.pass == 1) {
+        if (active && tl < C::L) store_partial<LOG2P>(nxt, v, cl, acc);
+        return;
+    }
+    if (WIN && win.pass == 2 && active) fold_partial<LOG2P>(nxt, v, cl, acc);
     node_tail<LOG2P, F32, WIDE>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
                                 sparse, s_changed, rdist64, rdist32, pow2);
 }
@@ -438,14 +486,15 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
 // One chunk of a heavy node, by a whole warp.  Each chunk leaves its
 // partial union in scratch; the last chunk to arrive combines them and
 // finishes the node.
-template <int LOG2P, bool F32, bool WIDE = false>
+template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false>
 __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t it,
                                            const int32_t *owner, const int64_t *cstart,
                                            const int32_t *list, int32_t *clist, int32_t *biglist,
                                            bool sparse, unsigned long long *s_changed,
                                            double rdist64, float rdist32,
-                                           const unsigned long long *pow2) {
+                                           const unsigned long long *pow2,
+                                           Window win = Window{0u, 0u, 0}) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int cl = lane & (C::L - 1);
@@ -462,7 +511,8 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P, 64>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err);
+    gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err, win.lo,
+                                win.span);
 #pragma unroll
     for (int o = C::L; o < 32; o <<= 1)
 #pragma unroll
@@ -494,6 +544,11 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
     }
+    if (WIN && win.pass == 1) {
+        if (slot == 0) store_partial<LOG2P>(nxt, v, cl, acc);
+        return;
+    }
+    if (WIN && win.pass == 2) fold_partial<LOG2P>(nxt, v, cl, acc);
     node_tail<LOG2P, F32, WIDE>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
                                 s_changed, rdist64, rdist32, pow2);
 }
@@ -703,12 +758,25 @@ __device__ __forceinline__ void union_tail_item(const StepArgs &a, int t, int64_
 // The gather kernel's body: every work item of the iteration's plan (heavy
 // chunks, then light items of each degree class), with the per-node tail
 // of one run per row or, WIDE, of several runs per row.
-template <int LOG2P, bool F32, bool WIDE>
+template <int LOG2P, bool F32, bool WIDE, bool WIN = false>
 __device__ __forceinline__ void step_body(const StepArgs &a) {
     using C = Cfg<LOG2P>;
     const Counters *ctr = a.ctr;
     const int t = ctr->t;
     const bool sparse = ctr->mode == 1;
+    // WIN: launch a.pass = 1 or 2 of the two-phase gather in dense
+    // iterations; frontier iterations take one pass over all arcs, in the
+    // pass-2 launch
+    Window win{0u, 0xffffffffu, 0};
+    if (WIN) {
+        if (sparse) {
+            if (a.pass == 1) return;
+        } else if (a.pass == 1) {
+            win = Window{0u, a.hot, 1};
+        } else {
+            win = Window{a.hot, (uint32_t)a.n - a.hot, 2};
+        }
+    }
     const Plan *pl = sparse ? a.plan_sparse : a.plan_dense;
     const int32_t *list = sparse ? a.slist : a.dense_list;
     const int32_t *owner = sparse ? a.owner_sparse : a.owner_dense;
@@ -730,7 +798,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     const double rdist64 = 1.0 / (double)(t + 1);
     const float rdist32 = 1.0f / (float)(t + 1);
     // most nodes change in the first iterations: fetch their accumulators early
-    const bool prefetch = !sparse && (t == 0 || 4 * (int64_t)ctr->prev_changed > a.n_pos);
+    const bool prefetch = !sparse && win.pass != 1 && (t == 0 || 4 * (int64_t)ctr->prev_changed > a.n_pos);
     if (threadIdx.x < 2) s_changed[threadIdx.x] = 0;
     if (threadIdx.x < 64) {
         const int M = threadIdx.x, sh = 64 - (WIDE ? a.gb : a.b);
@@ -741,8 +809,8 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = gw; it < items; it += nw) {
         if (it < hch) {
-            heavy_item<LOG2P, F32, WIDE>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
-                                         s_changed, rdist64, rdist32, s_pow2);
+            heavy_item<LOG2P, F32, WIDE, WIN>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
+                                              s_changed, rdist64, rdist32, s_pow2, win);
         } else {
             const int64_t li = it - hch;
             int j = 0;
@@ -751,9 +819,9 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
             for (int q = 1; q < C::NLIGHT; ++q)
                 if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
             const int64_t pos0 = seg0 + ((li - ibj) << j);
-            light_item<LOG2P, F32, WIDE>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
-                                         clist, biglist, sparse, s_changed, rdist64, rdist32, s_pow2,
-                                         prefetch && !WIDE);
+            light_item<LOG2P, F32, WIDE, WIN>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
+                                              clist, biglist, sparse, s_changed, rdist64, rdist32, s_pow2,
+                                              prefetch && !WIDE, win);
         }
     }
     __syncthreads();

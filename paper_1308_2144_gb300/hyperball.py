@@ -51,7 +51,7 @@ EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
            "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
-           "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
+           "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_set_hot_nodes", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
            "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_cancel", "hb_server_take",
            "hb_server_stats", "hb_server_destroy"]
 
@@ -68,7 +68,8 @@ class HBNotConverged(HBError):
 
 class Options(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("frontier", ctypes.c_int32),
-                ("max_steps", ctypes.c_int32), ("stream", ctypes.c_void_p), ("arcs_per_slot", ctypes.c_int32)]
+                ("max_steps", ctypes.c_int32), ("stream", ctypes.c_void_p), ("arcs_per_slot", ctypes.c_int32),
+                ("hot_nodes", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -80,7 +81,8 @@ class Info(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_double), ("kernel_bytes", ctypes.c_double),
                 ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
-                ("push_bytes", ctypes.c_double)]
+                ("push_bytes", ctypes.c_double), ("arcs_per_slot", ctypes.c_int32),
+                ("hot_nodes", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -166,6 +168,8 @@ def load():
         L.hb_get_discounted.argtypes = [_vp, _vp]
         L.hb_set_class_sizing.restype = st
         L.hb_set_class_sizing.argtypes = [_vp, ctypes.c_int32]
+        L.hb_set_hot_nodes.restype = st
+        L.hb_set_hot_nodes.argtypes = [_vp, ctypes.c_int32]
         L.hb_tune.restype = st
         L.hb_tune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
         L.hb_batch_tune.restype = st
@@ -273,7 +277,7 @@ def _stream_ptr(stream):
 
 def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
                  max_steps=1 << 20, stream=None, profile=False, pull_gather=False,
-                 neighbourhood=False, arcs_per_slot=0) -> Options:
+                 neighbourhood=False, arcs_per_slot=0, hot_nodes=0) -> Options:
     o = Options()
     load().hb_default_options(ctypes.byref(o))
     o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
@@ -284,6 +288,7 @@ def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, fro
     o.max_steps = int(max_steps)
     o.stream = _stream_ptr(stream)
     o.arcs_per_slot = int(arcs_per_slot)
+    o.hot_nodes = int(hot_nodes)
     return o
 
 
@@ -683,6 +688,11 @@ class HyperBall:
 
     def set_class_sizing(self, arcs_per_slot: int):
         _check(load().hb_set_class_sizing(self._h, int(arcs_per_slot)))
+
+    def set_hot_nodes(self, hot_nodes: int):
+        """Hot range of the two-phase gather (0: one pass); results do not
+        depend on it."""
+        _check(load().hb_set_hot_nodes(self._h, int(hot_nodes)))
 
     def set_weights(self, weights=None):
         """Node weights by replicas (Sec. 6); restarts the computation."""
