@@ -120,6 +120,34 @@ uint32_t hot_window(const hb_graph *g, int64_t hot_nodes) {
     return (uint32_t)(hot_nodes < g->n ? hot_nodes : g->n);
 }
 
+// Put the two-phase gather's hot range in place: with hot > 0 and the
+// library's own copy of the targets, every node's list is reordered hot
+// targets first (once per hot range) and the passes split each list at
+// hcnt[v]; with the caller's borrowed targets each pass tests every arc.
+hb_status apply_hot(hb_graph *g, int64_t hot_nodes) {
+    const uint32_t hot = hot_window(g, hot_nodes);
+    g->a.hot = hot;
+    g->a.hcnt = nullptr;
+    if (hot == 0 || !g->own_tgt) return HB_OK;
+    if (g->hcnt_hot != hot) {
+        if (!g->hcnt) {
+            g->hcnt = g->mem.alloc<int32_t>((size_t)(g->n > 0 ? g->n : 1));
+            if (!g->hcnt) return fail(HB_ERR_OOM, "out of device memory (hot counts)");
+        }
+        g->hcnt_hot = 0;
+        cudaError_t e = partition_hot(g->off, g->tgt, g->n, g->m, hot, g->hcnt, g->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+        if (e != cudaSuccess) {
+            g->a.hot = 0;
+            return e == cudaErrorMemoryAllocation ? fail(HB_ERR_OOM, "out of device memory (hot partition)")
+                                                   : cuda_fail(e, "hot partition");
+        }
+        g->hcnt_hot = hot;
+    }
+    g->a.hcnt = g->hcnt;
+    return HB_OK;
+}
+
 // Copy `bytes` from a host or device source into device memory.
 cudaError_t to_device(void *dst, const void *src, size_t bytes, cudaStream_t s) {
     if (bytes == 0) return cudaSuccess;
@@ -238,7 +266,7 @@ hb_status setup_shared(hb_graph *g) {
     a.aps = g->y.aps;
     a.frontier = g->opt.frontier;
     a.sparse_frac = 0.25;
-    a.hot = hot_window(g, g->opt.hot_nodes);
+    a.hot = 0;   // the hot range is put in place after set-up (apply_hot)
     if (dense_list) {
         int64_t *sb_dev = M.alloc<int64_t>(kSegs);
         unsigned long long *fill = M.alloc<unsigned long long>(kSegs);
@@ -612,6 +640,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     } else {
         g->off = in_off;
         g->tgt = in_tgt;
+        g->own_tgt = own_in_tgt;
     }
 
     hb_status st;
@@ -619,6 +648,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         NvtxRange nv("setup");
         st = finish_setup(g);
     }
+    if (st == HB_OK && o.hot_nodes > 0) st = apply_hot(g, o.hot_nodes);
     if (g->indeg) M.release(g->indeg);
     g->indeg = nullptr;
     if (st == HB_OK) st = init_state(g, seed);
@@ -941,8 +971,8 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
         std::vector<float> hot_ms(nh, 1e30f);
         for (int pass = 0; pass < 2 * nh && st == HB_OK; ++pass) {
             const int ci = pass < nh ? pass : 2 * nh - 1 - pass;
-            g->a.hot = cands[ci];
-            st = init_state(g, seed);
+            st = apply_hot(g, cands[ci]);
+            if (st == HB_OK) st = init_state(g, seed);
             if (st != HB_OK) break;
             cudaEventRecord(e0, g->s);
             for (int i = 0; i < kTuneIters && st == HB_OK && !g->converged; ++i) st = hb_step(g, nullptr);
@@ -958,7 +988,7 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
                 bh = hot_ms[ci];
                 best_hot = cands[ci];
             }
-        g->a.hot = best_hot;
+        if (st == HB_OK) st = apply_hot(g, best_hot);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -974,8 +1004,7 @@ hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes) {
     if (hot_nodes < 0) return fail(HB_ERR_INVALID, "hot_nodes must be >= 0");
     if (g->lruns && hot_nodes > 0)
         return fail(HB_ERR_INVALID, "handles of several runs per row gather in one pass");
-    g->a.hot = hot_window(g, hot_nodes);
-    return HB_OK;
+    return apply_hot(g, hot_nodes);
 }
 
 hb_status hb_reset(hb_graph *g, uint64_t seed) {
@@ -1332,6 +1361,7 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     }
     if (!ok) { fclose(f); delete g; return fail(HB_ERR_INVALID, "truncated checkpoint or no memory"); }
     hb_status st = finish_setup(g);
+    if (st == HB_OK && o.hot_nodes > 0) st = apply_hot(g, o.hot_nodes);
     if (st == HB_OK) st = init_state(g, h.seed);
     if (st != HB_OK) { fclose(f); delete g; return st; }
     // restore the state of iteration t: counters into both buffers

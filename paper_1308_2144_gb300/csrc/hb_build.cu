@@ -562,9 +562,63 @@ cudaError_t count_degree_segments(const int64_t *off, int64_t n, const Layout &y
 cudaError_t build_dense_list(const int64_t *off, int64_t n, const Layout &y,
                              const int64_t *seg_begin, int32_t *list, unsigned long long *fill,
                              cudaStream_t s) {
-    cudaMemsetAsync(fill, 0, sizeof(unsigned long long) * kSegs, s);
+    cudaError_t e = cudaMemsetAsync(fill, 0, sizeof(unsigned long long) * kSegs, s);
+    if (e != cudaSuccess) return e;
     if (n > 0) dense_list_kernel<<<grid_for(n, 256), 256, 0, s>>>(off, n, bounds_of(y), seg_begin, list, fill);
     return cudaGetLastError();
+}
+
+namespace {
+
+// One warp per node: the node's targets below `hot` first, then the
+// others (each group in its original order), written to out; hcnt[v]
+// receives the size of the first group.  A node's arcs stay in its own
+// range [off[v], off[v+1]), so the CSR is the same graph.
+__global__ void partition_hot_kernel(const int64_t *__restrict__ off, const int32_t *__restrict__ tgt,
+                                     int64_t n, uint32_t hot, int32_t *__restrict__ out, int32_t *hcnt) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = gw; v < n; v += nw) {
+        const int64_t e0 = off[v], e1 = off[v + 1];
+        int64_t c = 0;
+        for (int64_t j0 = e0; j0 < e1; j0 += 32) {
+            const int64_t j = j0 + lane;
+            c += __popc(__ballot_sync(FULL, j < e1 && (uint32_t)tgt[j] < hot));
+        }
+        int64_t hp = e0, cp = e0 + c;
+        for (int64_t j0 = e0; j0 < e1; j0 += 32) {
+            const int64_t j = j0 + lane;
+            const bool valid = j < e1;
+            const int32_t w = valid ? tgt[j] : 0;
+            const bool h = valid && (uint32_t)w < hot;
+            const unsigned bh = __ballot_sync(FULL, h), bc = __ballot_sync(FULL, valid && !h);
+            if (h) out[hp + __popc(bh & lt)] = w;
+            else if (valid) out[cp + __popc(bc & lt)] = w;
+            hp += __popc(bh);
+            cp += __popc(bc);
+        }
+        if (lane == 0) hcnt[v] = (int32_t)c;
+    }
+}
+
+}  // namespace
+
+cudaError_t partition_hot(const int64_t *off, int32_t *tgt, int64_t n, int64_t m, uint32_t hot, int32_t *hcnt,
+                          cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int32_t *tmp = nullptr;
+    cudaError_t e = tmp_alloc(&tmp, sizeof(int32_t) * (size_t)(m > 0 ? m : 1), s);
+    if (e != cudaSuccess) return e;
+    partition_hot_kernel<<<grid_for(32 * n, 256), 256, 0, s>>>(off, tgt, n, hot, tmp, hcnt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(tgt, tmp, sizeof(int32_t) * (size_t)m,
+                                                       cudaMemcpyDeviceToDevice, s);
+    const cudaError_t f = cudaFreeAsync(tmp, s);
+    return e != cudaSuccess ? e : f;
 }
 
 }  // namespace hb

@@ -120,6 +120,9 @@ struct hb_graph {
     int64_t *roff = nullptr;
     int32_t *rtgt = nullptr;
     int32_t *perm = nullptr, *inv = nullptr;
+    bool own_tgt = true;           // tgt is the library's copy (its lists may be reordered)
+    int32_t *hcnt = nullptr;       // two-phase gather: hot arcs at the head of each list
+    uint32_t hcnt_hot = 0;         // the hot range hcnt and the list order were made for
     unsigned long long *indeg = nullptr;   // create time only: in-degree of each caller node
     int64_t *wfirst = nullptr;     // Sec. 6: first replica item of each caller node (n+1), or null
     double *disc = nullptr;        // Sec. 7: discounted accumulator (n), or null

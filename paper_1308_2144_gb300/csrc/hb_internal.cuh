@@ -162,6 +162,8 @@ struct StepArgs {
                                   // counters [0, hot) first (the most gathered ones after the
                                   // degree relabelling), then the others
     int32_t pass;                 // which launch of the two-phase gather this is (1 or 2)
+    const int32_t *hcnt;          // two-phase gather: every node's targets below hot come
+                                  // first, hcnt[v] of them (null: each arc tested in both passes)
 };
 
 // ------------------------------------------------------------ helpers --
@@ -411,6 +413,11 @@ cudaError_t count_degree_segments(const int64_t *off, int64_t n, const Layout &y
 cudaError_t build_dense_list(const int64_t *off, int64_t n, const Layout &y,
                              const int64_t *seg_begin, int32_t *list, unsigned long long *fill,
                              cudaStream_t s);
+
+// Two-phase gather: reorder every node's targets so that those below `hot`
+// come first (within the node's own range), and hcnt[v] = their number.
+cudaError_t partition_hot(const int64_t *off, int32_t *tgt, int64_t n, int64_t m, uint32_t hot, int32_t *hcnt,
+                          cudaStream_t s);
 
 cudaError_t heavy_chunk_total(const int64_t *off, int64_t n, const Layout &y, int64_t *total_host,
                               cudaStream_t s);

@@ -12,6 +12,14 @@
 #ifndef HB_UNROLL
 #define HB_UNROLL 8
 #endif
+// Targets staged in shared memory (1) or read from global memory by each
+// lane (0), and arcs in flight per lane in the staged gather.
+#ifndef HB_STAGE
+#define HB_STAGE 0
+#endif
+#ifndef HB_STAGED_UNROLL
+#define HB_STAGED_UNROLL 4
+#endif
 #ifndef HB_MIN_BLOCKS
 #define HB_MIN_BLOCKS 5
 #endif
@@ -140,6 +148,99 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
+    }
+}
+
+// ------------------------------------------- targets staged in shared memory --
+// In dense iterations of a relabelled graph a warp item's nodes are
+// consecutive ids, so their arcs are one contiguous range of the target
+// array.  The warp copies that range, kTile targets at a time, into its
+// shared-memory tile with coalesced 16-byte loads (32 lanes read 512
+// contiguous bytes per instruction), and each lane then reads its arcs'
+// targets from the tile: one L1 request per 128 targets instead of one per
+// arc and lane, and the gathers no longer wait on a global load of their
+// target.
+constexpr int kTile = 512;                 // targets per warp tile
+constexpr int kWarpsPerBlock = kStepThreads / 32;
+
+// Copy targets [cb, ce) (cb a multiple of 4, ce <= cb + kTile, rounded up
+// to a multiple of 4 as far as targets exist, < m) into tile; called by
+// the whole warp, followed by __syncwarp.
+__device__ __forceinline__ void load_tile(int32_t *tile, const int32_t *__restrict__ tgt, int64_t cb,
+                                          int64_t ce, int64_t m, int lane) {
+    const int nq = (int)((ce - cb + 3) >> 2);
+    for (int q = lane; q < nq; q += 32) {
+        const int64_t e = cb + 4 * q;
+        if (e + 4 <= m) {
+            reinterpret_cast<int4 *>(tile)[q] = __ldcs(reinterpret_cast<const int4 *>(tgt + e));
+        } else {
+            for (int i = 0; i < 4; ++i)
+                if (e + i < m) tile[4 * q + i] = ld_stream(tgt + e + i);
+        }
+    }
+}
+
+// As gather_arcs, for arcs e, e+S, ... < eend that all lie in the tile
+// holding targets [cb, cb + kTile).
+template <int LOG2P, int UMAX, bool WIN = false>
+__device__ __forceinline__ void gather_staged(const int32_t *tile, int64_t cb,
+                                              const uint8_t *__restrict__ cur, int64_t e, int64_t eend,
+                                              int logS, int cl, uint4 (&acc)[Cfg<LOG2P>::CPL], int64_t n,
+                                              unsigned long long *err, uint32_t wlo, uint32_t wspan) {
+    using C = Cfg<LOG2P>;
+    constexpr int U0 = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_STAGED_UNROLL));
+    constexpr int U = U0 < UMAX ? U0 : UMAX;
+    if (e >= eend) return;
+    const int cnt = (int)((eend - e + (1LL << logS) - 1) >> logS);
+    const int32_t *tp = tile + (e - cb);
+    const uint8_t *base = cur + cl * 16;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (int j = 0; j < cnt; j += U) {
+        int32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            w[u] = j + u < cnt ? tp[(j + u) << logS] : -1;
+#if HB_DEBUG
+            if (w[u] >= 0 && (uint64_t)(uint32_t)w[u] >= (uint64_t)n) {
+                atomicOr(err, kErrTarget);
+                w[u] = -1;
+            }
+#endif
+        }
+        uint4 g[U][C::CPL];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c)
+                g[u][c] = (w[u] >= 0 && (!WIN || (uint32_t)w[u] - wlo < wspan))
+                              ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                              : z;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], g[u][c]);
+    }
+}
+
+// The arcs e0, e0+S, ... < e1 of one lane, gathered tile by tile over the
+// warp's contiguous arc range [A0, A1) (which contains [e0, e1)).  Called
+// by the whole warp.
+template <int LOG2P, int UMAX, bool WIN = false>
+__device__ __forceinline__ void gather_range_staged(int32_t *tile, const int32_t *__restrict__ tgt, int64_t m,
+                                                    const uint8_t *__restrict__ cur, int64_t A0, int64_t A1,
+                                                    int64_t e0, int64_t e1, int logS, int cl,
+                                                    uint4 (&acc)[Cfg<LOG2P>::CPL], int64_t n,
+                                                    unsigned long long *err, uint32_t wlo, uint32_t wspan) {
+    const int lane = threadIdx.x & 31;
+    const int64_t S = 1LL << logS;
+    for (int64_t cb = A0 & ~(int64_t)3; cb < A1; cb += kTile) {
+        __syncwarp();
+        load_tile(tile, tgt, cb, cb + kTile < A1 ? cb + kTile : A1, m, lane);
+        __syncwarp();
+        const int64_t ce = cb + kTile < e1 ? cb + kTile : e1;
+        int64_t e = e0;
+        if (e < cb) e += ((cb - e + S - 1) >> logS) << logS;
+        if (e < ce) gather_staged<LOG2P, UMAX, WIN>(tile, cb, cur, e, ce, logS, cl, acc, n, err, wlo, wspan);
     }
 }
 
@@ -442,7 +543,8 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
                                            int32_t *clist, int32_t *biglist, bool sparse,
                                            unsigned long long *s_changed, double rdist64,
                                            float rdist32, const unsigned long long *pow2,
-                                           bool prefetch, Window win = Window{0u, 0u, 0}) {
+                                           bool prefetch, Window win = Window{0u, 0u, 0},
+                                           int32_t *tile = nullptr) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int logT = C::LOGL + logS;
@@ -457,13 +559,32 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
         v = list ? (int64_t)list[pos] : pos;
         e0 = a.off[v];
         e1 = a.off[v + 1];
+        if (WIN && win.pass != 0 && a.hcnt) {
+            // partitioned lists: the hot targets are the node's first hcnt[v] arcs
+            const int64_t sp = e0 + a.hcnt[v];
+            if (win.pass == 1) e1 = sp;
+            else e0 = sp;
+        }
         if (prefetch && tl == 0) prefetch_accumulators(a, v, F32);
     }
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
     const uint32_t wlo = win.lo, wspan = win.span;
-    if (logS == C::LOGSMAX)
+    if (tile) {
+        // consecutive nodes pos0 .. : their arcs are one contiguous range
+        const int64_t plast = pos0 + (32 >> logT) < pos_end ? pos0 + (32 >> logT) : pos_end;
+        const int64_t A0 = a.off[pos0], A1 = a.off[plast];
+        if (a.aps <= 2)
+            gather_range_staged<LOG2P, 2, WIN>(tile, a.tgt, a.m, cur, A0, A1, e0 + slot, e1, logS, cl, acc, a.n,
+                                               &a.ctr->err, wlo, wspan);
+        else if (a.aps <= 4 && logS != C::LOGSMAX)
+            gather_range_staged<LOG2P, 4, WIN>(tile, a.tgt, a.m, cur, A0, A1, e0 + slot, e1, logS, cl, acc, a.n,
+                                               &a.ctr->err, wlo, wspan);
+        else
+            gather_range_staged<LOG2P, 64, WIN>(tile, a.tgt, a.m, cur, A0, A1, e0 + slot, e1, logS, cl, acc,
+                                                a.n, &a.ctr->err, wlo, wspan);
+    } else if (logS == C::LOGSMAX)
         gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
     else if (a.aps <= 2)
         gather_arcs<LOG2P, 2, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
@@ -494,7 +615,7 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
                                            bool sparse, unsigned long long *s_changed,
                                            double rdist64, float rdist32,
                                            const unsigned long long *pow2,
-                                           Window win = Window{0u, 0u, 0}) {
+                                           Window win = Window{0u, 0u, 0}, int32_t *tile = nullptr) {
     using C = Cfg<LOG2P>;
     const int lane = threadIdx.x & 31;
     const int cl = lane & (C::L - 1);
@@ -506,13 +627,25 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
     const int64_t pos = a.seg_begin[0] + hp;
     const int64_t v = list ? (int64_t)list[pos] : pos;
     const int64_t a1 = a.off[v + 1];
-    const int64_t e0 = a.off[v] + k * C::CHUNK;
-    const int64_t e1 = e0 + C::CHUNK < a1 ? e0 + C::CHUNK : a1;
+    int64_t e0 = a.off[v] + k * C::CHUNK;
+    int64_t e1 = e0 + C::CHUNK < a1 ? e0 + C::CHUNK : a1;
+    if (WIN && win.pass != 0 && a.hcnt) {
+        // partitioned lists: this pass takes the chunk's part of the node's
+        // first hcnt[v] arcs (pass 1) or of the rest (pass 2)
+        const int64_t sp = a.off[v] + a.hcnt[v];
+        if (win.pass == 1) e1 = e1 < sp ? e1 : sp;
+        else e0 = e0 > sp ? e0 : sp;
+        if (e1 < e0) e1 = e0;
+    }
     uint4 acc[C::CPL];
 #pragma unroll
     for (int c = 0; c < C::CPL; ++c) acc[c] = make_uint4(0u, 0u, 0u, 0u);
-    gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err, win.lo,
-                                win.span);
+    if (tile)
+        gather_range_staged<LOG2P, 64, WIN>(tile, a.tgt, a.m, cur, e0, e1, e0 + slot, e1, C::LOGSMAX, cl, acc,
+                                            a.n, &a.ctr->err, win.lo, win.span);
+    else
+        gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err, win.lo,
+                                    win.span);
 #pragma unroll
     for (int o = C::L; o < 32; o <<= 1)
 #pragma unroll
@@ -771,6 +904,9 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     if (WIN) {
         if (sparse) {
             if (a.pass == 1) return;
+        } else if (a.hcnt) {
+            // partitioned lists: each pass takes its own part of every list
+            win = Window{0u, 0xffffffffu, a.pass == 1 ? 1 : 2};
         } else if (a.pass == 1) {
             win = Window{0u, a.hot, 1};
         } else {
@@ -795,6 +931,12 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     for (int j = 0; j < C::NLIGHT; ++j) cnt[j] = pl->count[j + 1];
     __shared__ unsigned long long s_changed[2];   // changed nodes; WIDE: mask of changed runs
     __shared__ unsigned long long s_pow2[64];
+    __shared__ int4 s_tile[kWarpsPerBlock][kTile / 4];
+    // targets staged in shared memory when a warp item's nodes are
+    // consecutive ids (no node list) and the target array is 16-byte aligned
+    int32_t *tile = (HB_STAGE && list == nullptr && (reinterpret_cast<uintptr_t>(a.tgt) & 15) == 0)
+                        ? reinterpret_cast<int32_t *>(s_tile[threadIdx.x >> 5])
+                        : nullptr;
     const double rdist64 = 1.0 / (double)(t + 1);
     const float rdist32 = 1.0f / (float)(t + 1);
     // most nodes change in the first iterations: fetch their accumulators early
@@ -810,7 +952,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     for (int64_t it = gw; it < items; it += nw) {
         if (it < hch) {
             heavy_item<LOG2P, F32, WIDE, WIN>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
-                                              s_changed, rdist64, rdist32, s_pow2, win);
+                                              s_changed, rdist64, rdist32, s_pow2, win, tile);
         } else {
             const int64_t li = it - hch;
             int j = 0;
@@ -821,7 +963,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
             const int64_t pos0 = seg0 + ((li - ibj) << j);
             light_item<LOG2P, F32, WIDE, WIN>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
                                               clist, biglist, sparse, s_changed, rdist64, rdist32, s_pow2,
-                                              prefetch && !WIDE, win);
+                                              prefetch && !WIDE, win, tile);
         }
     }
     __syncthreads();

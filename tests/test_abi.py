@@ -33,10 +33,17 @@ def test_every_declared_symbol_is_exported(lib):
     assert sorted(hbl.EXPORTS) == sorted(n for n in names if n in hbl.EXPORTS)
 
 
-def test_library_is_built_for_sm103a():
-    out = build.nvcc()
-    assert os.path.exists(out)
-    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+def test_library_is_built_for_sm103a(tmp_path):
+    """One translation unit compiled with the library's own arch and flags:
+    ptxas reports every kernel it assembles for sm_103a and none for any
+    other target."""
+    import subprocess
+    src = os.path.join(os.path.dirname(build.__file__), "csrc", "hb_noalloc.cu")
+    r = subprocess.run([build.nvcc(), *build.ARCH, *build.FLAGS, "-Xptxas", "-v", "-c", src,
+                        "-o", str(tmp_path / "x.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    targets = re.findall(r"for '(sm_\w+)'", r.stderr)
+    assert targets and set(targets) == {"sm_103a"}, set(targets)
 
 
 def test_version_string(lib):

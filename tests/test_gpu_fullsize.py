@@ -6,12 +6,14 @@ times (frontier AUTO, degree relabelling, FP64 estimates, default grid).
   every iteration's changed set, the final registers and the iteration
   count must be bit-exact, accumulators and centralities within 1e-9.
 * web-like graph (R-MAT scale 28, 4.26G arcs, log2m 4, FP32 estimates):
-  too large for a full oracle run, so (a) a 1M-node induced subgraph is
-  checked completely, and (b) on the full graph the counters after the
-  first two iterations are checked on sampled nodes against unions the
-  oracle's initial counters define, plus monotonicity on the sample.
-  Set HB_SKIP_WEB=1 to skip (b) on machines without ~120 GB of device
-  memory.
+  too large for a full oracle run, so (a) the same recipe at scale 22
+  (4.2M nodes, 66M arcs) is checked against the oracle at every iteration,
+  (b) on the full graph the counters after the first two iterations are
+  checked on sampled nodes against unions the oracle's initial counters
+  define, plus monotonicity on the sample, and (c) on the full graph the
+  pushed frontier, the gathered frontier and the two-phase gather agree
+  bit for bit to the fixpoint.  Set HB_SKIP_WEB=1 to skip (b) and (c) on
+  machines without ~200 GB of device memory.
 
 Precision form (A8): the FP32-estimate run is compared with the FP64 run
 and the oracle; the error of each centrality (max, p99, median relative)
@@ -121,43 +123,95 @@ def web():
     if os.environ.get("HB_SKIP_WEB"):
         pytest.skip("HB_SKIP_WEB set")
     free, _ = torch.cuda.mem_get_info()
-    if free < 120 * 2**30:
-        pytest.skip("needs ~120 GB of free device memory")
+    if free < 200 * 2**30:
+        pytest.skip("needs ~200 GB of free device memory")
     g = graphs.web_graph(device="cuda")
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     return g
 
 
-def test_web_induced_subgraph_full_parity(orc, web):
-    """A seeded 1M-node induced subgraph of the web-like graph, checked
-    completely in both precision forms."""
-    g = web
-    sample = graphs.permutation(g.n, 77, 9, device="cuda")[:1_000_000]
-    sub = graphs.induced_subgraph(g, torch.sort(sample).values)
-    off, tgt = sub.numpy()
-    b, seed = 4, 42
-    ref = orc.run(off, tgt, b, seed)
-    fin = orc.finalize(b, ref.regs, ref.sumd, ref.harm)
-    for fp32 in (False, True):
-        hb = hbl.HyperBall(sub.offsets, sub.targets, log2m=b, seed=seed, n=sub.n, fp32=fp32)
-        assert hb.run() == ref.steps
-        assert np.array_equal(hb.registers(device="cpu").numpy(), ref.regs)
+@pytest.mark.parametrize("fp32,hot", [(False, None), (True, None), (True, "eighth")])
+def test_web_recipe_scale22_every_iteration(orc, fp32, hot):
+    """The web-like recipe at a size the oracle runs whole: R-MAT (0.57,
+    0.19, 0.19, 0.05) at scale 22 (4,194,304 nodes), edge factor 16, labels
+    permuted, transpose scanned, log2m 4, in bench.py's launch configuration
+    (frontier AUTO, degree relabelling, the autotuner's class sizing and hot
+    range), or with the two-phase gather forced to a hot range of n/8.  At
+    every iteration: registers and changed set bit-exact, the FP64
+    accumulators within 1e-9 (FP32 estimates: within the bound of the
+    precision form), and the iteration count exact."""
+    g = graphs.web_graph(scale=22, device="cuda", bucket_bits=2)
+    off, tgt = g.numpy()
+    n, b, seed = g.n, 4, 42
+    hb = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=n, fp32=fp32)
+    if hot is None:
+        hb.tune()
+    else:
+        hb.set_hot_nodes(n // 8)
+    c = orc.init(n, b, seed)
+    s_ref, h_ref = np.zeros(n), np.zeros(n)
+    assert np.array_equal(hb.registers(device="cpu").numpy(), c)
+    t = 0
+    while True:
+        c, ch, k = orc.step(off, tgt, b, t, c, s_ref, h_ref)
+        assert hb.step() == k, t
+        assert np.array_equal(hb.registers(device="cpu").numpy(), c), t
+        gch, _ = hb.frontier(device="cpu")
+        assert np.array_equal(gch.numpy(), ch), t
         s, h = (x.numpy() for x in hb.accumulators(device="cpu"))
-        cen = {k: v.numpy() for k, v in hb.centralities(device="cpu").items()}
         if not fp32:
-            close(s, ref.sumd)
-            close(h, ref.harm)
-            for key in fin:
-                close(cen[key], fin[key])
-        else:
-            T = ref.steps
-            reach = fin["reachable"]
-            assert np.all(np.abs(s - ref.sumd) <= 2.0 ** -20 * reach * T * T + 1e-12)
-            assert np.all(np.abs(h - ref.harm) <= 2.0 ** -20 * reach * (1 + math.log(T)) + 1e-12)
-            rep = [_rel_report(k, cen[k], fin[k]) for k in ("closeness", "harmonic", "lin", "reachable")]
-            print("\nPRECISION_REPORT web-1M-subgraph vs oracle " + json.dumps(rep))
-        hb.close()
+            close(s, s_ref)
+            close(h, h_ref)
+        t += 1
+        if k == 0:
+            break
+    assert t >= 6
+    fin = orc.finalize(b, c, s_ref, h_ref)
+    cen = {k_: v.numpy() for k_, v in hb.centralities(device="cpu").items()}
+    if fp32:
+        reach = fin["reachable"]
+        assert np.all(np.abs(s - s_ref) <= 2.0 ** -20 * reach * t * t + 1e-12)
+        assert np.all(np.abs(h - h_ref) <= 2.0 ** -20 * reach * (1 + math.log(t)) + 1e-12)
+        rep = [_rel_report(k_, cen[k_], fin[k_]) for k_ in ("closeness", "harmonic", "lin", "reachable")]
+        print("\nPRECISION_REPORT web-recipe-scale22 vs oracle " + json.dumps(rep))
+    else:
+        for key in fin:
+            close(cen[key], fin[key])
+    hb.close()
+
+
+def test_web_full_size_pushed_gathered_two_pass_agree(web):
+    """The full web-like graph, FP32 estimates: the pushed frontier (bench's
+    configuration), the gathered frontier and the two-phase gather (hot
+    range of 64 MiB of counters) agree bit for bit through to the fixpoint:
+    counters and changed sets at every iteration, then accumulators and
+    centralities."""
+    g = web
+    b, seed = 4, 42
+    hp = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n, fp32=True)
+    hg = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n, fp32=True, pull_gather=True)
+    hg.set_hot_nodes((64 << 20) >> b)
+    t = 0
+    while True:
+        kp, kg = hp.step(), hg.step()
+        assert kp == kg, t
+        assert torch.equal(hp.registers(), hg.registers()), t
+        fp, fg = hp.frontier(), hg.frontier()
+        assert torch.equal(fp[0], fg[0]), t
+        del fp, fg
+        t += 1
+        if kp == 0:
+            break
+    assert 5 <= t <= 64
+    for x, y in zip(hp.accumulators(), hg.accumulators()):
+        assert torch.equal(x, y)
+    cp, cg = hp.centralities(), hg.centralities()
+    for key in cp:
+        assert torch.equal(cp[key], cg[key]), key
+    assert hg.info()["hot_nodes"] == (64 << 20) >> b
+    hp.close()
+    hg.close()
 
 
 def test_web_full_size_sampled(orc, web):
