@@ -13,10 +13,15 @@ autotuner unless --aps fixes it.
 
 Metric: arc-updates per second (arcs scanned by all iterations / time to
 fixpoint), plus time to fixpoint and the roofline fraction of the gather
-kernel.  The default workload is the encyclopedia-link-like graph: R-MAT
-(0.57, 0.19, 0.19, 0.05) with 4,206,785 nodes and 101,355,853 arcs drawn,
-scanned as its transpose, log2m = 6.  Under torchrun each rank runs an
-independent replica (weak scaling); rank 0 prints one JSON line.
+kernel.  The default workload is the largest single graph, the web-like
+precision form: R-MAT (0.57, 0.19, 0.19, 0.05) at scale 28 (268,435,456
+nodes) with edge factor 16 (2^32 arcs drawn, 4.26G after dedup), int64
+offsets, scanned as its transpose, log2m = 4, FP32 estimates and FP64
+accumulators.  The encyclopedia-like graph (4,206,785 nodes, 101,355,853
+arcs drawn, log2m = 6, FP64) is measured the same way under "secondary",
+and a reduced run of the batched and served forms against one graph at a
+time under "forms".  Under torchrun each rank runs an independent replica
+(weak scaling); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -150,6 +155,16 @@ def recorded_traffic(workload):
         return None
 
 
+def recorded_traffic_note(workload):
+    """Why no DRAM traffic accompanies this workload's line."""
+    path = os.path.join(ROOT, "profiles", f"step_kernel_{workload}_traffic.txt")
+    if not os.path.exists(path):
+        return (f"no committed capture for this workload (profiles/step_kernel_{workload}_traffic.txt): "
+                "a full-size capture exceeds the profiling size rule and its traffic does not scale with "
+                "size (the L2 hit rate falls as the counters grow); see the profiling-size captures")
+    return "the committed capture was taken on other kernel sources (digest mismatch)"
+
+
 def kernel_source_digest():
     """sha256 over the sources the gather kernel is compiled from."""
     h = hashlib.sha256()
@@ -205,85 +220,142 @@ def replica_throughput(units, ms, world):
 
 # ------------------------------------------------------------- the oracle --
 
-def cpu_oracle_sample(g_cpu, log2m, seed, budget_s=20.0, max_iters=64):
-    """The oracle, as it stands, on the host cores: Algorithm 2 on the full
-    graph (every node recomputed each iteration) until the fixpoint or until
-    the time budget is spent."""
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo or lscpu)."""
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu model")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return "unknown"
+
+
+def _oracle_rows(oracle, off, tgt, log2m, c, rows):
+    """One Algorithm 2 iteration (t = 0) of the oracle, as it stands, on the
+    first `rows` nodes of the graph (their arcs reach every node's counter
+    in c); returns (arc-updates, seconds)."""
+    n = off.size - 1
+    sumd = np.zeros(n)
+    harm = np.zeros(n)
+    t0 = time.perf_counter()
+    oracle.step(off[:rows + 1], tgt, log2m, 0, c, sumd, harm)
+    return int(off[rows] - off[0]), time.perf_counter() - t0
+
+
+def _sized_rows(oracle, off, tgt, log2m, c, budget_s):
+    """A prefix of the rows whose oracle iteration takes about budget_s
+    (labels are permuted, so a prefix is a uniform node sample)."""
+    n = off.size - 1
+    rows = min(n, max(1024, n // 4096))
+    arcs, secs = _oracle_rows(oracle, off, tgt, log2m, c, rows)
+    while rows < n and secs < 0.25 * budget_s:
+        rows = min(n, rows * 4)
+        arcs, secs = _oracle_rows(oracle, off, tgt, log2m, c, rows)
+    if rows < n and secs > 0:
+        rows = int(min(n, max(rows, rows * budget_s / secs)))
+    return rows
+
+
+def cpu_oracle_sample(g_cpu, log2m, seed, budget_s=12.0, budget_one_s=6.0):
+    """The oracle, as it stands, on the host cores: one Algorithm 2
+    iteration (every sampled node recomputed from all its successors) over a
+    prefix of the nodes sized to about budget_s with every thread, and over
+    a smaller prefix with one thread."""
     import oracle
     off, tgt = g_cpu
     n = off.size - 1
     c = oracle.init(n, log2m, seed)
-    sumd = np.zeros(n)
-    harm = np.zeros(n)
-    arcs, secs, iters = 0, 0.0, 0
-    for t in range(max_iters):
-        t0 = time.perf_counter()
-        c, _, k = oracle.step(off, tgt, log2m, t, c, sumd, harm)
-        secs += time.perf_counter() - t0
-        arcs += tgt.size
-        iters += 1
-        if k == 0 or secs > budget_s:
-            break
-    return {"value": arcs / secs, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": f"{iters} iteration(s) of Algorithm 2 on the full graph"
-                      f"{' (to the fixpoint)' if k == 0 else ' (time budget)'}: {arcs} arc-updates in "
-                      f"{secs:.2f} s, every node recomputed each iteration"}
+    threads = oracle.get_threads()
+    rows = _sized_rows(oracle, off, tgt, log2m, c, budget_s)
+    arcs, secs = _oracle_rows(oracle, off, tgt, log2m, c, rows)
+    oracle.set_threads(1)
+    try:
+        rows1 = _sized_rows(oracle, off, tgt, log2m, c, budget_one_s)
+        arcs1, secs1 = _oracle_rows(oracle, off, tgt, log2m, c, rows1)
+    finally:
+        oracle.set_threads(0)
+    return {"value": arcs / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "sample": f"one Algorithm 2 iteration (t = 0, every sampled node recomputed from all its "
+                      f"successors) over the first {rows} of {n} nodes (a uniform sample: labels are "
+                      f"permuted): {arcs} arc-updates in {secs:.2f} s on {threads} threads",
+            "single_thread": {"value": arcs1 / secs1, "unit": UNIT, "cores": 1,
+                              "sample": f"the same iteration over the first {rows1} nodes: {arcs1} "
+                                        f"arc-updates in {secs1:.2f} s"}}
 
 
 # ------------------------------------------------------------------ arms --
 
 def run_reference(args, world, rank):
+    """The oracle on the host cores, as it stands: each step is one
+    Algorithm 2 iteration over a fixed prefix of the workload's nodes (a
+    uniform sample; sized at setup to about --ref-step-s seconds)."""
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     g = make_graph(args.workload, dev)
     off, tgt = g.numpy()
+    del g
     import oracle
     n = off.size - 1
-    vals, secs_all = [], []
+    c = oracle.init(n, wl["log2m"], wl["seed"])
+    rows = _sized_rows(oracle, off, tgt, wl["log2m"], c, args.ref_step_s)
+    secs_all, arcs_all = [], 0
     for k in range(args.warmup + args.steps):
-        c = oracle.init(n, wl["log2m"], wl["seed"] + k)
-        sumd, harm = np.zeros(n), np.zeros(n)
-        t0 = time.perf_counter()
-        oracle.step(off, tgt, wl["log2m"], 0, c, sumd, harm)
-        dt = time.perf_counter() - t0
+        arcs, dt = _oracle_rows(oracle, off, tgt, wl["log2m"], c, rows)
         if k >= args.warmup:
             secs_all.append(dt)
+            arcs_all += arcs
     total = sum(secs_all)
-    value = tgt.size * len(secs_all) / total
+    value = arcs_all / total
+    sample = (f"one Algorithm 2 iteration (t = 0, every sampled node recomputed from all its successors) "
+              f"over the first {rows} of {n} nodes per step (a uniform sample: labels are permuted)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(secs_all),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "n": int(n), "m": int(tgt.size),
-                   "step": "one full iteration of Algorithm 2 (every node recomputed) by the CPU oracle"},
+        "config": {"workload": wl["desc"], "n": int(n), "m": int(tgt.size), "log2m": wl["log2m"],
+                   "step": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.get_threads(), "kind": "oracle",
-                         "sample": "one iteration of Algorithm 2 on the full graph per step"},
+                         "nproc": os.cpu_count(), "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, world, rank, local):
-    from paper_1308_2144_gb300 import build, hyperball as hbl
-    build.build()
-    hbl.load()
-    wl = WORKLOADS[args.workload]
-    fp32 = args.fp32 or args.workload.startswith("web")
-    stream = torch.cuda.current_stream()
-    g = make_graph(args.workload, "cuda")
+def measure(args, name, world, local, stream, with_e2e):
+    """One workload on the GPU: setup (graph, handle, tuning), W untimed
+    and K timed whole computations, the gather kernel's roofline; returns
+    the fields of the JSON line."""
+    from paper_1308_2144_gb300 import hyperball as hbl
+    wl = WORKLOADS[name]
+    fp32 = args.fp32 or name.startswith("web")
+    g = make_graph(name, "cuda")
     n, m, log2m = g.n, g.m, wl["log2m"]
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     opts = dict(log2m=log2m, seed=wl["seed"], n=n, fp32=fp32, frontier=args.frontier,
                 stream=stream, profile=True, relabel=not args.no_relabel)
     hb = hbl.HyperBall(g.offsets, g.targets, **opts)
-    # class sizing (arcs per slot): part of setup, like the relabelling
-    aps = hb.tune() if args.aps == "tune" else int(args.aps)
-    if args.aps != "tune":
+    # class sizing and hot range of the gather: part of setup, like the relabelling
+    if args.aps == "tune":
+        aps = hb.tune()
+    else:
+        aps = int(args.aps)
         hb.set_class_sizing(aps)
+    if args.hot_mib is not None:
+        hb.set_hot_nodes((int(args.hot_mib) << 20) >> log2m)
+    hot = hb.info()["hot_nodes"]
     cen = {k: torch.empty(n, dtype=torch.float64, device="cuda")
            for k in ("closeness", "harmonic", "lin", "reachable")}
 
@@ -291,8 +363,7 @@ def run_ours(args, world, rank, local):
         hbl.hb_reset(hb._h, seed)
         steps = hbl.hb_run_to_fixpoint(hb._h)
         hbl.hb_get_centralities(hb._h, cen["closeness"], cen["harmonic"], cen["lin"], cen["reachable"])
-        info = hb.info()
-        return steps, info
+        return steps, hb.info()
 
     for k in range(args.warmup):
         one_run(wl["seed"] + k)
@@ -328,49 +399,81 @@ def run_ours(args, world, rank, local):
 
     # roofline of the gather kernel (events recorded by the library on this stream)
     peak, peak_kind = measured_peaks()
-    achieved = (kbytes / klaunch) / ((kms / klaunch) / 1e3) / 1e9 if klaunch else 0.0
+    ms_launch = kms / klaunch if klaunch else 0.0
+    bytes_launch = kbytes / klaunch if klaunch else 0.0
+    achieved = bytes_launch / (ms_launch / 1e3) / 1e9 if klaunch else 0.0
+    traffic = recorded_traffic(name)
+    dram = traffic / (ms_launch / 1e3) / 1e9 if traffic and ms_launch else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                "frac": achieved / peak, "traffic": traffic,
+                "dram_frac": dram / peak if dram else None,
+                "dram_over_algorithmic": traffic / bytes_launch if traffic and bytes_launch else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s", "kernel": "step_kernel (gather + union + estimator)",
-                "bytes_per_launch": kbytes / klaunch if klaunch else 0.0,
-                "ms_per_launch": kms / klaunch if klaunch else 0.0,
+                else "fallback 6.8 TB/s",
+                "kernel": "step_kernel (gather + union + estimator; both passes of the two-phase gather)",
+                "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
+                "launches_timed": klaunch,
                 # frontier iterations done by the pushed union (separate kernels)
                 "pushed_iterations": {"per_step": plaunch / args.steps,
                                       "ms_per_iteration": pms / plaunch if plaunch else 0.0,
                                       "GBps": pbytes / pms / 1e6 if pms else 0.0}}
+    if traffic is None:
+        roofline["traffic_note"] = recorded_traffic_note(name)
+    out = {
+        "value": value, "ms_per_step": ms_max / args.steps, "gpu_launches": launches,
+        "config": {"workload": wl["desc"], "n": n, "m": m, "log2m": log2m,
+                   "estimate": "fp32" if fp32 else "fp64", "accumulators": "fp64",
+                   "frontier": args.frontier, "arcs_per_slot": aps, "hot_nodes": hot,
+                   "gather_tuning": "autotuner" if args.aps == "tune" else "fixed",
+                   "iterations_to_fixpoint": steps_list,
+                   "arc_updates_per_step": arcs / args.steps,
+                   "time_to_fixpoint_ms": ms_max / args.steps,
+                   "l2": "inputs larger than L2 (no flush): counters 2 x %.0f MB, targets %.0f MB"
+                         % (n * (1 << log2m) / 1e6, m * 4 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline, "clocks": clk.summary(),
+    }
+    if with_e2e:
+        out["e2e"] = run_e2e(args, g, opts, wl, world, cen, aps, hot)
+    hb.close()
+    out["_graph"] = g
+    return out
 
-    # end to end through the public API: host CSR in pinned memory, results
-    # back to pinned host memory, handle created and destroyed every step
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(args, g, opts, wl, world, cen, aps)
+
+def run_ours(args, world, rank, local):
+    from paper_1308_2144_gb300 import build, hyperball as hbl
+    build.build()
+    hbl.load()
+    stream = torch.cuda.current_stream()
+    head = measure(args, args.workload, world, local, stream, not args.no_e2e)
+    g = head.pop("_graph")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(g.numpy(), log2m, wl["seed"])
+        cpu = cpu_oracle_sample(g.numpy(), WORKLOADS[args.workload]["log2m"], WORKLOADS[args.workload]["seed"])
+    del g
+    torch.cuda.empty_cache()
+    secondary = None
+    if args.secondary and args.secondary != args.workload:
+        sec = measure(args, args.secondary, world, local, stream, False)
+        sec.pop("_graph")
+        torch.cuda.empty_cache()
+        secondary = {"workload": sec["config"]["workload"], "value": sec["value"], "unit": UNIT,
+                     "ms_per_step": sec["ms_per_step"], "config": sec["config"], "roofline": sec["roofline"],
+                     "clocks": sec["clocks"]}
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        from paper_1308_2144_gb300 import bench_forms
+        forms = bench_forms.forms_summary()
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": n, "m": m, "log2m": log2m,
-                       "estimate": "fp32" if fp32 else "fp64", "accumulators": "fp64",
-                       "frontier": args.frontier, "arcs_per_slot": aps,
-                       "arcs_per_slot_source": "autotuner" if args.aps == "tune" else "fixed",
-                       "iterations_to_fixpoint": steps_list,
-                       "arc_updates_per_step": arcs / args.steps,
-                       "time_to_fixpoint_ms": ms_max / args.steps,
-                       "l2": "inputs larger than L2 (no flush): counters 2 x %.0f MB, targets %.0f MB"
-                             % (n * (1 << log2m) / 1e6, m * 4 / 1e6),
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "config": head["config"], "roofline": head["roofline"], "cpu_baseline": cpu,
+            "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
+            "secondary": secondary, "forms": forms,
         }
         print(json.dumps(line), flush=True)
-    hb.close()
 
 
 def trace_run(hb, seed, log2m):
@@ -392,10 +495,10 @@ def trace_run(hb, seed, log2m):
             break
 
 
-def run_e2e(args, g, opts, wl, world, cen, aps):
+def run_e2e(args, g, opts, wl, world, cen, aps, hot):
     """Same metric through the public API from host memory: pinned host CSR
-    in, handle created (upload + setup) with the class sizing chosen above
-    given at creation (hb_options.arcs_per_slot),
+    in, handle created (upload + setup) with the class sizing and hot range
+    chosen above given at creation (hb_options.arcs_per_slot, hot_nodes),
     run to the fixpoint, centralities back to pinned host memory, handle
     destroyed, every step; one untimed step first."""
     from paper_1308_2144_gb300 import hyperball as hbl
@@ -409,7 +512,7 @@ def run_e2e(args, g, opts, wl, world, cen, aps):
     opts_h.pop("profile")
 
     def one(seed):
-        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed, arcs_per_slot=aps))
+        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed, arcs_per_slot=aps, hot_nodes=hot))
         h.run()
         hbl.hb_get_centralities(h._h, outs_h["closeness"], outs_h["harmonic"], outs_h["lin"],
                                 outs_h["reachable"])
@@ -440,7 +543,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="enwiki")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="web")
+    ap.add_argument("--secondary", choices=sorted(WORKLOADS) + [""], default="enwiki",
+                    help="a second workload measured the same way and reported under 'secondary' "
+                         "('' for none)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the reduced batched and served measurement ('forms')")
+    ap.add_argument("--hot-mib", type=int, default=None,
+                    help="fix the two-phase gather's hot range (MiB of counters; 0 = one pass) "
+                         "instead of the autotuner's choice")
+    ap.add_argument("--ref-step-s", type=float, default=1.5,
+                    help="--impl reference: seconds of oracle work per step")
     ap.add_argument("--frontier", choices=["auto", "push", "pull", "off"], default="auto")
     ap.add_argument("--fp32", action="store_true", help="precision form (FP32 estimates)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -199,13 +199,14 @@ hb_status hb_reset(hb_graph *g, uint64_t seed);
  * candidates the powers of two from 1 to 128) by timing the first eight
  * iterations (or all, if the fixpoint comes sooner) with each candidate,
  * twice (ascending, then descending order; the faster time counts).  Then,
- * with that sizing and the same timing, the hot range of the two-phase
- * gather (hb_set_hot_nodes): one pass, or hot counters of 16, 32, 48, 64 or
- * 96 MiB, tried when the handle holds one run per row and its counters
- * exceed the device's L2 cache.  Finally the counters are re-initialised
- * with the handle's seed.  Results never depend on either choice.
- * *arcs_per_slot (may be NULL) receives the sizing; hb_get_info reports
- * both. */
+ * with the same timing, the hot range of the two-phase gather
+ * (hb_set_hot_nodes): one pass with that sizing, or hot counters of 32, 64,
+ * 96, 128 or 192 MiB, each with 1, 2 and 4 times that sizing (each pass
+ * gathers only part of every list), tried when the handle holds one run per
+ * row and its counters exceed the device's L2 cache.  Finally the counters
+ * are re-initialised with the handle's seed.  Results never depend on
+ * either choice.  *arcs_per_slot (may be NULL) receives the sizing;
+ * hb_get_info reports both. */
 hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
 
 /* Set the class sizing directly (a power of two from 1 to 128) and
@@ -444,6 +445,13 @@ typedef struct {
     uint32_t flags;           /* HB_FP32_ESTIMATE or 0 */
     int32_t max_steps;        /* per-request iteration cap */
     int64_t reserve_bytes;    /* device memory left free when admitting */
+    int64_t large_arcs;       /* a request on a graph of at least this many arcs is "large" */
+    int32_t large_slots;      /* large requests running at once, at most (0: no limit).  With a
+                                 limit, a large request at the head of the queue waits for a
+                                 large slot while the small requests behind it are admitted, so
+                                 large requests share the device only with small ones (they are
+                                 served first come, first served among themselves) and small
+                                 requests never queue behind a large one */
 } hb_server_options;
 
 typedef struct {
@@ -455,7 +463,7 @@ typedef struct {
 
 typedef struct hb_server hb_server;
 
-void hb_server_default_options(hb_server_options *opt);   /* 32 slots, 4 GiB reserve */
+void hb_server_default_options(hb_server_options *opt);   /* 32 slots, 4 GiB reserve, no large limit */
 hb_status hb_server_create(const hb_server_options *opt, hb_server **out);
 /* Add a graph to the pool (CSR copied to the device once) and prepare it
  * for each log2m listed (relabelling, reverse CSR, plans shared by all its

@@ -16,9 +16,11 @@ all-fixpoint for both, aggregate arc-updates/s, speedup.
 serve: a pool of R-MAT graphs (node counts log-uniform in [1e4, 2e7], edge
 factor 16), requests arriving as a Poisson stream (graph uniform from the
 pool, log2m 4 or 6, seed = request id).  The continuous-batching server
-(many slots) versus the same server with one slot (a FIFO one at a time),
-on the same arrival stream.  Prints one JSON line per server: p50/p99
-latency from arrival to results in host memory, and arc-updates/s.
+(many slots) with at most --large-slots requests on graphs of the pool's top
+quarter by arcs running at once, the same server without that limit, and
+the server with one slot (a FIFO one at a time), on the same arrival
+stream.  Prints one JSON line per server: p50/p99 latency from arrival to
+results in host memory, and arc-updates/s.
 
 runs: the paper's multiple runs (Sec. 5) on the encyclopedia-like graph
 (log2m 6): R runs with seeds 42..42+R-1, each to its fixpoint, then the
@@ -53,6 +55,10 @@ def _rmat(n, ef, seed):
 
 
 def batch_main(args):
+    print(json.dumps(batch_measure(args)), flush=True)
+
+
+def batch_measure(args) -> dict:
     rng = np.random.default_rng(args.seed)
     mix = []
     t0 = time.time()
@@ -95,17 +101,18 @@ def batch_main(args):
     for h in solos:
         h.close()
     bt, st = min(times), min(solo_times)
-    print(json.dumps({
+    return {
         "form": "batched", "graphs": args.graphs, "arcs_in_graphs": arcs_total,
         "batch_ms": round(1e3 * bt, 3), "batch_iterations": iters, "arc_updates": arcs,
         "batch_arc_updates_per_s": arcs / bt, "one_at_a_time_ms": round(1e3 * st, 3),
         "one_at_a_time_arc_updates_per_s": solo_arcs / st, "speedup": st / bt,
         "estimate": "fp32" if args.fp32 else "fp64", "generate_s": round(gen_s, 1),
-        "create_s": round(create_s, 1)}), flush=True)
+        "create_s": round(create_s, 1)}
 
 
-def serve_run(pool, args, slots, label):
-    srv = hbl.HyperBallServer(slots=slots, fp32=args.fp32, reserve_bytes=args.reserve_gb << 30)
+def serve_run(pool, args, slots, label, large_slots=0, large_arcs=None):
+    srv = hbl.HyperBallServer(slots=slots, fp32=args.fp32, reserve_bytes=args.reserve_gb << 30,
+                              large_slots=large_slots, large_arcs=large_arcs)
     gids = [srv.add_graph(g.offsets, g.targets, g.n, log2ms=(4, 6)) for g in pool]
     rng = np.random.default_rng(args.seed + 7)
     total = args.warm + args.seconds
@@ -162,7 +169,8 @@ def serve_run(pool, args, slots, label):
         if mask.any():
             by_size[key] = {"requests": int(mask.sum()), "p50_s": float(np.percentile(L[mask], 50)),
                             "p99_s": float(np.percentile(L[mask], 99))}
-    return {"form": "served", "server": label, "slots": slots, "rate_per_s": args.rate,
+    return {"form": "served", "server": label, "slots": slots, "large_slots": large_slots,
+            "large_arcs": large_arcs, "rate_per_s": args.rate,
             "requests": len(sel), "p50_latency_s": float(np.percentile(L, 50)),
             "p99_latency_s": float(np.percentile(L, 99)), "mean_latency_s": float(L.mean()),
             "latency_by_size": by_size,
@@ -171,7 +179,7 @@ def serve_run(pool, args, slots, label):
             "pool_arcs": int(sum(g.m for g in pool))}
 
 
-def serve_main(args):
+def serve_pool(args):
     rng = np.random.default_rng(args.seed)
     pool = []
     t0 = time.time()
@@ -180,11 +188,52 @@ def serve_main(args):
         pool.append(_rmat(n, 16, 5000 + i))
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
-    gen_s = time.time() - t0
-    for slots, label in ((args.slots, "continuous-batching"), (1, "fifo-one-at-a-time")):
-        r = serve_run(pool, args, slots, label)
+    return pool, time.time() - t0
+
+
+def serve_measure(args) -> list:
+    """On the same arrival stream over the same pool: the continuous-batching
+    server with at most one large request running (large: a graph in the
+    top quarter of the pool by arcs), the same server without that limit,
+    and the FIFO one-at-a-time server."""
+    pool, gen_s = serve_pool(args)
+    large = int(np.quantile([g.m for g in pool], 0.75))
+    out = []
+    for slots, label, ls in ((args.slots, "continuous-batching-size-aware", args.large_slots),
+                             (args.slots, "continuous-batching", 0), (1, "fifo-one-at-a-time", 0)):
+        r = serve_run(pool, args, slots, label, large_slots=ls, large_arcs=large if ls else None)
         r["generate_s"] = round(gen_s, 1)
+        out.append(r)
+    return out
+
+
+def serve_main(args):
+    for r in serve_measure(args):
         print(json.dumps(r), flush=True)
+
+
+def forms_summary(graphs=64, rate=200.0, seconds=8.0, warm=2.0, pool=16, fp32=False) -> dict:
+    """A reduced run of both forms for the benchmark line: a batch of
+    `graphs` graphs of the batched mix against one graph at a time, and
+    both servers at `rate` requests/s over a pool of `pool` graphs."""
+    ba = argparse.Namespace(graphs=graphs, max_n=2e6, repeat=3, seed=4, fp32=fp32)
+    sa = argparse.Namespace(pool=pool, max_n=2e7, rate=rate, seconds=seconds, warm=warm, slots=32,
+                            reserve_gb=8, seed=5, fp32=fp32, large_slots=1)
+    batched = batch_measure(ba)
+    served = serve_measure(sa)
+    cb, cb_plain, fifo = served
+    keep = ("requests", "p50_latency_s", "p99_latency_s", "arc_updates_per_s", "latency_by_size")
+    return {
+        "batched": {k: batched[k] for k in ("graphs", "arcs_in_graphs", "batch_ms", "one_at_a_time_ms",
+                                            "speedup", "batch_arc_updates_per_s", "estimate")},
+        "served": {"rate_per_s": rate, "seconds": seconds, "pool_graphs": pool,
+                   "continuous_batching": dict({k: cb[k] for k in keep}, large_slots=cb["large_slots"],
+                                               large_arcs=cb["large_arcs"]),
+                   "continuous_batching_no_large_limit": {k: cb_plain[k] for k in keep},
+                   "fifo_one_at_a_time": {k: fifo[k] for k in keep},
+                   "p50_ratio_fifo_over_batching": fifo["p50_latency_s"] / cb["p50_latency_s"],
+                   "p99_ratio_fifo_over_batching": fifo["p99_latency_s"] / cb["p99_latency_s"]},
+    }
 
 
 def runs_main(args):
@@ -298,6 +347,8 @@ def main():
     s.add_argument("--seconds", type=float, default=60.0)
     s.add_argument("--warm", type=float, default=10.0)
     s.add_argument("--slots", type=int, default=32)
+    s.add_argument("--large-slots", type=int, default=1,
+                   help="large requests running at once in the size-aware server")
     s.add_argument("--reserve-gb", type=int, default=8)
     s.add_argument("--seed", type=int, default=5)
     s.add_argument("--fp32", action="store_true")

@@ -962,16 +962,25 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     const int64_t row = (int64_t)1 << g->b;
     if (st == HB_OK && !g->lruns && g->n * row > (int64_t)l2) {
+        // each pass gathers part of every list, so each hot range is tried
+        // with the sizing above and with 2 and 4 times as many arcs per slot
         std::vector<uint32_t> cands{0u};
+        std::vector<int> cand_aps{best};
         for (int64_t mb : kTuneHotMiB) {
             const int64_t h = (mb << 20) / row;
-            if (h < g->n) cands.push_back((uint32_t)h);
+            if (h >= g->n) continue;
+            for (int f = 1; f <= 4; f *= 2)
+                if (best * f <= kTuneAps[sizeof(kTuneAps) / sizeof(kTuneAps[0]) - 1]) {
+                    cands.push_back((uint32_t)h);
+                    cand_aps.push_back(best * f);
+                }
         }
         const int nh = (int)cands.size();
         std::vector<float> hot_ms(nh, 1e30f);
         for (int pass = 0; pass < 2 * nh && st == HB_OK; ++pass) {
             const int ci = pass < nh ? pass : 2 * nh - 1 - pass;
-            st = apply_hot(g, cands[ci]);
+            if (g->y.aps != cand_aps[ci]) st = retune(g, cand_aps[ci]);
+            if (st == HB_OK) st = apply_hot(g, cands[ci]);
             if (st == HB_OK) st = init_state(g, seed);
             if (st != HB_OK) break;
             cudaEventRecord(e0, g->s);
@@ -983,11 +992,15 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
                 hot_ms[ci] = ms;
         }
         float bh = 1e30f;
+        int best_aps = best;
         for (int ci = 0; ci < nh; ++ci)
             if (hot_ms[ci] < bh) {
                 bh = hot_ms[ci];
                 best_hot = cands[ci];
+                best_aps = cand_aps[ci];
             }
+        best = best_aps;
+        if (st == HB_OK && g->y.aps != best) st = retune(g, best);
         if (st == HB_OK) st = apply_hot(g, best_hot);
     }
     cudaEventDestroy(e0);

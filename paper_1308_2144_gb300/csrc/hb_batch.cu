@@ -910,6 +910,7 @@ struct ServeReq {
     int64_t n = 0;
     double *dres = nullptr;   // device: closeness, harmonic, lin, reachable (n each)
     bool cancel = false;      // running: retire at the next iteration boundary
+    bool large = false;       // its graph has at least large_arcs arcs
 };
 
 struct PoolGraph {
@@ -1006,11 +1007,21 @@ void serve_loop(hb_server *S) {
         bool changed = false;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            // admission: FIFO, into free slots, while device memory allows
+            // admission: FIFO, into free slots, while device memory allows;
+            // with a large-request limit, large requests beyond it stay
+            // queued (in order) and the requests behind them go first
             bool trimmed = false;
+            int large_running = 0;
+            if (S->opt.large_slots > 0)
+                for (int q = 0; q < k; ++q)
+                    if (S->slot_req[q] >= 0 && S->reqs[S->slot_req[q]].large) ++large_running;
             for (int slot = 0; slot < k && !S->queue.empty(); ++slot) {
                 if (S->slot_req[slot] >= 0) continue;
-                const int64_t id = S->queue.front();
+                auto qit = S->queue.begin();
+                if (S->opt.large_slots > 0 && large_running >= S->opt.large_slots)
+                    while (qit != S->queue.end() && S->reqs[*qit].large) ++qit;
+                if (qit == S->queue.end()) break;
+                const int64_t id = *qit;
                 ServeReq &r = S->reqs[id];
                 hb_graph *tmpl = S->graphs[r.graph].tmpl[r.log2m];
                 // admission by device memory: free memory plus what the
@@ -1027,7 +1038,7 @@ void serve_loop(hb_server *S) {
                     (trimmed && !any_running && avail < need + S->opt.reserve_bytes)) {
                     // can never fit, or does not fit while none of the
                     // server's requests holds memory: refuse it
-                    S->queue.pop_front();
+                    qit = S->queue.erase(qit);
                     r.state = HB_REQ_FAILED;
                     r.err = HB_ERR_OOM;
                     r.t_done = S->now();
@@ -1057,7 +1068,7 @@ void serve_loop(hb_server *S) {
                     }
                     break;
                 }
-                S->queue.pop_front();
+                qit = S->queue.erase(qit);
                 lk.unlock();
                 hb_graph *inst = nullptr;
                 hb_status st = make_instance(tmpl, r.seed, b->s, &inst, S->pool, S->ctr_host);
@@ -1070,6 +1081,7 @@ void serve_loop(hb_server *S) {
                     --slot;
                     continue;
                 }
+                if (r.large) ++large_running;
                 r.inst = inst;
                 r.slot = slot;
                 r.state = HB_REQ_RUNNING;
@@ -1199,6 +1211,8 @@ void hb_server_default_options(hb_server_options *o) {
     o->flags = 0;
     o->max_steps = 1 << 16;
     o->reserve_bytes = (int64_t)4 << 30;
+    o->large_arcs = (int64_t)1 << 25;
+    o->large_slots = 0;
 }
 
 hb_status hb_server_create(const hb_server_options *opt, hb_server **out) {
@@ -1210,6 +1224,7 @@ hb_status hb_server_create(const hb_server_options *opt, hb_server **out) {
     if (o.slots < 1 || o.slots > kMaxBatch) return sfail(HB_ERR_INVALID, "slots must lie in [1, 4096]");
     if (o.max_steps <= 0) o.max_steps = 1 << 16;
     if (o.reserve_bytes < 0) o.reserve_bytes = 0;
+    if (o.large_slots < 0 || o.large_arcs < 0) return sfail(HB_ERR_INVALID, "large_slots and large_arcs must be >= 0");
     cudaFree(nullptr);
     hb_server *S = new hb_server();
     S->opt = o;
@@ -1303,6 +1318,7 @@ hb_status hb_server_submit(hb_server *S, int32_t graph_id, int32_t log2m, uint64
     r.graph = graph_id;
     r.log2m = log2m;
     r.seed = seed;
+    r.large = S->graphs[graph_id].m >= S->opt.large_arcs;
     r.t_submit = S->now();
     S->queue.push_back(id);
     *request_id = id;

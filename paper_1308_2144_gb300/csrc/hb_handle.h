@@ -98,7 +98,7 @@ constexpr int kTuneAps[] = {1, 2, 4, 8, 16, 32, 64, 128};
 constexpr int kTuneIters = 8;
 // Candidate sizes (MiB of counters) of the hot range of the two-phase
 // gather the autotuner tries, beside one pass.
-constexpr int64_t kTuneHotMiB[] = {16, 32, 48, 64, 96};
+constexpr int64_t kTuneHotMiB[] = {32, 64, 96, 128, 192};
 
 }  // namespace hb
 

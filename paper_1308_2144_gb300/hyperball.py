@@ -90,7 +90,7 @@ class Info(ctypes.Structure):
 
 class ServerOptions(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int32), ("flags", ctypes.c_uint32), ("max_steps", ctypes.c_int32),
-                ("reserve_bytes", ctypes.c_int64)]
+                ("reserve_bytes", ctypes.c_int64), ("large_arcs", ctypes.c_int64), ("large_slots", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -532,12 +532,16 @@ class HyperBallServer:
     """The serving form: a request loop with continuous batching over a
     pool of device-resident graphs (see hb_server_* in hyperball.h)."""
 
-    def __init__(self, slots=32, fp32=False, max_steps=1 << 16, reserve_bytes=4 << 30):
+    def __init__(self, slots=32, fp32=False, max_steps=1 << 16, reserve_bytes=4 << 30, large_slots=0,
+                 large_arcs=None):
         L = load()
         o = ServerOptions()
         L.hb_server_default_options(ctypes.byref(o))
         o.slots, o.flags, o.max_steps, o.reserve_bytes = int(slots), HB_FP32_ESTIMATE if fp32 else 0, \
             int(max_steps), int(reserve_bytes)
+        o.large_slots = int(large_slots)
+        if large_arcs is not None:
+            o.large_arcs = int(large_arcs)
         self._h = _vp()
         _check(L.hb_server_create(ctypes.byref(o), ctypes.byref(self._h)))
         self.sizes = []

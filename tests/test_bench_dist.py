@@ -67,3 +67,16 @@ def test_reference_arm_reports_the_oracle():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["n"] == 10_000
+
+
+def test_cpu_baseline_sample_reports_threads_model_and_one_thread():
+    """bench.py's cpu_baseline: the oracle on a prefix of the nodes with
+    every thread and with one, the core count, nproc and the CPU model."""
+    import bench
+    from paper_1308_2144_gb300 import graphs
+    off, tgt = graphs.plain_graph(n=10_000, seed=1).numpy()
+    cpu = bench.cpu_oracle_sample((off, tgt), 4, 42, budget_s=0.5, budget_one_s=0.2)
+    assert cpu["kind"] == "oracle" and cpu["value"] > 0 and cpu["cores"] >= 1
+    assert cpu["nproc"] == os.cpu_count() and isinstance(cpu["cpu_model"], str) and cpu["cpu_model"]
+    assert cpu["single_thread"]["cores"] == 1 and cpu["single_thread"]["value"] > 0
+    assert "of 10000 nodes" in cpu["sample"]

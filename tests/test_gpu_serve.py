@@ -151,3 +151,41 @@ def test_request_that_cannot_fit_is_refused():
     assert e.value.status == hbl.HB_ERR_OOM
     assert _state(srv, rid)[1] == hbl.HB_REQ_FAILED
     srv.close()
+
+
+def test_size_aware_admission_keeps_one_large_request_and_results():
+    """With large_slots = 1, at most one request on a large graph runs at a
+    time (their admit-to-done intervals never overlap), small requests
+    submitted behind a large one are admitted while it waits, and every
+    result equals the solo run bit for bit."""
+    pool = _pool()
+    large = pool[1].m                      # the scale-13 graph is "large"
+    srv = hbl.HyperBallServer(slots=6, reserve_bytes=0, large_slots=1, large_arcs=large)
+    gids = [srv.add_graph(g.offsets.cuda(), g.targets.cuda(), g.n, log2ms=(4, 6)) for g in pool]
+    order = [1, 1, 1, 0, 2, 1, 0, 2, 2, 1, 0]
+    jobs = [(gi, 4 + 2 * (r % 2), 500 + r, srv.submit(gids[gi], 4 + 2 * (r % 2), 500 + r))
+            for r, gi in enumerate(order)]
+    infos = []
+    for gi, b, seed, rid in jobs:
+        info = srv.wait(rid, timeout=120)
+        assert info["state"] == hbl.HB_REQ_DONE
+        res = srv.take(rid, pool[gi].n)
+        steps, solo = _solo(pool[gi], b, seed)
+        assert info["steps"] == steps
+        for key in solo:
+            assert np.array_equal(res[key], solo[key]), key
+        infos.append((gi, info))
+    spans = sorted((i["admit_s"], i["done_s"]) for gi, i in infos if gi == 1)
+    for (a0, d0), (a1, d1) in zip(spans, spans[1:]):
+        assert a1 >= d0 - 1e-6, (a0, d0, a1, d1)
+    # the small request submitted behind the first three large ones is
+    # admitted before the last of them
+    small_admit = infos[3][1]["admit_s"]
+    assert small_admit <= max(i["admit_s"] for gi, i in infos[:3])
+    srv.close()
+
+
+def test_server_rejects_negative_large_options():
+    with pytest.raises(hbl.HBError) as e:
+        hbl.HyperBallServer(slots=2, large_slots=-1)
+    assert e.value.status == hbl.HB_ERR_INVALID
