@@ -354,8 +354,8 @@ def measure(args, name, world, local, stream, with_e2e):
         aps = int(args.aps)
         hb.set_class_sizing(aps)
     if args.hot_mib is not None:
-        hb.set_hot_nodes((int(args.hot_mib) << 20) >> log2m)
-    hot = hb.info()["hot_nodes"]
+        hb.set_hot_nodes((int(args.hot_mib) << 20) >> log2m, args.hot_passes)
+    hot, hot_passes = hb.info()["hot_nodes"], hb.info()["hot_passes"]
     cen = {k: torch.empty(n, dtype=torch.float64, device="cuda")
            for k in ("closeness", "harmonic", "lin", "reachable")}
 
@@ -410,7 +410,7 @@ def measure(args, name, world, local, stream, with_e2e):
                 "dram_over_algorithmic": traffic / bytes_launch if traffic and bytes_launch else None,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
-                "kernel": "step_kernel (gather + union + estimator; both passes of the two-phase gather)",
+                "kernel": "step_kernel (gather + union + estimator; both launches of the two-phase gather)",
                 "bytes_per_launch": bytes_launch, "ms_per_launch": ms_launch,
                 "launches_timed": klaunch,
                 # frontier iterations done by the pushed union (separate kernels)
@@ -424,6 +424,7 @@ def measure(args, name, world, local, stream, with_e2e):
         "config": {"workload": wl["desc"], "n": n, "m": m, "log2m": log2m,
                    "estimate": "fp32" if fp32 else "fp64", "accumulators": "fp64",
                    "frontier": args.frontier, "arcs_per_slot": aps, "hot_nodes": hot,
+                   "hot_passes": hot_passes,
                    "gather_tuning": "autotuner" if args.aps == "tune" else "fixed",
                    "iterations_to_fixpoint": steps_list,
                    "arc_updates_per_step": arcs / args.steps,
@@ -434,7 +435,7 @@ def measure(args, name, world, local, stream, with_e2e):
         "roofline": roofline, "clocks": clk.summary(),
     }
     if with_e2e:
-        out["e2e"] = run_e2e(args, g, opts, wl, world, cen, aps, hot)
+        out["e2e"] = run_e2e(args, g, opts, wl, world, cen, aps, hot, hot_passes)
     hb.close()
     out["_graph"] = g
     return out
@@ -495,10 +496,11 @@ def trace_run(hb, seed, log2m):
             break
 
 
-def run_e2e(args, g, opts, wl, world, cen, aps, hot):
+def run_e2e(args, g, opts, wl, world, cen, aps, hot, hot_passes):
     """Same metric through the public API from host memory: pinned host CSR
     in, handle created (upload + setup) with the class sizing and hot range
-    chosen above given at creation (hb_options.arcs_per_slot, hot_nodes),
+    chosen above given at creation (hb_options.arcs_per_slot, hot_nodes,
+    hot_passes),
     run to the fixpoint, centralities back to pinned host memory, handle
     destroyed, every step; one untimed step first."""
     from paper_1308_2144_gb300 import hyperball as hbl
@@ -512,7 +514,8 @@ def run_e2e(args, g, opts, wl, world, cen, aps, hot):
     opts_h.pop("profile")
 
     def one(seed):
-        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed, arcs_per_slot=aps, hot_nodes=hot))
+        h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed, arcs_per_slot=aps, hot_nodes=hot,
+                                                   hot_passes=hot_passes))
         h.run()
         hbl.hb_get_centralities(h._h, outs_h["closeness"], outs_h["harmonic"], outs_h["lin"],
                                 outs_h["reachable"])
@@ -550,8 +553,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the reduced batched and served measurement ('forms')")
     ap.add_argument("--hot-mib", type=int, default=None,
-                    help="fix the two-phase gather's hot range (MiB of counters; 0 = one pass) "
-                         "instead of the autotuner's choice")
+                    help="fix the gather's hot range (MiB of counters; 0 = none) instead of the "
+                         "autotuner's choice")
+    ap.add_argument("--hot-passes", type=int, choices=[1, 2], default=1,
+                    help="with --hot-mib: one pass with L2 priorities (1) or the two-phase gather (2)")
     ap.add_argument("--ref-step-s", type=float, default=1.5,
                     help="--impl reference: seconds of oracle work per step")
     ap.add_argument("--frontier", choices=["auto", "push", "pull", "off"], default="auto")

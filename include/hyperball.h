@@ -83,9 +83,11 @@ typedef struct {
     int32_t arcs_per_slot; /* class sizing of the gather from creation (as hb_set_class_sizing:
                               a power of two from 1 to 128), for callers who know it from an
                               earlier hb_tune; 0 = the default, 16.  Results never depend on it. */
-    int32_t hot_nodes;   /* hot range of the two-phase gather from creation (as
-                            hb_set_hot_nodes), for callers who know it from an earlier
-                            hb_tune; 0 = one pass.  Results never depend on it. */
+    int32_t hot_nodes;   /* hot range of the gather from creation (as hb_set_hot_nodes),
+                            for callers who know it from an earlier hb_tune; 0 = none.
+                            Results never depend on it. */
+    int32_t hot_passes;  /* how the hot range is used: 1 (or 0) one pass with L2
+                            priorities, 2 the two-phase gather (as hb_set_hot_nodes) */
 } hb_options;
 
 typedef struct hb_graph hb_graph;   /* opaque handle */
@@ -110,8 +112,9 @@ typedef struct {
     double push_ms;              /* HB_PROFILE: their summed duration (push + per-node tail) */
     double push_bytes;           /* HB_PROFILE: their summed algorithmic bytes (see below) */
     int32_t arcs_per_slot;       /* the gather's class sizing (hb_set_class_sizing, hb_tune) */
-    int32_t hot_nodes;           /* hot range of the two-phase gather, 0 = one pass
-                                    (hb_set_hot_nodes, hb_tune) */
+    int32_t hot_nodes;           /* hot range of the gather, 0 = none (hb_set_hot_nodes,
+                                    hb_tune) */
+    int32_t hot_passes;          /* 1: one pass with L2 priorities; 2: the two-phase gather */
 } hb_info;
 
 /* Algorithmic bytes of one gather-kernel launch, counted from the nodes it
@@ -199,34 +202,40 @@ hb_status hb_reset(hb_graph *g, uint64_t seed);
  * candidates the powers of two from 1 to 128) by timing the first eight
  * iterations (or all, if the fixpoint comes sooner) with each candidate,
  * twice (ascending, then descending order; the faster time counts).  Then,
- * with the same timing, the hot range of the two-phase gather
- * (hb_set_hot_nodes): one pass with that sizing, or hot counters of 32, 64,
- * 96, 128 or 192 MiB, each with 1, 2 and 4 times that sizing (each pass
- * gathers only part of every list), tried when the handle holds one run per
- * row and its counters exceed the device's L2 cache.  Finally the counters
- * are re-initialised with the handle's seed.  Results never depend on
- * either choice.  *arcs_per_slot (may be NULL) receives the sizing;
- * hb_get_info reports both. */
+ * with the same timing, the hot range of the gather (hb_set_hot_nodes),
+ * tried when the handle holds one run per row and its counters exceed the
+ * device's L2 cache: none, one pass with L2 priorities for hot counters of
+ * 32, 64, 96 or 128 MiB with 1 and 2 times that sizing, or the two-phase
+ * gather for 64, 128 or 192 MiB with 1, 2 and 4 times that sizing (each
+ * pass gathers only part of every list).  Finally the counters are
+ * re-initialised with the handle's seed.  Results never depend on any of
+ * these choices.  *arcs_per_slot (may be NULL) receives the sizing;
+ * hb_get_info reports all three. */
 hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
 
 /* Set the class sizing directly (a power of two from 1 to 128) and
  * re-initialise. */
 hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot);
 
-/* The two-phase gather of dense iterations.  With hot_nodes > 0 (clipped to
- * n), each dense iteration reads its successors' counters in two passes:
- * first only arcs whose target is one of the nodes [0, hot_nodes) of the
- * handle's internal order, then the others.  The register-wise maximum does
- * not depend on the order in which counters are read, so results are
- * identical to one pass; what changes is that while the first pass runs,
- * the random reads fall on hot_nodes * p bytes of counters.  After the
- * degree relabelling the lowest ids are the nodes of highest out-degree,
- * and, on graphs whose in- and out-degrees go together (the R-MAT graphs
- * here), also the most gathered counters, which then stay in L2.  Costs a
- * second read of the targets and p bytes written and read per node.  0 (the
- * default) gathers in one pass; handles of several runs per row take only
- * 0 (HB_ERR_INVALID otherwise).  Takes effect at the next iteration. */
-hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes);
+/* The hot range of dense iterations' gather: the nodes [0, hot_nodes) of
+ * the handle's internal order (clipped to n).  After the degree relabelling
+ * the lowest ids are the nodes of highest out-degree, and, on graphs whose
+ * in- and out-degrees go together (the R-MAT graphs here), also the most
+ * gathered counters.  passes = 1: one pass that reads the hot counters with
+ * the normal L2 eviction priority and every other counter with evict-first,
+ * so that the cold counters, each read by one or two arcs per iteration,
+ * leave L2 before the hot ones.  passes = 2: the two-phase gather, each
+ * iteration reading its successors' counters in two launches, first the
+ * arcs whose target is hot, then the others (with the library's own copy of
+ * the targets every node's list is reordered hot targets first, once per
+ * hot range; with borrowed targets each pass tests every arc), so that
+ * while the first pass runs the random reads fall on hot_nodes * p bytes of
+ * counters; it costs p bytes written and read per node.  The register-wise
+ * maximum does not depend on the order or the cache policy of the reads, so
+ * results are identical in every case.  hot_nodes = 0 (the default) uses no
+ * hot range; handles of several runs per row take only 0 (HB_ERR_INVALID
+ * otherwise).  Takes effect at the next iteration. */
+hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes, int32_t passes);
 
 /* Node weights (Sec. 6).  The paper simulates an integer weight w(v) by
  * replicas: the ball of radius 0 around v holds w(v) distinct items, and

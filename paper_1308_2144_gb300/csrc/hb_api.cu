@@ -101,6 +101,7 @@ void default_opts(hb_options *o) {
     o->stream = nullptr;
     o->arcs_per_slot = 0;
     o->hot_nodes = 0;
+    o->hot_passes = 1;
 }
 
 // The class sizing an options block asks for (0: the default); false if it
@@ -120,15 +121,18 @@ uint32_t hot_window(const hb_graph *g, int64_t hot_nodes) {
     return (uint32_t)(hot_nodes < g->n ? hot_nodes : g->n);
 }
 
-// Put the two-phase gather's hot range in place: with hot > 0 and the
-// library's own copy of the targets, every node's list is reordered hot
-// targets first (once per hot range) and the passes split each list at
-// hcnt[v]; with the caller's borrowed targets each pass tests every arc.
-hb_status apply_hot(hb_graph *g, int64_t hot_nodes) {
+// Put the hot range of the gather in place.  One pass (passes = 1): the
+// gather reads counters [0, hot) with the normal L2 priority and the others
+// with evict-first.  Two passes: with the library's own copy of the
+// targets, every node's list is reordered hot targets first (once per hot
+// range) and the passes split each list at hcnt[v]; with the caller's
+// borrowed targets each pass tests every arc.
+hb_status apply_hot(hb_graph *g, int64_t hot_nodes, int passes) {
     const uint32_t hot = hot_window(g, hot_nodes);
     g->a.hot = hot;
+    g->a.two_pass = passes == 2 ? 1 : 0;
     g->a.hcnt = nullptr;
-    if (hot == 0 || !g->own_tgt) return HB_OK;
+    if (hot == 0 || passes != 2 || !g->own_tgt) return HB_OK;
     if (g->hcnt_hot != hot) {
         if (!g->hcnt) {
             g->hcnt = g->mem.alloc<int32_t>((size_t)(g->n > 0 ? g->n : 1));
@@ -503,6 +507,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     int aps = 0;
     if (!sizing_of(o, &aps)) return fail(HB_ERR_INVALID, "arcs_per_slot must be 0 or a power of two from 1 to 128");
     if (o.hot_nodes < 0) return fail(HB_ERR_INVALID, "hot_nodes must be >= 0");
+    if (o.hot_passes < 0 || o.hot_passes > 2) return fail(HB_ERR_INVALID, "hot_passes must be 0, 1 or 2");
     cudaError_t e = cudaFree(nullptr);   // make sure a context exists
     if (e != cudaSuccess) return cuda_fail(e, "CUDA context");
 
@@ -648,7 +653,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
         NvtxRange nv("setup");
         st = finish_setup(g);
     }
-    if (st == HB_OK && o.hot_nodes > 0) st = apply_hot(g, o.hot_nodes);
+    if (st == HB_OK && o.hot_nodes > 0) st = apply_hot(g, o.hot_nodes, o.hot_passes);
     if (g->indeg) M.release(g->indeg);
     g->indeg = nullptr;
     if (st == HB_OK) st = init_state(g, seed);
@@ -906,6 +911,7 @@ hb_status hb_get_info(hb_graph *g, hb_info *info) {
     info->push_bytes = g->push_bytes;
     info->arcs_per_slot = g->y.aps;
     info->hot_nodes = (int32_t)g->a.hot;
+    info->hot_passes = g->a.two_pass ? 2 : 1;
     return HB_OK;
 }
 
@@ -956,31 +962,32 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
     // then the hot range of the two-phase gather, with that sizing: one
     // pass, or hot counters filling each candidate share of L2 (single-run
     // handles whose counters do not fit in L2 alone)
-    uint32_t best_hot = g->a.hot;
     int dev = 0, l2 = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     const int64_t row = (int64_t)1 << g->b;
     if (st == HB_OK && !g->lruns && g->n * row > (int64_t)l2) {
-        // each pass gathers part of every list, so each hot range is tried
-        // with the sizing above and with 2 and 4 times as many arcs per slot
-        std::vector<uint32_t> cands{0u};
-        std::vector<int> cand_aps{best};
-        for (int64_t mb : kTuneHotMiB) {
+        // candidates: one pass without a hot range (the sizing above); one
+        // pass with L2 priorities, each hot range with 1 and 2 times the
+        // sizing; two passes, each hot range with 1, 2 and 4 times it (each
+        // pass gathers only part of every list)
+        struct Cand { uint32_t hot; int aps, passes; };
+        std::vector<Cand> cands{{0u, best, 1}};
+        const int aps_max = kTuneAps[sizeof(kTuneAps) / sizeof(kTuneAps[0]) - 1];
+        auto add = [&](int64_t mb, int passes) {
             const int64_t h = (mb << 20) / row;
-            if (h >= g->n) continue;
-            for (int f = 1; f <= 4; f *= 2)
-                if (best * f <= kTuneAps[sizeof(kTuneAps) / sizeof(kTuneAps[0]) - 1]) {
-                    cands.push_back((uint32_t)h);
-                    cand_aps.push_back(best * f);
-                }
-        }
+            if (h >= g->n) return;
+            for (int f = 1; f <= (passes == 1 ? 2 : 4); f *= 2)
+                if (best * f <= aps_max) cands.push_back({(uint32_t)h, best * f, passes});
+        };
+        for (int64_t mb : kTuneHintMiB) add(mb, 1);
+        for (int64_t mb : kTuneHotMiB) add(mb, 2);
         const int nh = (int)cands.size();
         std::vector<float> hot_ms(nh, 1e30f);
         for (int pass = 0; pass < 2 * nh && st == HB_OK; ++pass) {
             const int ci = pass < nh ? pass : 2 * nh - 1 - pass;
-            if (g->y.aps != cand_aps[ci]) st = retune(g, cand_aps[ci]);
-            if (st == HB_OK) st = apply_hot(g, cands[ci]);
+            if (g->y.aps != cands[ci].aps) st = retune(g, cands[ci].aps);
+            if (st == HB_OK) st = apply_hot(g, cands[ci].hot, cands[ci].passes);
             if (st == HB_OK) st = init_state(g, seed);
             if (st != HB_OK) break;
             cudaEventRecord(e0, g->s);
@@ -991,17 +998,12 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
                 cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < hot_ms[ci])
                 hot_ms[ci] = ms;
         }
-        float bh = 1e30f;
-        int best_aps = best;
-        for (int ci = 0; ci < nh; ++ci)
-            if (hot_ms[ci] < bh) {
-                bh = hot_ms[ci];
-                best_hot = cands[ci];
-                best_aps = cand_aps[ci];
-            }
-        best = best_aps;
+        int bi = 0;
+        for (int ci = 1; ci < nh; ++ci)
+            if (hot_ms[ci] < hot_ms[bi]) bi = ci;
+        best = cands[bi].aps;
         if (st == HB_OK && g->y.aps != best) st = retune(g, best);
-        if (st == HB_OK) st = apply_hot(g, best_hot);
+        if (st == HB_OK) st = apply_hot(g, cands[bi].hot, cands[bi].passes);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1011,13 +1013,14 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
     return st;
 }
 
-hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes) {
+hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes, int32_t passes) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
     if (hot_nodes < 0) return fail(HB_ERR_INVALID, "hot_nodes must be >= 0");
+    if (passes < 1 || passes > 2) return fail(HB_ERR_INVALID, "passes must be 1 or 2");
     if (g->lruns && hot_nodes > 0)
-        return fail(HB_ERR_INVALID, "handles of several runs per row gather in one pass");
-    return apply_hot(g, hot_nodes);
+        return fail(HB_ERR_INVALID, "handles of several runs per row take no hot range");
+    return apply_hot(g, hot_nodes, passes);
 }
 
 hb_status hb_reset(hb_graph *g, uint64_t seed) {
@@ -1374,7 +1377,7 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     }
     if (!ok) { fclose(f); delete g; return fail(HB_ERR_INVALID, "truncated checkpoint or no memory"); }
     hb_status st = finish_setup(g);
-    if (st == HB_OK && o.hot_nodes > 0) st = apply_hot(g, o.hot_nodes);
+    if (st == HB_OK && o.hot_nodes > 0) st = apply_hot(g, o.hot_nodes, o.hot_passes);
     if (st == HB_OK) st = init_state(g, h.seed);
     if (st != HB_OK) { fclose(f); delete g; return st; }
     // restore the state of iteration t: counters into both buffers

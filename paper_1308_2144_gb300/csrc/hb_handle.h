@@ -96,9 +96,10 @@ constexpr int kTuneAps[] = {1, 2, 4, 8, 16, 32, 64, 128};
 // The autotuner times each candidate over the first iterations (most of a
 // run's work: the dense ones), up to the fixpoint.
 constexpr int kTuneIters = 8;
-// Candidate sizes (MiB of counters) of the hot range of the two-phase
-// gather the autotuner tries, beside one pass.
-constexpr int64_t kTuneHotMiB[] = {32, 64, 96, 128, 192};
+// Candidate sizes (MiB of counters) of the hot range the autotuner tries:
+// for the one-pass gather with L2 priorities, and for the two-phase gather.
+constexpr int64_t kTuneHintMiB[] = {32, 64, 96, 128};
+constexpr int64_t kTuneHotMiB[] = {64, 128, 192};
 
 }  // namespace hb
 

@@ -158,10 +158,13 @@ struct StepArgs {
     int32_t lruns;                // log2 of the runs sharing each row (0: one run per row)
     const uint64_t *run_seeds;    // hash seed of each run of a row
     double sparse_frac;           // AUTO: push when the last push arcs <= sparse_frac * m
-    uint32_t hot;                 // > 0: dense iterations gather in two passes, arcs into
-                                  // counters [0, hot) first (the most gathered ones after the
-                                  // degree relabelling), then the others
+    uint32_t hot;                 // > 0: counters [0, hot) (the most gathered ones after the
+                                  // degree relabelling) get the treatment two_pass selects
     int32_t pass;                 // which launch of the two-phase gather this is (1 or 2)
+    int32_t two_pass;             // with hot > 0: 1 = the two-phase gather, 0 = one pass
+                                  // reading counters [0, hot) with the normal L2 priority and
+                                  // the others with evict-first
+    uint32_t hint;                // set by the launcher of the one-pass gather: hot
     const int32_t *hcnt;          // two-phase gather: every node's targets below hot come
                                   // first, hcnt[v] of them (null: each arc tested in both passes)
 };

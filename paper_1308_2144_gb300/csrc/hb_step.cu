@@ -14,6 +14,9 @@
 //   step_kernel     gather + register-wise max (union), changed test,
 //                   estimator and accumulators for changed nodes
 //   step_end        count the iteration, record convergence
+#include <map>
+#include <mutex>
+
 #include "hb_step_dev.cuh"
 
 namespace hb {
@@ -252,6 +255,19 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_MI
     step_body<LOG2P, F32, false>(a);
 }
 
+// The one-pass gather with L2 priorities: counters of nodes below a.hint
+// are read with the normal eviction priority, the others with evict-first.
+// Built for one block fewer per SM than step_kernel, so that the two cache
+// policies fit in registers without spilling.
+#ifndef HB_HINT_MIN_BLOCKS
+#define HB_HINT_MIN_BLOCKS 4
+#endif
+template <int LOG2P, bool F32>
+__global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_HINT_MIN_BLOCKS)
+    step_kernel_hint(StepArgs a) {
+    step_body<LOG2P, F32, false, false, true>(a);
+}
+
 // The same gather in two passes (a.pass = 1, then 2): dense iterations
 // first gather the arcs into the hot counters [0, a.hot), then the others.
 template <int LOG2P, bool F32>
@@ -295,8 +311,9 @@ __global__ void __launch_bounds__(kStepThreads) union_tail_kernel(StepArgs a) {
 // predecessor count and the ones with many predecessors.
 __global__ void __launch_bounds__(256) compact_changed_kernel(StepArgs a) {
     if (a.ctr->mode != 0) return;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.n; base += (int64_t)gridDim.x * blockDim.x)
-        compact_tile(a, a.ctr->t, base);
+    const int t = a.ctr->t;
+    for (int64_t base = (int64_t)blockIdx.x * 2048; base < a.n; base += (int64_t)gridDim.x * 2048)
+        compact_tile_wide(a, t, base);
 }
 
 // --------------------------------------------------------------- outputs --
@@ -351,7 +368,63 @@ __global__ void frontier_out_kernel(StepArgs a, const int32_t *inv, uint8_t *cha
 }
 
 template <bool F32>
-cudaError_t launch_step_t(const StepArgs &a, int log2m, int grid, cudaStream_t s) {
+const void *step_kernel_ptr(int log2m) {
+    switch (log2m) {
+#define HB_CASE(B) case B: return reinterpret_cast<const void *>(&step_kernel<B, F32>);
+        HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+        HB_CASE(12)
+#undef HB_CASE
+        default: return nullptr;
+    }
+}
+
+template <bool F32>
+const void *hint_kernel_ptr(int log2m) {
+    switch (log2m) {
+#define HB_CASE(B) case B: return reinterpret_cast<const void *>(&step_kernel_hint<B, F32>);
+        HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+        HB_CASE(12)
+#undef HB_CASE
+        default: return nullptr;
+    }
+}
+
+// Resident blocks per SM of a kernel, looked up once per kernel.
+int blocks_per_sm_of(const void *k) {
+    static std::mutex mu;
+    static std::map<const void *, int> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(k);
+    if (it != cache.end()) return it->second;
+    int blocks = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k, kStepThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        blocks = 4;
+    }
+    if (blocks < 1) blocks = 1;
+    cache[k] = blocks;
+    return blocks;
+}
+
+template <bool F32>
+cudaError_t launch_step_t(const StepArgs &a_in, int log2m, int grid, cudaStream_t s) {
+    StepArgs a = a_in;
+    if (a.hot > 0 && !a.two_pass) {
+        // one pass with L2 priorities: the grid of the hint kernel's own
+        // occupancy over the same SMs
+        a.hint = a.hot;
+        const int per = blocks_per_sm_of(step_kernel_ptr<F32>(log2m));
+        const int per_h = blocks_per_sm_of(hint_kernel_ptr<F32>(log2m));
+        const int g = (grid / per) * per_h;
+        switch (log2m) {
+#define HB_CASE(B) case B: step_kernel_hint<B, F32><<<g, kStepThreads, 0, s>>>(a); break;
+            HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+            HB_CASE(12)
+#undef HB_CASE
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     if (a.hot > 0) {
         // two launches: pass 1 (hot counters; dense iterations only), pass 2
         StepArgs a1 = a, a2 = a;
@@ -390,17 +463,6 @@ cudaError_t launch_union_tail_t(const StepArgs &a, int log2m, int grid, cudaStre
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-
-template <bool F32>
-const void *step_kernel_ptr(int log2m) {
-    switch (log2m) {
-#define HB_CASE(B) case B: return reinterpret_cast<const void *>(&step_kernel<B, F32>);
-        HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
-        HB_CASE(12)
-#undef HB_CASE
-        default: return nullptr;
-    }
 }
 
 }  // namespace
@@ -504,7 +566,7 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
                   : fp32    ? launch_step_t<true>(a, y.log2m, step_grid, s)
                             : launch_step_t<false>(a, y.log2m, step_grid, s);
     if (e != cudaSuccess) return e;
-    if (a.hot > 0 && !a.lruns) ++k;   // the two-phase gather's second launch
+    if (a.hot > 0 && a.two_pass && !a.lruns) ++k;   // the two-phase gather's second launch
     if (ev) cudaEventRecord(ev[1], s);
     if (a.push_union) {
         e = a.lruns ? launch_runs_tail(a, y.log2m, fp32, step_grid, s)
@@ -514,7 +576,7 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
         if (ev) cudaEventRecord(ev[3], s);
     }
     if (a.frontier != HB_FRONTIER_OFF) {
-        compact_changed_kernel<<<grid_for(a.n, 256), 256, 0, s>>>(a);
+        compact_changed_kernel<<<grid_for((a.n + 7) / 8, 256), 256, 0, s>>>(a);
         ++k;
     }
     step_end_kernel<<<1, 1, 0, s>>>(a);

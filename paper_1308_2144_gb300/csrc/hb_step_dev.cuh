@@ -75,6 +75,46 @@ __device__ __forceinline__ void mark_append(const StepArgs &a, int32_t u, int la
     if (lane == 0 && dd) atomicAdd(&a.ctr->arcs, dd);
 }
 
+// A successor's counter chunk.  HINT (the one-pass gather with L2
+// priorities): counters of nodes below `hint` (the most gathered ones
+// after the degree relabelling) are read with the normal L2 eviction
+// priority and all others with evict-first, so that the lines of the cold
+// counters, each read by one or two arcs per iteration, leave L2 before the
+// lines of the hot ones.
+// HB_HINT_COLD_NO_L1 builds also keep the cold lines out of L1.
+#ifndef HB_HINT_COLD_NO_L1
+#define HB_HINT_COLD_NO_L1 0
+#endif
+template <bool HINT>
+__device__ __forceinline__ uint4 ld_counter_h(const uint8_t *p, uint32_t w, uint32_t hint) {
+    if constexpr (HINT) {
+        uint64_t pn, pf;
+        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pn));
+        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pf));
+        uint4 r;
+#if HB_HINT_COLD_NO_L1
+        if (w < hint)
+            asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                : "l"(p), "l"(pn));
+        else
+            asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                : "l"(p), "l"(pf));
+#else
+        const uint64_t pol = w < hint ? pn : pf;
+        asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+            : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+            : "l"(p), "l"(pol));
+#endif
+        return r;
+    } else {
+        (void)w;
+        (void)hint;
+        return ld_counter(p);
+    }
+}
+
 // An arc's target, checked against [0, n) in debug builds (-1 if outside).
 __device__ __forceinline__ int32_t arc_target(const int32_t *p, int64_t n, unsigned long long *err) {
     const int32_t w = ld_stream(p);
@@ -93,13 +133,13 @@ __device__ __forceinline__ int32_t arc_target(const int32_t *p, int64_t n, unsig
 // builds check them here).  n and err serve the debug check only.  WIN:
 // only targets w with w - wlo < wspan (unsigned) are gathered, the others
 // are skipped (the two-phase gather below).
-template <int LOG2P, int UMAX, bool WIN = false>
+template <int LOG2P, int UMAX, bool WIN = false, bool HINT = false>
 __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
                                             const uint8_t *__restrict__ cur, int64_t e,
                                             int64_t eend, int logS, int cl,
                                             uint4 (&acc)[Cfg<LOG2P>::CPL], int64_t n,
                                             unsigned long long *err, uint32_t wlo = 0u,
-                                            uint32_t wspan = 0u) {
+                                            uint32_t wspan = 0u, uint32_t hint = 0xffffffffu) {
     using C = Cfg<LOG2P>;
     constexpr int U0 = C::CPL >= 8 ? 1 : (C::CPL == 4 ? 2 : (C::CPL == 2 ? 4 : HB_UNROLL));
     constexpr int U = U0 < UMAX ? U0 : UMAX;
@@ -119,11 +159,11 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
             for (int c = 0; c < C::CPL; ++c)
 #if HB_DEBUG
                 g[u][c] = (w[u] >= 0 && (!WIN || (uint32_t)w[u] - wlo < wspan))
-                              ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                              ? ld_counter_h<HINT>(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, (uint32_t)w[u], hint)
                               : make_uint4(0u, 0u, 0u, 0u);
 #else
                 g[u][c] = (!WIN || (uint32_t)w[u] - wlo < wspan)
-                              ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                              ? ld_counter_h<HINT>(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, (uint32_t)w[u], hint)
                               : make_uint4(0u, 0u, 0u, 0u);
 #endif
 #pragma unroll
@@ -142,7 +182,7 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c)
                 g[u][c] = (w[u] >= 0 && (!WIN || (uint32_t)w[u] - wlo < wspan))
-                              ? ld_counter(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16)
+                              ? ld_counter_h<HINT>(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, (uint32_t)w[u], hint)
                               : z;
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -536,7 +576,7 @@ __device__ __forceinline__ void fold_partial(const uint8_t *__restrict__ nxt, in
         acc[c] = vmax16(acc[c], __ldcs(reinterpret_cast<const uint4 *>(src + c * C::L * 16)));
 }
 
-template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false>
+template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false, bool HINT = false>
 __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t pos0,
                                            int64_t pos_end, int logS, const int32_t *list,
@@ -585,13 +625,17 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
             gather_range_staged<LOG2P, 64, WIN>(tile, a.tgt, a.m, cur, A0, A1, e0 + slot, e1, logS, cl, acc,
                                                 a.n, &a.ctr->err, wlo, wspan);
     } else if (logS == C::LOGSMAX)
-        gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
+        gather_arcs<LOG2P, 64, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
+                                    a.hint);
     else if (a.aps <= 2)
-        gather_arcs<LOG2P, 2, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
+        gather_arcs<LOG2P, 2, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
+                                   a.hint);
     else if (a.aps <= 4)
-        gather_arcs<LOG2P, 4, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
+        gather_arcs<LOG2P, 4, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
+                                   a.hint);
     else
-        gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan);
+        gather_arcs<LOG2P, 64, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
+                                    a.hint);
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
@@ -607,7 +651,7 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
 // One chunk of a heavy node, by a whole warp.  Each chunk leaves its
 // partial union in scratch; the last chunk to arrive combines them and
 // finishes the node.
-template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false>
+template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false, bool HINT = false>
 __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t it,
                                            const int32_t *owner, const int64_t *cstart,
@@ -644,8 +688,8 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
         gather_range_staged<LOG2P, 64, WIN>(tile, a.tgt, a.m, cur, e0, e1, e0 + slot, e1, C::LOGSMAX, cl, acc,
                                             a.n, &a.ctr->err, win.lo, win.span);
     else
-        gather_arcs<LOG2P, 64, WIN>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err, win.lo,
-                                    win.span);
+        gather_arcs<LOG2P, 64, WIN, HINT>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err, win.lo,
+                                    win.span, a.hint);
 #pragma unroll
     for (int o = C::L; o < 32; o <<= 1)
 #pragma unroll
@@ -891,7 +935,7 @@ __device__ __forceinline__ void union_tail_item(const StepArgs &a, int t, int64_
 // The gather kernel's body: every work item of the iteration's plan (heavy
 // chunks, then light items of each degree class), with the per-node tail
 // of one run per row or, WIDE, of several runs per row.
-template <int LOG2P, bool F32, bool WIDE, bool WIN = false>
+template <int LOG2P, bool F32, bool WIDE, bool WIN = false, bool HINT = false>
 __device__ __forceinline__ void step_body(const StepArgs &a) {
     using C = Cfg<LOG2P>;
     const Counters *ctr = a.ctr;
@@ -951,7 +995,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = gw; it < items; it += nw) {
         if (it < hch) {
-            heavy_item<LOG2P, F32, WIDE, WIN>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
+            heavy_item<LOG2P, F32, WIDE, WIN, HINT>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
                                               s_changed, rdist64, rdist32, s_pow2, win, tile);
         } else {
             const int64_t li = it - hch;
@@ -961,7 +1005,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
             for (int q = 1; q < C::NLIGHT; ++q)
                 if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
             const int64_t pos0 = seg0 + ((li - ibj) << j);
-            light_item<LOG2P, F32, WIDE, WIN>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
+            light_item<LOG2P, F32, WIDE, WIN, HINT>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
                                               clist, biglist, sparse, s_changed, rdist64, rdist32, s_pow2,
                                               prefetch && !WIDE, win, tile);
         }
@@ -1098,6 +1142,65 @@ __device__ __forceinline__ void compact_tile(const StepArgs &a, int t, int64_t b
     if (ch) clist[sbase + off + __popc(bc & lanemask_lt())] = (int32_t)v;
     if (big) biglist[bbase + offb + __popc(bb & lanemask_lt())] = (int32_t)v;
     if (threadIdx.x == 0 && spush) atomicAdd(&a.ctr->push_arcs, spush);
+    __syncthreads();
+}
+
+// The same compaction over the 2048 nodes from `base` (base a multiple of
+// 8), eight consecutive nodes per thread: one 8-byte load of their flags,
+// one block scan of the packed counts (changed nodes in the low half, nodes
+// with many predecessors in the high half) and one global atomic per list
+// per tile.  Called by one block of 256 threads.
+__device__ __forceinline__ void compact_tile_wide(const StepArgs &a, int t, int64_t base) {
+    int32_t *clist = a.clist[t & 1];
+    int32_t *biglist = a.biglist[t & 1];
+    __shared__ unsigned long long sbase, bbase;
+    const int lane = threadIdx.x & 31;
+    const int64_t v0 = base + 8 * (int64_t)threadIdx.x;
+    uint32_t flags = 0;   // bit i: node v0 + i changed
+    if (v0 + 8 <= a.n) {
+        const uint2 x = *reinterpret_cast<const uint2 *>(a.changed + v0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            flags |= (((x.x >> (8 * i)) & 0xffu) ? 1u : 0u) << i;
+            flags |= (((x.y >> (8 * i)) & 0xffu) ? 1u : 0u) << (4 + i);
+        }
+    } else {
+        for (int i = 0; i < 8; ++i)
+            if (v0 + i < a.n && a.changed[v0 + i]) flags |= 1u << i;
+    }
+    uint32_t bigs = 0;
+    unsigned long long ps = 0;
+    if (flags && a.has_reverse) {
+        int64_t r = a.roff[v0 + __ffs(flags) - 1];
+        for (int i = __ffs(flags) - 1; i < 8; ++i) {
+            const int64_t r1 = (v0 + i < a.n) ? a.roff[v0 + i + 1] : r;
+            if ((flags >> i) & 1u) {
+                const int64_t rd = r1 - r;
+                ps += (unsigned long long)rd;
+                if (rd > kBigRdeg) bigs |= 1u << i;
+            }
+            r = r1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) ps += __shfl_xor_sync(FULL, ps, o);
+    if (lane == 0 && ps) atomicAdd(&a.ctr->push_arcs, ps);
+    int64_t excl;
+    const int64_t packed = (int64_t)__popc(flags) + ((int64_t)__popc(bigs) << 32);
+    const int64_t tot = block_excl_scan(packed, excl);
+    if (threadIdx.x == 0) {
+        const unsigned long long nc = (unsigned long long)(tot & 0xffffffffLL);
+        const unsigned long long nb = (unsigned long long)(tot >> 32);
+        sbase = nc ? atomicAdd(&a.ctr->list_len, nc) : 0;
+        bbase = nb ? atomicAdd(&a.ctr->n_big, nb) : 0;
+    }
+    __syncthreads();
+    unsigned long long cpos = sbase + (unsigned long long)(excl & 0xffffffffLL);
+    unsigned long long bpos = bbase + (unsigned long long)(excl >> 32);
+    for (int i = 0; i < 8; ++i) {
+        if ((flags >> i) & 1u) clist[cpos++] = (int32_t)(v0 + i);
+        if ((bigs >> i) & 1u) biglist[bpos++] = (int32_t)(v0 + i);
+    }
     __syncthreads();
 }
 

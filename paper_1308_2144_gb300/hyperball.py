@@ -69,7 +69,7 @@ class HBNotConverged(HBError):
 class Options(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("frontier", ctypes.c_int32),
                 ("max_steps", ctypes.c_int32), ("stream", ctypes.c_void_p), ("arcs_per_slot", ctypes.c_int32),
-                ("hot_nodes", ctypes.c_int32)]
+                ("hot_nodes", ctypes.c_int32), ("hot_passes", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -82,7 +82,7 @@ class Info(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double), ("kernel_bytes", ctypes.c_double),
                 ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
                 ("push_bytes", ctypes.c_double), ("arcs_per_slot", ctypes.c_int32),
-                ("hot_nodes", ctypes.c_int32)]
+                ("hot_nodes", ctypes.c_int32), ("hot_passes", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -169,7 +169,7 @@ def load():
         L.hb_set_class_sizing.restype = st
         L.hb_set_class_sizing.argtypes = [_vp, ctypes.c_int32]
         L.hb_set_hot_nodes.restype = st
-        L.hb_set_hot_nodes.argtypes = [_vp, ctypes.c_int32]
+        L.hb_set_hot_nodes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
         L.hb_tune.restype = st
         L.hb_tune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
         L.hb_batch_tune.restype = st
@@ -277,7 +277,7 @@ def _stream_ptr(stream):
 
 def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
                  max_steps=1 << 20, stream=None, profile=False, pull_gather=False,
-                 neighbourhood=False, arcs_per_slot=0, hot_nodes=0) -> Options:
+                 neighbourhood=False, arcs_per_slot=0, hot_nodes=0, hot_passes=1) -> Options:
     o = Options()
     load().hb_default_options(ctypes.byref(o))
     o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
@@ -289,6 +289,7 @@ def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, fro
     o.stream = _stream_ptr(stream)
     o.arcs_per_slot = int(arcs_per_slot)
     o.hot_nodes = int(hot_nodes)
+    o.hot_passes = int(hot_passes)
     return o
 
 
@@ -693,10 +694,11 @@ class HyperBall:
     def set_class_sizing(self, arcs_per_slot: int):
         _check(load().hb_set_class_sizing(self._h, int(arcs_per_slot)))
 
-    def set_hot_nodes(self, hot_nodes: int):
-        """Hot range of the two-phase gather (0: one pass); results do not
+    def set_hot_nodes(self, hot_nodes: int, passes: int = 1):
+        """Hot range of the gather (0: none): one pass with L2 priorities
+        (passes=1) or the two-phase gather (passes=2); results do not
         depend on it."""
-        _check(load().hb_set_hot_nodes(self._h, int(hot_nodes)))
+        _check(load().hb_set_hot_nodes(self._h, int(hot_nodes), int(passes)))
 
     def set_weights(self, weights=None):
         """Node weights by replicas (Sec. 6); restarts the computation."""

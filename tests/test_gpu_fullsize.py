@@ -131,13 +131,14 @@ def web():
     return g
 
 
-@pytest.mark.parametrize("fp32,hot", [(False, None), (True, None), (True, "eighth")])
-def test_web_recipe_scale22_every_iteration(orc, fp32, hot):
+@pytest.mark.parametrize("fp32,passes", [(False, None), (True, None), (True, 1), (True, 2)])
+def test_web_recipe_scale22_every_iteration(orc, fp32, passes):
     """The web-like recipe at a size the oracle runs whole: R-MAT (0.57,
     0.19, 0.19, 0.05) at scale 22 (4,194,304 nodes), edge factor 16, labels
     permuted, transpose scanned, log2m 4, in bench.py's launch configuration
     (frontier AUTO, degree relabelling, the autotuner's class sizing and hot
-    range), or with the two-phase gather forced to a hot range of n/8.  At
+    range), or with a hot range of n/8 forced, in one pass with L2
+    priorities or in the two-phase gather.  At
     every iteration: registers and changed set bit-exact, the FP64
     accumulators within 1e-9 (FP32 estimates: within the bound of the
     precision form), and the iteration count exact."""
@@ -145,10 +146,10 @@ def test_web_recipe_scale22_every_iteration(orc, fp32, hot):
     off, tgt = g.numpy()
     n, b, seed = g.n, 4, 42
     hb = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=n, fp32=fp32)
-    if hot is None:
+    if passes is None:
         hb.tune()
     else:
-        hb.set_hot_nodes(n // 8)
+        hb.set_hot_nodes(n // 8, passes)
     c = orc.init(n, b, seed)
     s_ref, h_ref = np.zeros(n), np.zeros(n)
     assert np.array_equal(hb.registers(device="cpu").numpy(), c)
@@ -182,16 +183,17 @@ def test_web_recipe_scale22_every_iteration(orc, fp32, hot):
 
 
 def test_web_full_size_pushed_gathered_two_pass_agree(web):
-    """The full web-like graph, FP32 estimates: the pushed frontier (bench's
-    configuration), the gathered frontier and the two-phase gather (hot
-    range of 64 MiB of counters) agree bit for bit through to the fixpoint:
-    counters and changed sets at every iteration, then accumulators and
-    centralities."""
+    """The full web-like graph, FP32 estimates: the pushed frontier with the
+    one-pass gather with L2 priorities (hot range of 64 MiB of counters), and
+    the gathered frontier with the two-phase gather (the same range), agree
+    bit for bit through to the fixpoint: counters and changed sets at every
+    iteration, then accumulators and centralities."""
     g = web
     b, seed = 4, 42
     hp = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n, fp32=True)
     hg = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=seed, n=g.n, fp32=True, pull_gather=True)
-    hg.set_hot_nodes((64 << 20) >> b)
+    hp.set_hot_nodes((64 << 20) >> b, 1)
+    hg.set_hot_nodes((64 << 20) >> b, 2)
     t = 0
     while True:
         kp, kg = hp.step(), hg.step()
@@ -209,7 +211,7 @@ def test_web_full_size_pushed_gathered_two_pass_agree(web):
     cp, cg = hp.centralities(), hg.centralities()
     for key in cp:
         assert torch.equal(cp[key], cg[key]), key
-    assert hg.info()["hot_nodes"] == (64 << 20) >> b
+    assert hg.info()["hot_nodes"] == (64 << 20) >> b and hg.info()["hot_passes"] == 2
     hp.close()
     hg.close()
 

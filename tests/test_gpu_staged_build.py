@@ -31,7 +31,7 @@ CHILD = textwrap.dedent("""
     for b in (4, 6):
         off, tgt = _degree_boundary_graph(b)
         walk_parity(oracle, off, tgt, b, 5, frontier="off", arcs_per_slot=128)
-        walk_parity(oracle, off, tgt, b, 5, frontier="auto", hot_nodes=(off.size - 1) // 3)
+        walk_parity(oracle, off, tgt, b, 5, frontier="auto", hot_nodes=(off.size - 1) // 3, hot_passes=2)
     print("staged build ok")
 """)
 

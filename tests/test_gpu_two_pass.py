@@ -1,13 +1,14 @@
-"""The two-phase gather of dense iterations (hb_set_hot_nodes, hot_nodes
-option, hb_tune) against the oracle and against the one-pass gather.
+"""The hot range of the gather (hb_set_hot_nodes, the hot_nodes and
+hot_passes options, hb_tune) against the oracle and against the plain
+gather: one pass with L2 priorities (passes = 1) and the two-phase gather
+(passes = 2).
 
-The register-wise maximum does not depend on the order in which the
-successors' counters are read, so a gather split into arcs into the hot
-counters [0, hot) and the rest must give the oracle's counters bit for bit,
-and, with the same per-node tail, the same accumulators bit for bit as the
-one-pass gather.  Cases: every log2m, hot ranges from one node to beyond n,
-heavy (split) nodes, every class sizing, both precisions, every frontier
-policy, changing the range between iterations, and the autotuner."""
+The register-wise maximum does not depend on the order or the cache policy
+of the reads, so both must give the oracle's counters bit for bit and, with
+the same per-node tail, the same accumulators bit for bit as the plain
+gather.  Cases: every log2m, hot ranges from one node to beyond n, heavy
+(split) nodes, every class sizing, both precisions, every frontier policy,
+changing the range and the mode between iterations, and the autotuner."""
 import numpy as np
 import pytest
 import torch
@@ -28,28 +29,32 @@ def _lib():
     hbl.load()
 
 
+@pytest.mark.parametrize("passes", [1, 2])
 @pytest.mark.parametrize("b", list(range(4, 13)))
-def test_two_pass_every_log2m_against_oracle(orc, b):
+def test_hot_range_every_log2m_against_oracle(orc, b, passes):
     off, tgt = graphs.rmat_graph(scale=11, edge_factor=8, seed=60 + b).numpy()
     n = off.size - 1
-    walk_parity(orc, off, tgt, b, 700 + b, frontier="off", hot_nodes=n // 7)
+    walk_parity(orc, off, tgt, b, 700 + b, frontier="off", hot_nodes=n // 7, hot_passes=passes)
 
 
 @pytest.mark.parametrize("frontier,pull_gather", [("auto", False), ("auto", True), ("push", False),
                                                   ("pull", False), ("off", False)])
 @pytest.mark.parametrize("relabel", [True, False])
-def test_two_pass_frontier_policies(orc, frontier, pull_gather, relabel):
+@pytest.mark.parametrize("passes", [1, 2])
+def test_hot_range_frontier_policies(orc, frontier, pull_gather, relabel, passes):
     off, tgt = graphs.rmat_graph(scale=12, edge_factor=8, seed=21).numpy()
     walk_parity(orc, off, tgt, 5, 77, frontier=frontier, relabel=relabel, pull_gather=pull_gather,
-                hot_nodes=500)
+                hot_nodes=500, hot_passes=passes)
 
 
+@pytest.mark.parametrize("passes", [1, 2])
 @pytest.mark.parametrize("b", [4, 6, 9, 12])
-def test_two_pass_degree_class_boundaries(orc, b):
-    # heavy nodes split into chunks in both passes, every class boundary
+def test_hot_range_degree_class_boundaries(orc, b, passes):
+    # heavy nodes split into chunks (in both passes), every class boundary
     off, tgt = _degree_boundary_graph(b)
     n = off.size - 1
-    walk_parity(orc, off, tgt, b, 5, check_every_step=(b <= 6), frontier="off", hot_nodes=n // 3)
+    walk_parity(orc, off, tgt, b, 5, check_every_step=(b <= 6), frontier="off", hot_nodes=n // 3,
+                hot_passes=passes)
 
 
 def _run_all(h):
@@ -62,9 +67,10 @@ def _run_all(h):
     return ks, regs
 
 
+@pytest.mark.parametrize("passes", [1, 2])
 @pytest.mark.parametrize("fp32", [False, True])
 @pytest.mark.parametrize("b", [4, 6])
-def test_two_pass_equals_one_pass_bitwise(fp32, b):
+def test_hot_range_equals_plain_gather_bitwise(fp32, b, passes):
     """Counters at every iteration, accumulators and centralities bitwise
     equal to the one-pass gather, for hot ranges of 1 node, a third, n - 1,
     n and beyond n, on an R-MAT graph with split nodes."""
@@ -76,8 +82,8 @@ def test_two_pass_equals_one_pass_bitwise(fp32, b):
     ref.close()
     for hot in (1, n // 3, n - 1, n, 2 * n):
         h = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=11, n=n, fp32=fp32, frontier="off",
-                          hot_nodes=hot)
-        assert h.info()["hot_nodes"] == min(hot, n)
+                          hot_nodes=hot, hot_passes=passes)
+        assert h.info()["hot_nodes"] == min(hot, n) and h.info()["hot_passes"] == passes
         ks, regs = _run_all(h)
         assert ks == ks0, hot
         for x, y in zip(regs, regs0):
@@ -90,13 +96,14 @@ def test_two_pass_equals_one_pass_bitwise(fp32, b):
         h.close()
 
 
+@pytest.mark.parametrize("passes", [1, 2])
 @pytest.mark.parametrize("aps", [1, 4, 16, 128])
-def test_two_pass_every_class_sizing(aps):
+def test_hot_range_every_class_sizing(aps, passes):
     g = graphs.rmat_graph(scale=14, edge_factor=12, seed=4, device="cuda")
     ref = hbl.HyperBall(g.offsets, g.targets, log2m=4, seed=2, n=g.n, frontier="off", arcs_per_slot=aps)
     ks0, regs0 = _run_all(ref)
     h = hbl.HyperBall(g.offsets, g.targets, log2m=4, seed=2, n=g.n, frontier="off", arcs_per_slot=aps,
-                      hot_nodes=g.n // 5)
+                      hot_nodes=g.n // 5, hot_passes=passes)
     ks, regs = _run_all(h)
     assert ks == ks0
     assert all(torch.equal(x, y) for x, y in zip(regs, regs0))
@@ -114,9 +121,9 @@ def test_hot_range_changed_between_iterations(orc):
     c = orc.init(n, 5, 3)
     s, hm = np.zeros(n), np.zeros(n)
     t = 0
-    hots = [0, n // 2, 17, n, 0, n // 9]
+    hots = [(0, 1), (n // 2, 2), (17, 1), (n, 2), (0, 2), (n // 9, 1), (n // 3, 2)]
     while True:
-        h.set_hot_nodes(hots[t % len(hots)])
+        h.set_hot_nodes(*hots[t % len(hots)])
         c, _, k = orc.step(off, tgt, 5, t, c, s, hm)
         assert h.step() == k
         assert np.array_equal(h.registers().cpu().numpy(), c), t
@@ -134,6 +141,9 @@ def test_hot_range_rejected_where_it_does_not_apply():
     h = hbl.HyperBall(g.offsets, g.targets, log2m=4, seed=1, n=g.n)
     with pytest.raises(hbl.HBError) as e:
         h.set_hot_nodes(-1)
+    assert e.value.status == hbl.HB_ERR_INVALID
+    with pytest.raises(hbl.HBError) as e:
+        h.set_hot_nodes(10, 3)
     assert e.value.status == hbl.HB_ERR_INVALID
     h.close()
     with pytest.raises(hbl.HBError) as e:
@@ -156,7 +166,7 @@ def test_tuner_chooses_a_hot_range_and_keeps_results(orc):
     aps = h.tune()
     info = h.info()
     assert info["arcs_per_slot"] == aps and info["t"] == 0
-    assert 0 <= info["hot_nodes"] <= g.n
+    assert 0 <= info["hot_nodes"] <= g.n and info["hot_passes"] in (1, 2)
     ks, regs = _run_all(h)
     assert ks == ks0
     assert all(torch.equal(x, y) for x, y in zip(regs, regs0))
