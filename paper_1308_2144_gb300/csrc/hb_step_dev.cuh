@@ -78,12 +78,14 @@ __device__ __forceinline__ void mark_append(const StepArgs &a, int32_t u, int la
 // A successor's counter chunk.  HINT (the one-pass gather with L2
 // priorities): counters of nodes below `hint` (the most gathered ones
 // after the degree relabelling) are read with the normal L2 eviction
-// priority and all others with evict-first, so that the lines of the cold
-// counters, each read by one or two arcs per iteration, leave L2 before the
-// lines of the hot ones.
-// HB_HINT_COLD_NO_L1 builds also keep the cold lines out of L1.
+// priority and all others with evict-first and without allocating in L1,
+// so that the lines of the cold counters, each read by one or two arcs per
+// iteration, leave L2 before the lines of the hot ones and take no L1
+// space from them.
+// HB_HINT_COLD_NO_L1 = 0 builds let the cold lines allocate in L1 (one
+// load instruction with a per-lane policy instead of two predicated ones).
 #ifndef HB_HINT_COLD_NO_L1
-#define HB_HINT_COLD_NO_L1 0
+#define HB_HINT_COLD_NO_L1 1
 #endif
 template <bool HINT>
 __device__ __forceinline__ uint4 ld_counter_h(const uint8_t *p, uint32_t w, uint32_t hint) {
