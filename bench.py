@@ -446,6 +446,16 @@ def run_ours(args, world, rank, local):
     build.build()
     hbl.load()
     stream = torch.cuda.current_stream()
+    # L2 fetch granularity: a limit of this process's context, put back at the end
+    l2_prev = hbl.hb_set_l2_fetch_bytes(args.l2_fetch)
+    try:
+        _run_ours(args, world, rank, local, stream, l2_prev)
+    finally:
+        if args.l2_fetch and l2_prev:
+            hbl.hb_set_l2_fetch_bytes(l2_prev)
+
+
+def _run_ours(args, world, rank, local, stream, l2_prev):
     head = measure(args, args.workload, world, local, stream, not args.no_e2e)
     g = head.pop("_graph")
     cpu = None
@@ -474,6 +484,7 @@ def run_ours(args, world, rank, local):
             "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
             "secondary": secondary, "forms": forms,
         }
+        line["config"]["l2_fetch_bytes"] = args.l2_fetch or l2_prev
         print(json.dumps(line), flush=True)
 
 
@@ -513,19 +524,31 @@ def run_e2e(args, g, opts, wl, world, cen, aps, hot, hot_passes):
     opts_h = dict(opts)
     opts_h.pop("profile")
 
+    phases = {"create": [], "run": [], "results": [], "destroy": []}
+
     def one(seed):
+        # every call below returns once its device work is done
+        t_a = time.perf_counter()
         h = hbl.HyperBall(off_h, tgt_h, **dict(opts_h, seed=seed, arcs_per_slot=aps, hot_nodes=hot,
                                                    hot_passes=hot_passes))
+        t_b = time.perf_counter()
         h.run()
+        t_c = time.perf_counter()
         hbl.hb_get_centralities(h._h, outs_h["closeness"], outs_h["harmonic"], outs_h["lin"],
                                 outs_h["reachable"])
+        t_d = time.perf_counter()
         arcs = h.info()["total_arcs"]
         h.close()
+        t_e = time.perf_counter()
+        for k_, (x, y) in zip(phases, ((t_a, t_b), (t_b, t_c), (t_c, t_d), (t_d, t_e))):
+            phases[k_].append(1e3 * (y - x))
         return arcs
 
     # one untimed pass first, as for the device-resident steps: the first
     # handle of a process grows the library's memory pool
     one(wl["seed"] + 99)
+    for v in phases.values():
+        v.clear()
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
@@ -537,7 +560,8 @@ def run_e2e(args, g, opts, wl, world, cen, aps, hot, hot_passes):
     h2d = off_h.numel() * off_h.element_size() + tgt_h.numel() * tgt_h.element_size()
     d2h = 4 * n * 8
     return {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps}
+            "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s / e2e_steps,
+            "phase_ms_median": {k: round(statistics.median(v), 1) for k, v in phases.items() if v}}
 
 
 def main():
@@ -557,6 +581,8 @@ def main():
                          "autotuner's choice")
     ap.add_argument("--hot-passes", type=int, choices=[1, 2], default=1,
                     help="with --hot-mib: one pass with L2 priorities (1) or the two-phase gather (2)")
+    ap.add_argument("--l2-fetch", type=int, choices=[0, 32, 64, 128], default=128,
+                    help="L2 fetch granularity of this process's context while it runs (0: leave it)")
     ap.add_argument("--ref-step-s", type=float, default=1.5,
                     help="--impl reference: seconds of oracle work per step")
     ap.add_argument("--frontier", choices=["auto", "push", "pull", "off"], default="auto")

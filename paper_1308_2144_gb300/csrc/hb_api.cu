@@ -1,6 +1,7 @@
 // hb_api.cu -- the C ABI of include/hyperball.h: argument checks, device
 // memory, the create-time pipeline (upload, validate, transpose, degree
 // relabelling, reverse CSR, plans, init) and the host side of iterations.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -815,20 +816,72 @@ hb_status hb_get_centralities(hb_graph *g, double *closeness, double *harmonic, 
     NvtxRange nv("hb_get_centralities");
     const int64_t n = g->n;
     double *outs[4] = {closeness, harmonic, lin, reachable};
-    double *dev[4] = {nullptr, nullptr, nullptr, nullptr};
-    DevMem tmp = scratch(g);
+    bool host[4] = {false, false, false, false};
+    bool any_host = false;
     for (int k = 0; k < 4; ++k) {
-        if (!outs[k]) continue;
-        dev[k] = is_device_ptr(outs[k]) ? outs[k] : tmp.alloc<double>(n);
+        host[k] = outs[k] && !is_device_ptr(outs[k]);
+        any_host |= host[k];
     }
+    cudaError_t e = cudaSuccess;
+    if (!any_host) {
+        // device outputs: written in the caller's order by one launch
+        e = launch_finalize(g->a, current_regs(g), g->inv, g->fp32, 0, n, outs[0], outs[1], outs[2], outs[3],
+                            g->s);
+        if (n > 0) g->launches += 1;
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
+        if (e != cudaSuccess) return cuda_fail(e, "centralities");
+        return HB_OK;
+    }
+    // host outputs: chunks of nodes computed into two alternating staging
+    // buffers on the handle's stream and copied out on a second stream, so
+    // the copies of one chunk overlap the computation of the next
+    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 24);
+    DevMem tmp = scratch(g);
+    double *stage[4][2] = {};
+    for (int k = 0; k < 4; ++k)
+        if (host[k]) {
+            stage[k][0] = tmp.alloc<double>(chunk > 0 ? chunk : 1);
+            stage[k][1] = tmp.alloc<double>(chunk > 0 ? chunk : 1);
+        }
     if (tmp.err != cudaSuccess) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
-    cudaError_t e = launch_finalize(g->a, current_regs(g), g->perm, g->fp32, dev[0], dev[1], dev[2],
-                                    dev[3], g->s);
-    if (n > 0) g->launches += 1;
-    for (int k = 0; k < 4 && e == cudaSuccess; ++k)
-        if (outs[k] && dev[k] != outs[k]) e = to_caller(outs[k], dev[k], sizeof(double) * n, g->s);
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev_k[2] = {nullptr, nullptr}, ev_c[2] = {nullptr, nullptr};
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaEventCreateWithFlags(&ev_k[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_c[i], cudaEventDisableTiming);
+    }
+    for (int64_t c = 0, u0 = 0; u0 < n && e == cudaSuccess; ++c, u0 += chunk) {
+        const int slot = (int)(c & 1);
+        const int64_t cnt = std::min(chunk, n - u0);
+        if (c >= 2) e = cudaStreamWaitEvent(g->s, ev_c[slot], 0);   // the slot's last copies are done
+        double *dst[4];
+        for (int k = 0; k < 4; ++k) dst[k] = !outs[k] ? nullptr : host[k] ? stage[k][slot] : outs[k] + u0;
+        if (e == cudaSuccess)
+            e = launch_finalize(g->a, current_regs(g), g->inv, g->fp32, u0, cnt, dst[0], dst[1], dst[2], dst[3],
+                                g->s);
+        g->launches += 1;
+        if (e == cudaSuccess) e = cudaEventRecord(ev_k[slot], g->s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev_k[slot], 0);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+            if (host[k])
+                e = cudaMemcpyAsync(outs[k] + u0, stage[k][slot], sizeof(double) * cnt, cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_c[slot], cs);
+    }
+    // the staging buffers go back to the pool on the handle's stream once
+    // the copies that read them are done
+    if (cs && e == cudaSuccess && n > 0) e = cudaStreamWaitEvent(g->s, ev_c[((n - 1) / chunk) & 1], 0);
+    if (cs) {
+        const cudaError_t f = cudaStreamSynchronize(cs);
+        if (e == cudaSuccess) e = f;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
     tmp.free_all();
+    for (int i = 0; i < 2; ++i) {
+        if (ev_k[i]) cudaEventDestroy(ev_k[i]);
+        if (ev_c[i]) cudaEventDestroy(ev_c[i]);
+    }
+    if (cs) cudaStreamDestroy(cs);
     if (e != cudaSuccess) return cuda_fail(e, "centralities");
     return HB_OK;
 }
@@ -1425,6 +1478,20 @@ void hb_destroy(hb_graph *g) {
     if (g->s) cudaStreamSynchronize(g->s);
     else cudaDeviceSynchronize();
     delete g;
+}
+
+hb_status hb_set_l2_fetch_bytes(int32_t bytes, int32_t *previous) {
+    if (bytes != 0 && bytes != 32 && bytes != 64 && bytes != 128)
+        return fail(HB_ERR_INVALID, "the L2 fetch granularity must be 32, 64 or 128 bytes (0: unchanged)");
+    size_t cur = 0;
+    cudaError_t e = cudaDeviceGetLimit(&cur, cudaLimitMaxL2FetchGranularity);
+    if (e != cudaSuccess) return cuda_fail(e, "L2 fetch granularity");
+    if (previous) *previous = (int32_t)cur;
+    if (bytes) {
+        e = cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "L2 fetch granularity");
+    }
+    return HB_OK;
 }
 
 hb_status hb_trim_memory(void) {

@@ -469,8 +469,11 @@ cudaError_t launch_step_kernel(const StepArgs &a, int log2m, bool fp32, int grid
 // alpha_p of the estimator and the thread-local message of hb_last_error().
 double hll_alpha_of(int p);
 void set_last_error(const char *msg);
-cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_t *perm, bool fp32,
-                            double *closeness, double *harmonic, double *lin, double *reachable,
+// Centralities of the caller's nodes [u0, u0 + count) into out[k][0 ..
+// count) (any output may be null); inv maps a caller's node to its internal
+// index (null: the identity).
+cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_t *inv, bool fp32, int64_t u0,
+                            int64_t count, double *closeness, double *harmonic, double *lin, double *reachable,
                             cudaStream_t s);
 cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *inv, int64_t n, int P,
                                uint8_t *out, cudaStream_t s);

@@ -318,18 +318,23 @@ __global__ void __launch_bounds__(256) compact_changed_kernel(StepArgs a) {
 
 // --------------------------------------------------------------- outputs --
 
+// Centralities of the caller's nodes u0 .. u0+count-1, written to out[k][u -
+// u0] in the caller's order: each thread reads its node's row and
+// accumulators at the internal index inv[u] (scattered 32-byte reads) and
+// writes contiguously (scattered 8-byte writes would each rewrite a sector).
 template <bool F32>
-__global__ void finalize_kernel(StepArgs a, const uint8_t *regs, const int32_t *perm, double *closeness,
-                                double *harmonic, double *lin, double *reachable) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < a.n;
-         v += (int64_t)gridDim.x * blockDim.x) {
+__global__ void finalize_kernel(StepArgs a, const uint8_t *regs, const int32_t *inv, int64_t u0, int64_t count,
+                                double *closeness, double *harmonic, double *lin, double *reachable) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = u0 + i;
+        const int64_t v = inv ? (int64_t)inv[u] : u;
         double c[4];
         node_centralities<F32>(a, regs, v, c);
-        const int64_t o = perm ? (int64_t)perm[v] : v;
-        if (closeness) closeness[o] = c[0];
-        if (harmonic) harmonic[o] = c[1];
-        if (lin) lin[o] = c[2];
-        if (reachable) reachable[o] = c[3];
+        if (closeness) closeness[i] = c[0];
+        if (harmonic) harmonic[i] = c[1];
+        if (lin) lin[i] = c[2];
+        if (reachable) reachable[i] = c[3];
     }
 }
 
@@ -585,16 +590,16 @@ cudaError_t launch_iteration(const StepArgs &a, const Layout &y, bool fp32, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_t *perm, bool fp32,
-                            double *closeness, double *harmonic, double *lin, double *reachable,
+cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_t *inv, bool fp32, int64_t u0,
+                            int64_t count, double *closeness, double *harmonic, double *lin, double *reachable,
                             cudaStream_t s) {
-    if (a.n == 0) return cudaSuccess;
+    if (count <= 0) return cudaSuccess;
     if (fp32)
-        finalize_kernel<true><<<grid_for(a.n, 256), 256, 0, s>>>(a, regs, perm, closeness, harmonic,
-                                                                 lin, reachable);
+        finalize_kernel<true><<<grid_for(count, 256), 256, 0, s>>>(a, regs, inv, u0, count, closeness, harmonic,
+                                                                   lin, reachable);
     else
-        finalize_kernel<false><<<grid_for(a.n, 256), 256, 0, s>>>(a, regs, perm, closeness, harmonic,
-                                                                  lin, reachable);
+        finalize_kernel<false><<<grid_for(count, 256), 256, 0, s>>>(a, regs, inv, u0, count, closeness, harmonic,
+                                                                    lin, reachable);
     return cudaGetLastError();
 }
 

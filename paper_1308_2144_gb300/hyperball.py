@@ -51,7 +51,7 @@ EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
            "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
-           "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_set_hot_nodes", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
+           "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_set_hot_nodes", "hb_set_l2_fetch_bytes", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
            "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_cancel", "hb_server_take",
            "hb_server_stats", "hb_server_destroy"]
 
@@ -168,6 +168,8 @@ def load():
         L.hb_get_discounted.argtypes = [_vp, _vp]
         L.hb_set_class_sizing.restype = st
         L.hb_set_class_sizing.argtypes = [_vp, ctypes.c_int32]
+        L.hb_set_l2_fetch_bytes.restype = st
+        L.hb_set_l2_fetch_bytes.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.hb_set_hot_nodes.restype = st
         L.hb_set_hot_nodes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
         L.hb_tune.restype = st
@@ -368,6 +370,14 @@ def hb_get_neighbourhood(h) -> np.ndarray:
     out = np.zeros(k.value, dtype=np.float64)
     _check(load().hb_get_neighbourhood(h, _ptr(out), k.value, ctypes.byref(k)))
     return out
+
+
+def hb_set_l2_fetch_bytes(nbytes: int) -> int:
+    """Set the L2 fetch granularity of this process's context on the current
+    device (32, 64 or 128 bytes; 0 only reads it); returns the value before."""
+    prev = ctypes.c_int32()
+    _check(load().hb_set_l2_fetch_bytes(int(nbytes), ctypes.byref(prev)))
+    return int(prev.value)
 
 
 def hb_tune(h) -> int:

@@ -63,3 +63,23 @@ def test_state_beyond_device_memory_is_refused(orc):
     hb = hbl.HyperBall(*to_dev(g_off, g_tgt), log2m=5, seed=3, n=g_off.size - 1)
     assert hb.run() == orc.run(g_off, g_tgt, 5, 3).steps
     hb.close()
+
+
+def test_l2_fetch_granularity_is_set_read_and_restored():
+    """hb_set_l2_fetch_bytes: a limit of this process's context; set, read
+    back, refused outside 32/64/128, and put back."""
+    prev = hbl.hb_set_l2_fetch_bytes(0)
+    assert prev in (0, 32, 64, 128)
+    try:
+        hbl.hb_set_l2_fetch_bytes(128)
+        assert hbl.hb_set_l2_fetch_bytes(0) == 128
+        hbl.hb_set_l2_fetch_bytes(32)
+        assert hbl.hb_set_l2_fetch_bytes(0) == 32
+        with pytest.raises(hbl.HBError) as e:
+            hbl.hb_set_l2_fetch_bytes(48)
+        assert e.value.status == hbl.HB_ERR_INVALID
+        assert hbl.hb_set_l2_fetch_bytes(0) == 32
+    finally:
+        if prev:
+            hbl.hb_set_l2_fetch_bytes(prev)
+    assert hbl.hb_set_l2_fetch_bytes(0) == prev

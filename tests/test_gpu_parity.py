@@ -436,3 +436,25 @@ def test_pinned_host_outputs(orc, plain):
     d_mean, d_sd = runs.run_stats("harmonic")
     assert torch.equal(mean, d_mean.cpu()) and torch.equal(sd, d_sd.cpu())
     runs.close()
+
+
+def test_centralities_to_host_in_chunks_equal_device():
+    """More nodes than one staging chunk (2^24): centralities delivered to
+    host memory (pinned and pageable, chunk by chunk, copies overlapping the
+    next chunk's computation) equal those delivered to device memory bit for
+    bit, in the caller's node order, also with an output left out."""
+    n = (1 << 24) * 2 + 12345          # two full chunks and a ragged third
+    g = graphs.rmat_graph(scale=26, edge_factor=1, seed=3, n=n, device="cuda")
+    hb = hbl.HyperBall(g.offsets, g.targets, log2m=4, seed=8, n=g.n)
+    hb.run()
+    dev = hb.centralities()
+    pinned = {k: torch.empty(g.n, dtype=torch.float64).pin_memory() for k in dev}
+    pageable = {k: torch.empty(g.n, dtype=torch.float64) for k in dev}
+    for out in (pinned, pageable):
+        hbl.hb_get_centralities(hb._h, out["closeness"], out["harmonic"], out["lin"], out["reachable"])
+        for k in dev:
+            assert torch.equal(out[k], dev[k].cpu()), k
+    part = torch.full((g.n,), -1.0, dtype=torch.float64)
+    hbl.hb_get_centralities(hb._h, None, part, None, None)
+    assert torch.equal(part, dev["harmonic"].cpu())
+    hb.close()
