@@ -78,6 +78,13 @@ def _load(path: str):
     L.orc_step_ex.restype = ctypes.c_int64
     L.orc_step_ex.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int, ctypes.c_int32,
                               _u8p, _u8p, _f64p, _f64p, ctypes.c_double, _f64p, _u8p]
+    L.orc_pack6.restype = ctypes.c_int
+    L.orc_pack6.argtypes = [_u8p, ctypes.c_int, _u8p]
+    L.orc_unpack6.restype = None
+    L.orc_unpack6.argtypes = [_u8p, ctypes.c_int, _u8p]
+    L.orc_step_packed.restype = ctypes.c_int64
+    L.orc_step_packed.argtypes = [ctypes.c_int64, _i64p, _i32p, ctypes.c_int, ctypes.c_int32,
+                                  _u8p, _u8p, _f64p, _f64p, _u8p]
     L.orc_discount.restype = ctypes.c_double
     L.orc_discount.argtypes = [_f64p, ctypes.c_int32, ctypes.c_int64]
     L.orc_run_ex.restype = ctypes.c_int
@@ -215,6 +222,41 @@ def step(offsets, targets, b: int, t: int, cur: np.ndarray,
         k = lib().orc_step_ex(n, _p(off, _i64p), _p(tgt, _i32p), b, t, _p(cur, _u8p),
                               _p(nxt, _u8p), _p(sumd, _f64p), _p(harm, _f64p), float(fdist),
                               _p(disc, _f64p), _p(changed, _u8p))
+    return nxt, changed, int(k)
+
+
+def pack6(regs: np.ndarray, b: int) -> np.ndarray:
+    """Counters (rows of p registers) packed six bits per register (Sec. 4.1
+    register width): rows of 3p/4 bytes.  ValueError if a register > 63."""
+    regs = np.ascontiguousarray(regs, dtype=np.uint8).reshape(-1, 1 << b)
+    out = np.zeros((regs.shape[0], 3 * (1 << b) // 4), dtype=np.uint8)
+    for v in range(regs.shape[0]):
+        if lib().orc_pack6(_p(regs[v], _u8p), b, _p(out[v], _u8p)) != 0:
+            raise ValueError("a register does not fit six bits")
+    return out
+
+
+def unpack6(packed: np.ndarray, b: int) -> np.ndarray:
+    """The inverse of pack6."""
+    packed = np.ascontiguousarray(packed, dtype=np.uint8).reshape(-1, 3 * (1 << b) // 4)
+    out = np.zeros((packed.shape[0], 1 << b), dtype=np.uint8)
+    for v in range(packed.shape[0]):
+        lib().orc_unpack6(_p(packed[v], _u8p), b, _p(out[v], _u8p))
+    return out
+
+
+def step_packed(offsets, targets, b: int, t: int, cur: np.ndarray, sumd: np.ndarray, harm: np.ndarray):
+    """One Algorithm 2 iteration on packed counters (rows of 3p/4 bytes).
+    Returns (next, changed, n_changed)."""
+    off, tgt = _csr(offsets, targets)
+    n = off.size - 1
+    cur = np.ascontiguousarray(cur, dtype=np.uint8)
+    nxt = np.empty_like(cur)
+    changed = np.zeros(n, dtype=np.uint8)
+    k = lib().orc_step_packed(n, _p(off, _i64p), _p(tgt, _i32p), b, t, _p(cur, _u8p), _p(nxt, _u8p),
+                              _p(sumd, _f64p), _p(harm, _f64p), _p(changed, _u8p))
+    if k < 0:
+        raise ValueError("a register does not fit six bits")
     return nxt, changed, int(k)
 
 

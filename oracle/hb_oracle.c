@@ -41,7 +41,11 @@
  *     give back the unweighted counters exactly; a weight of 0 (outside the
  *     paper's 1..W) leaves the node's own counter empty;
  *   - discount (Sec. 7): f is given as a table, f(d) = table[d-1] for
- *     d = 1..len and 0 for longer distances.
+ *     d = 1..len and 0 for longer distances;
+ *   - packed registers (Sec. 4.1, register width): six bits per register,
+ *     register j at bits 6j .. 6j+5 of the counter's bit string, least
+ *     significant bit first; every register value (<= 64-b) fits, so the
+ *     packed counters are the unpacked ones exactly.
  */
 #include <math.h>
 #include <stdint.h>
@@ -135,6 +139,43 @@ double orc_size(const uint8_t *M, int b)
     return E;
 }
 
+/* ------------------------------------------------ packed registers -- */
+
+/* Sec. 4.1: a register needs only about log2 log2 n bits.  With the 64-bit
+ * hash, rho+ never exceeds 64-b <= 60 < 2^6, so six bits hold every
+ * register exactly (no clamping).  The packed counter is the bit string of
+ * 6p bits in which register j occupies bits 6j .. 6j+5 (least significant
+ * bit first), stored in 3p/4 bytes, bit i in bit i%8 of byte i/8.
+ * Returns -1, writing nothing useful, if a register does not fit. */
+int orc_pack6(const uint8_t *M, int b, uint8_t *out)
+{
+    int p = 1 << b;
+    memset(out, 0, (size_t)(3 * p / 4));
+    for (int j = 0; j < p; ++j) {
+        if (M[j] > 63) return -1;
+        for (int bit = 0; bit < 6; ++bit)
+            if ((M[j] >> bit) & 1) {
+                int i = 6 * j + bit;
+                out[i / 8] |= (uint8_t)(1u << (i % 8));
+            }
+    }
+    return 0;
+}
+
+/* The inverse of orc_pack6: register j from bits 6j .. 6j+5. */
+void orc_unpack6(const uint8_t *in, int b, uint8_t *M)
+{
+    int p = 1 << b;
+    for (int j = 0; j < p; ++j) {
+        uint8_t v = 0;
+        for (int bit = 0; bit < 6; ++bit) {
+            int i = 6 * j + bit;
+            v |= (uint8_t)(((in[i / 8] >> (i % 8)) & 1) << bit);
+        }
+        M[j] = v;
+    }
+}
+
 /* ----------------------------------------------------------- HyperBall -- */
 
 static int g_threads = 0;
@@ -175,6 +216,17 @@ void orc_init_weighted(int64_t n, int b, uint64_t seed, const int64_t *w, uint8_
     }
 }
 
+/* Sec. 5 (and Sec. 7): node v's counter grew by delta (in size) at loop
+ * index t, so delta nodes sit at distance t+1. */
+static void accumulate(int64_t v, int32_t t, double delta, double *sumd, double *harm,
+                       double fdist, double *disc)
+{
+    double dist = (double)(t + 1);
+    sumd[v] = sumd[v] + dist * delta;
+    harm[v] = harm[v] + delta / dist;
+    if (disc) disc[v] = disc[v] + fdist * delta;
+}
+
 /* One iteration of the do/until loop of Algorithm 2 at loop index t.
  * Reads only `cur` (c_t) and writes `next` (c_{t+1}): the update file of
  * the paper is applied after the whole scan.  For every node whose counter
@@ -210,15 +262,50 @@ int64_t orc_step_ex(int64_t n, const int64_t *offsets, const int32_t *targets,
         changed[v] = (uint8_t)ch;
         if (ch) {
             double delta = orc_size(a, b) - orc_size(cur + v * p, b);
-            double dist = (double)(t + 1);
-            sumd[v] = sumd[v] + dist * delta;
-            harm[v] = harm[v] + delta / dist;
-            if (disc) disc[v] = disc[v] + fdist * delta;
+            accumulate(v, t, delta, sumd, harm, fdist, disc);
             n_changed += 1;
         }
         memcpy(next + v * p, a, (size_t)p);                  /* write <v, a> */
     }
     return n_changed;
+}
+
+/* One iteration of Algorithm 2 on packed counters (orc_pack6 rows of
+ * 3p/4 bytes): each counter is unpacked where it is read, the union and
+ * the Sec. 5 accumulators are those of orc_step_ex, and the new counter is
+ * packed again.  Returns the number of changed nodes, or -1 if a register
+ * did not fit six bits. */
+int64_t orc_step_packed(int64_t n, const int64_t *offsets, const int32_t *targets,
+                        int b, int32_t t, const uint8_t *cur, uint8_t *next,
+                        double *sumd, double *harm, uint8_t *changed)
+{
+    int64_t p = (int64_t)1 << b;
+    int64_t row = 3 * p / 4;
+    int64_t n_changed = 0;
+    int bad = 0;
+#ifdef _OPENMP
+    int nt = orc_get_threads();
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : n_changed) reduction(| : bad) num_threads(nt)
+#endif
+    for (int64_t v = 0; v < n; ++v) {
+        uint8_t own[4096], a[4096], cw[4096];
+        orc_unpack6(cur + v * row, b, own);                  /* c[v] */
+        memcpy(a, own, (size_t)p);                           /* a <- c[v] */
+        for (int64_t e = offsets[v]; e < offsets[v + 1]; ++e) {
+            orc_unpack6(cur + (int64_t)targets[e] * row, b, cw);
+            for (int64_t i = 0; i < p; ++i)                  /* a <- union(c[w], a) */
+                if (cw[i] > a[i]) a[i] = cw[i];
+        }
+        int ch = memcmp(a, own, (size_t)p) != 0;
+        changed[v] = (uint8_t)ch;
+        if (ch) {
+            double delta = orc_size(a, b) - orc_size(own, b);
+            accumulate(v, t, delta, sumd, harm, 0.0, NULL);
+            n_changed += 1;
+        }
+        if (orc_pack6(a, b, next + v * row) != 0) bad = 1;  /* write <v, a> */
+    }
+    return bad ? -1 : n_changed;
 }
 
 /* The unweighted, undiscounted iteration. */
