@@ -67,6 +67,16 @@ typedef enum {
                                        counters along the reverse CSR (results are the same) */
 #define HB_NEIGHBOURHOOD      0x40u /* record the neighbourhood function N(t) after every iteration
                                        (hb_get_neighbourhood) */
+#define HB_PACKED_REGISTERS   0x80u /* hold each register in six bits, not a byte (Sec. 4.1: a
+                                       register needs about log2 log2 n bits; every value the
+                                       method produces, at most 64 - log2m, fits): a counter
+                                       takes 3p/4 bytes, 16 registers in 12 bytes, register j
+                                       at bits 6j .. 6j+5 of the counter read as one
+                                       little-endian bit string.  Results are identical to
+                                       byte registers.  Needs HB_FRONTIER_OFF; not with
+                                       hot_nodes, hb_set_hot_nodes, hb_set_weights, hb_save,
+                                       hb_create_runs, the batched or served forms
+                                       (HB_ERR_INVALID, or HB_ERR_STATE on a handle). */
 
 /* hb_options.frontier: how the nodes to recompute are chosen each step
  * (Sec. 5 / 5.1 modification tracking).  Results never depend on it. */
@@ -115,6 +125,7 @@ typedef struct {
     int32_t hot_nodes;           /* hot range of the gather, 0 = none (hb_set_hot_nodes,
                                     hb_tune) */
     int32_t hot_passes;          /* 1: one pass with L2 priorities; 2: the two-phase gather */
+    int32_t packed;              /* 1 if the counters are packed six bits per register */
 } hb_info;
 
 /* Algorithmic bytes of one gather-kernel launch, counted from the nodes it
@@ -132,7 +143,8 @@ typedef struct {
  *   + K * (5 + 3p)                list entry, pushed union, own counter,
  *                                 counter write, flag
  *   + C * (4 + 32 + 2e)           as above
- * In a pushed iteration last_arcs (the arc-updates) counts the P arcs. */
+ * In a pushed iteration last_arcs (the arc-updates) counts the P arcs.
+ * With HB_PACKED_REGISTERS a counter read or write counts 3p/4 bytes. */
 
 /* Fill *opt with the defaults: flags 0, HB_FRONTIER_AUTO, max_steps 1<<20,
  * stream NULL, arcs_per_slot 0. */

@@ -5,6 +5,7 @@ runs on the same GPU.
     python -m paper_1308_2144_gb300.bench_forms batch [--graphs 512]
     python -m paper_1308_2144_gb300.bench_forms serve [--rate 200 --seconds 60 --warm 10]
     python -m paper_1308_2144_gb300.bench_forms runs [--runs 16]
+    python -m paper_1308_2144_gb300.bench_forms packed [--graph enwiki --log2m 6]
 
 batch: independent R-MAT graphs (0.57, 0.19, 0.19, 0.05) with node counts
 log-uniform in [1e3, 2e6], edge factor uniform in 4..32, log2m uniform in
@@ -30,6 +31,17 @@ sharing one copy of the graph (hb_batch_create_runs), and the R runs one
 after the other on one handle (statistics of the R results with torch).
 Prints one JSON line: time of each, and arc-updates/s counted per run (the
 arcs each run scans, summed over the runs).
+
+packed: registers held in six bits (HB_PACKED_REGISTERS, Sec. 4.1 register
+width) against byte registers on one graph (encyclopedia-like, or web-like
+at scale 25 or 28, scanned as transposes): both with every node recomputed
+at every iteration (HB_FRONTIER_OFF, the packed form's policy), and byte
+registers with the default frontier policy for context.  Each arm runs
+--repeat times from t = 0 to its fixpoint (best time kept); every arm must
+end with the same accumulators, else the line says so.  Prints one JSON
+line: per arm the time to the fixpoint, iterations, arc-updates/s, the
+gather kernel's mean duration and algorithmic GB/s (CUDA events,
+HB_PROFILE), and the bytes of the counters.
 """
 from __future__ import annotations
 
@@ -331,6 +343,58 @@ def runs_main(args):
     print(json.dumps(line), flush=True)
 
 
+def packed_main(args):
+    if args.graph == "web":
+        g = graphs.web_graph(device="cuda")
+        desc = "web-like (R-MAT scale 28, 268,435,456 nodes, edge factor 16), transpose"
+    elif args.graph == "web25":
+        g = graphs.web_graph(scale=25, device="cuda", bucket_bits=3)
+        desc = "web-like at profiling size (R-MAT scale 25, 33,554,432 nodes, edge factor 16), transpose"
+    else:
+        g = graphs.enwiki_graph(device="cuda")
+        desc = "encyclopedia-like (R-MAT scale 23, 4,206,785 nodes), transpose"
+    b = args.log2m
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    arms = {"byte_off": dict(frontier="off"), "packed_off": dict(frontier="off", packed=True),
+            "byte_auto": dict(frontier="auto")}
+    line = {"form": "packed", "graph": desc, "n": g.n, "m": g.m, "log2m": b,
+            "estimate": "fp32" if args.fp32 else "fp64"}
+    ref_acc = None
+    identical = True
+    for name, opts in arms.items():
+        h = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=42, n=g.n, fp32=args.fp32, profile=True, **opts)
+        h.run()                                   # warm-up
+        best, info = float("inf"), None
+        for _ in range(args.repeat):
+            h.reset(42)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.run()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if dt < best:
+                best, info = dt, h.info()
+        acc = h.accumulators()
+        if ref_acc is None:
+            ref_acc = acc
+        else:
+            identical &= all(torch.equal(x, y) for x, y in zip(acc, ref_acc))
+        del acc
+        h.close()
+        torch.cuda.empty_cache()
+        line[f"{name}_ms"] = round(1e3 * best, 3)
+        line[f"{name}_iterations"] = info["t"]
+        line[f"{name}_arc_updates_per_s"] = info["total_arcs"] / best
+        if info["kernel_launches"]:
+            line[f"{name}_gather_ms"] = round(info["kernel_ms"] / info["kernel_launches"], 4)
+            line[f"{name}_gather_gbs"] = round(info["kernel_bytes"] / (1e6 * info["kernel_ms"]), 1)
+        line[f"{name}_counter_bytes"] = g.n * ((3 << b) // 4 if opts.get("packed") else 1 << b)
+    line["identical_accumulators"] = bool(identical)
+    line["packed_speedup_vs_byte_off"] = line["byte_off_ms"] / line["packed_off_ms"]
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -357,10 +421,15 @@ def main():
     r.add_argument("--graph", choices=["enwiki", "web", "web25"], default="enwiki")
     r.add_argument("--repeat", type=int, default=3)
     r.add_argument("--fp32", action="store_true")
+    k = sub.add_parser("packed")
+    k.add_argument("--graph", choices=["enwiki", "web", "web25"], default="enwiki")
+    k.add_argument("--log2m", type=int, default=6)
+    k.add_argument("--repeat", type=int, default=3)
+    k.add_argument("--fp32", action="store_true")
     args = ap.parse_args()
     build.build()
     hbl.load()
-    {"batch": batch_main, "serve": serve_main, "runs": runs_main}[args.cmd](args)
+    {"batch": batch_main, "serve": serve_main, "runs": runs_main, "packed": packed_main}[args.cmd](args)
 
 
 if __name__ == "__main__":

@@ -236,6 +236,7 @@ hb_status setup_shared(hb_graph *g) {
     a.roff = g->roff;
     a.rtgt = g->rtgt;
     a.has_reverse = want_reverse ? 1 : 0;
+    a.packed = g->packed ? 1 : 0;
     g->push_union = want_reverse && (g->opt.flags & HB_PULL_GATHER) == 0;
     a.push_union = g->push_union ? 1 : 0;
     a.plan_dense = M.alloc<Plan>(1);
@@ -310,7 +311,7 @@ size_t run_bytes(const hb_graph *g) {
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     size_t b = 0;
     const int64_t nr = n << g->lruns;   // (node, run) pairs
-    b += 2 * up((size_t)n * P);
+    b += 2 * up((size_t)n * row_bytes(g));
     b += 2 * up(sizeof(double) * nr);
     b += up((g->fp32 ? sizeof(float) : sizeof(double)) * nr);
     b += up((size_t)n);
@@ -334,8 +335,8 @@ hb_status setup_run(hb_graph *g) {
     size_t off = 0;
     auto take = [&](size_t bytes) { uint8_t *p = base + off; off += (bytes + 255) & ~(size_t)255; return p; };
     StepArgs &a = g->a;
-    a.regs[0] = take((size_t)n * P);
-    a.regs[1] = take((size_t)n * P);
+    a.regs[0] = take((size_t)n * row_bytes(g));
+    a.regs[1] = take((size_t)n * row_bytes(g));
     const int64_t nr = n << g->lruns;
     a.sumd = reinterpret_cast<double *>(take(sizeof(double) * nr));
     a.harm = reinterpret_cast<double *>(take(sizeof(double) * nr));
@@ -509,6 +510,12 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     if (!sizing_of(o, &aps)) return fail(HB_ERR_INVALID, "arcs_per_slot must be 0 or a power of two from 1 to 128");
     if (o.hot_nodes < 0) return fail(HB_ERR_INVALID, "hot_nodes must be >= 0");
     if (o.hot_passes < 0 || o.hot_passes > 2) return fail(HB_ERR_INVALID, "hot_passes must be 0, 1 or 2");
+    if (o.flags & HB_PACKED_REGISTERS) {
+        if (o.frontier != HB_FRONTIER_OFF)
+            return fail(HB_ERR_INVALID, "HB_PACKED_REGISTERS needs the frontier policy HB_FRONTIER_OFF");
+        if (lruns) return fail(HB_ERR_INVALID, "HB_PACKED_REGISTERS is for handles of one run");
+        if (o.hot_nodes) return fail(HB_ERR_INVALID, "HB_PACKED_REGISTERS takes no hot range");
+    }
     cudaError_t e = cudaFree(nullptr);   // make sure a context exists
     if (e != cudaSuccess) return cuda_fail(e, "CUDA context");
 
@@ -525,6 +532,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     g->relabel = (o.flags & HB_NO_RELABEL) == 0;
     g->profile = (o.flags & HB_PROFILE) != 0;
     g->track_nf = (o.flags & HB_NEIGHBOURHOOD) != 0;
+    g->packed = (o.flags & HB_PACKED_REGISTERS) != 0;
     if (g->profile) {
         for (cudaEvent_t &x : g->ev)
             if (cudaEventCreate(&x) != cudaSuccess) {
@@ -782,7 +790,7 @@ hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     } else if (g->profile) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, g->ev[0], g->ev[1]) == cudaSuccess) {
-            const double p = (double)(1 << g->b);
+            const double p = (double)row_bytes(g);   // bytes of a counter
             const double esz = g->fp32 ? 4.0 : 8.0;
             g->kernel_ms += ms;
             g->kernel_launches += 1;
@@ -917,7 +925,7 @@ hb_status hb_get_registers(hb_graph *g, uint8_t *out) {
     DevMem tmp = scratch(g);
     uint8_t *d = is_device_ptr(out) ? out : tmp.alloc<uint8_t>(bytes);
     if (!d) { tmp.free_all(); return fail(HB_ERR_OOM, "out of device memory"); }
-    cudaError_t e = launch_gather_rows(current_regs(g), g->inv, g->n, 1 << g->b, d, g->s);
+    cudaError_t e = launch_gather_rows(current_regs(g), g->inv, g->n, 1 << g->b, d, g->s, g->packed);
     if (e == cudaSuccess && d != out) e = to_caller(out, d, bytes, g->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
     tmp.free_all();
@@ -959,6 +967,7 @@ hb_status hb_get_info(hb_graph *g, hb_info *info) {
     info->kernel_launches = g->kernel_launches;
     info->kernel_ms = g->kernel_ms;
     info->kernel_bytes = g->kernel_bytes;
+    info->packed = g->packed ? 1 : 0;
     info->push_launches = g->push_launches;
     info->push_ms = g->push_ms;
     info->push_bytes = g->push_bytes;
@@ -1019,7 +1028,7 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
     const int64_t row = (int64_t)1 << g->b;
-    if (st == HB_OK && !g->lruns && g->n * row > (int64_t)l2) {
+    if (st == HB_OK && !g->lruns && !g->packed && g->n * row > (int64_t)l2) {
         // candidates: one pass without a hot range (the sizing above); one
         // pass with L2 priorities, each hot range with 1 and 2 times the
         // sizing; two passes, each hot range with 1, 2 and 4 times it (each
@@ -1073,6 +1082,8 @@ hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes, int32_t passes) {
     if (passes < 1 || passes > 2) return fail(HB_ERR_INVALID, "passes must be 1 or 2");
     if (g->lruns && hot_nodes > 0)
         return fail(HB_ERR_INVALID, "handles of several runs per row take no hot range");
+    if (g->packed && hot_nodes > 0)
+        return fail(HB_ERR_STATE, "handles with HB_PACKED_REGISTERS take no hot range");
     return apply_hot(g, hot_nodes, passes);
 }
 
@@ -1085,6 +1096,7 @@ hb_status hb_reset(hb_graph *g, uint64_t seed) {
 hb_status hb_set_weights(hb_graph *g, const int64_t *weights) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
+    if (g->packed) return fail(HB_ERR_STATE, "handles with HB_PACKED_REGISTERS take no node weights");
     DevMem &M = g->mem;
     if (!weights) {
         if (g->wfirst) M.release(g->wfirst);
@@ -1348,6 +1360,7 @@ hb_status hb_save(hb_graph *g, const char *path) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
     if (g->lruns) return fail(HB_ERR_STATE, "checkpoints need a handle of one run");
+    if (g->packed) return fail(HB_ERR_STATE, "checkpoints hold byte registers, not HB_PACKED_REGISTERS");
     if (!path) return fail(HB_ERR_INVALID, "path is NULL");
     FILE *f = fopen(path, "wb");
     if (!f) return fail(HB_ERR_INVALID, std::string("cannot open ") + path);
@@ -1405,6 +1418,10 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
     if (!sizing_of(o, &aps)) {
         fclose(f);
         return fail(HB_ERR_INVALID, "arcs_per_slot must be 0 or a power of two from 1 to 128");
+    }
+    if (o.flags & HB_PACKED_REGISTERS) {
+        fclose(f);
+        return fail(HB_ERR_INVALID, "checkpoints hold byte registers, not HB_PACKED_REGISTERS");
     }
     cudaFree(nullptr);
     hb_graph *g = new hb_graph();

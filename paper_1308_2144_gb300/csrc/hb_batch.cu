@@ -606,6 +606,7 @@ hb_status new_batch(int k, const hb_options *opt, hb_options *o, hb_batch **out)
     if (o->max_steps <= 0) o->max_steps = 1 << 20;
     if (o->frontier == HB_FRONTIER_PULL) o->frontier = HB_FRONTIER_AUTO;
     o->flags &= ~(uint32_t)HB_PROFILE;
+    if (o->flags & HB_PACKED_REGISTERS) return bfail(HB_ERR_INVALID, "batches hold byte registers, not HB_PACKED_REGISTERS");
     hb_batch *b = new hb_batch();
     b->k = k;
     b->fp32 = (o->flags & HB_FP32_ESTIMATE) != 0;
@@ -1225,6 +1226,7 @@ hb_status hb_server_create(const hb_server_options *opt, hb_server **out) {
     if (o.max_steps <= 0) o.max_steps = 1 << 16;
     if (o.reserve_bytes < 0) o.reserve_bytes = 0;
     if (o.large_slots < 0 || o.large_arcs < 0) return sfail(HB_ERR_INVALID, "large_slots and large_arcs must be >= 0");
+    if (o.flags & HB_PACKED_REGISTERS) return sfail(HB_ERR_INVALID, "servers hold byte registers, not HB_PACKED_REGISTERS");
     cudaFree(nullptr);
     hb_server *S = new hb_server();
     S->opt = o;

@@ -133,6 +133,7 @@ struct hb_graph {
     uint64_t *run_seeds = nullptr; // their seeds (device)
     std::vector<int32_t> run_last; // per run: last iteration in which it changed (-1: none)
     bool track_nf = false;         // HB_NEIGHBOURHOOD: N(t) after every iteration
+    bool packed = false;           // HB_PACKED_REGISTERS: rows of 3p/4 bytes, six bits per register
     double *nf_part = nullptr;     // block partials of the estimate sum
     std::vector<double> nf;        // N(0), N(1), ... of the current run
     Counters *ctr = nullptr;
@@ -163,4 +164,11 @@ struct hb_graph {
         mem.free_all();
     }
 };
+
+// Bytes of one node's row of counters: p registers, one byte each, or six
+// bits each with HB_PACKED_REGISTERS.
+inline int64_t row_bytes(const hb_graph *g) {
+    const int64_t P = (int64_t)1 << g->b;
+    return g->packed ? 3 * P / 4 : P;
+}
 

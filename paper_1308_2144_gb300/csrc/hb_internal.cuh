@@ -165,6 +165,7 @@ struct StepArgs {
                                   // reading counters [0, hot) with the normal L2 priority and
                                   // the others with evict-first
     uint32_t hint;                // set by the launcher of the one-pass gather: hot
+    int32_t packed;               // counters packed six bits per register (rows of 3p/4 bytes)
     const int32_t *hcnt;          // two-phase gather: every node's targets below hot come
                                   // first, hcnt[v] of them (null: each arc tested in both passes)
 };
@@ -230,6 +231,41 @@ __device__ __forceinline__ uint4 shfl_xor16(uint4 a, int o) {
 // Counter loads: the read buffer does not change during a step.
 __device__ __forceinline__ uint4 ld_counter(const uint8_t *p) {
     return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+// Packed registers (Sec. 4.1 register width): six bits per register, a
+// chunk of 16 registers in 12 bytes (three words, 96 bits, register j at
+// bits 6j .. 6j+5, least significant first), so a counter of p registers
+// takes 3p/4 bytes.  Every register value (<= 64 - b <= 60) fits.  In
+// registers a chunk is unpacked to the usual 16 bytes, one per register.
+__device__ __forceinline__ uint32_t spread24(uint32_t x) {   // 4 fields of 6 bits -> 4 bytes
+    return (x & 0x3Fu) | ((x << 2) & 0x3F00u) | ((x << 4) & 0x3F0000u) | ((x << 6) & 0x3F000000u);
+}
+__device__ __forceinline__ uint32_t gather24(uint32_t y) {   // 4 bytes (each < 64) -> 24 bits
+    return (y & 0x3Fu) | ((y >> 2) & 0xFC0u) | ((y >> 4) & 0x3F000u) | ((y >> 6) & 0xFC0000u);
+}
+__device__ __forceinline__ uint4 unpack_chunk(uint32_t w0, uint32_t w1, uint32_t w2) {
+    return make_uint4(spread24(w0 & 0xFFFFFFu), spread24(__funnelshift_r(w0, w1, 24) & 0xFFFFFFu),
+                      spread24(__funnelshift_r(w1, w2, 16) & 0xFFFFFFu), spread24(w2 >> 8));
+}
+__device__ __forceinline__ void pack_chunk(uint4 c, uint32_t &w0, uint32_t &w1, uint32_t &w2) {
+    const uint32_t x0 = gather24(c.x), x1 = gather24(c.y), x2 = gather24(c.z), x3 = gather24(c.w);
+    w0 = x0 | (x1 << 24);
+    w1 = (x1 >> 8) | (x2 << 16);
+    w2 = (x2 >> 16) | (x3 << 8);
+}
+// Chunk k of the packed counter at row: 12 bytes from row + 12 k.
+__device__ __forceinline__ uint4 ld_packed(const uint8_t *row, int k) {
+    const uint32_t *q = reinterpret_cast<const uint32_t *>(row + 12 * k);
+    return unpack_chunk(__ldg(q), __ldg(q + 1), __ldg(q + 2));
+}
+__device__ __forceinline__ void st_packed(uint8_t *row, int k, uint4 c) {
+    uint32_t w0, w1, w2;
+    pack_chunk(c, w0, w1, w2);
+    uint32_t *q = reinterpret_cast<uint32_t *>(row + 12 * k);
+    __stcs(q, w0);
+    __stcs(q + 1, w1);
+    __stcs(q + 2, w2);
 }
 
 // Targets are streamed once per step.
@@ -337,8 +373,13 @@ __device__ __forceinline__ void node_centralities(const StepArgs &a, const uint8
     const int CH = P >> 4;
     uint32_t V = 0;
     unsigned long long S = 0;
-    const uint4 *row = reinterpret_cast<const uint4 *>(regs + v * P);
-    for (int c = 0; c < CH; ++c) chunk_sums(row[c], a.b, V, S);
+    if (a.packed) {
+        const uint8_t *prow = regs + v * (3 * P / 4);
+        for (int c = 0; c < CH; ++c) chunk_sums(ld_packed(prow, c), a.b, V, S);
+    } else {
+        const uint4 *row = reinterpret_cast<const uint4 *>(regs + v * P);
+        for (int c = 0; c < CH; ++c) chunk_sums(row[c], a.b, V, S);
+    }
     double r;
     if (F32) r = (double)estimate32(V, S, P, a.b, a.c32, a.thr_x, a.lc32);
     else r = estimate64(V, S, P, a.b, a.c64, a.thr_x, a.lc64);
@@ -475,8 +516,10 @@ void set_last_error(const char *msg);
 cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_t *inv, bool fp32, int64_t u0,
                             int64_t count, double *closeness, double *harmonic, double *lin, double *reachable,
                             cudaStream_t s);
+// Rows of p = P registers in the caller's order, one byte per register
+// (packed: the rows are held six bits per register).
 cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *inv, int64_t n, int P,
-                               uint8_t *out, cudaStream_t s);
+                               uint8_t *out, cudaStream_t s, bool packed = false);
 cudaError_t launch_gather_f64(const double *src, const int32_t *inv, int64_t n, double *out,
                               cudaStream_t s);
 cudaError_t launch_frontier_out(const StepArgs &a, const int32_t *inv, uint8_t *changed,

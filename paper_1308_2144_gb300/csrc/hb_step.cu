@@ -70,9 +70,9 @@ __global__ void __launch_bounds__(1024) estimate_total_kernel(const double *part
 
 // Algorithm 2, first loop: add(c[v], v) into an empty counter, in both
 // buffers (the second buffer then already holds c_0 for nodes that are
-// never recomputed).
+// never recomputed).  packed: 16-register chunks written as 12 bytes.
 __global__ void init_rows_kernel(uint8_t *r0, uint8_t *r1, const int32_t *perm, int64_t n, int b,
-                                 uint64_t seed) {
+                                 uint64_t seed, int packed) {
     const int CH = (1 << b) >> 4;
     const int64_t total = n * CH;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
@@ -85,8 +85,17 @@ __global__ void init_rows_kernel(uint8_t *r0, uint8_t *r1, const int32_t *perm, 
         uint32_t w[4] = {0u, 0u, 0u, 0u};
         if ((int)(idx >> 4) == c) w[(idx >> 2) & 3] = rho << (8 * (idx & 3));
         uint4 val = make_uint4(w[0], w[1], w[2], w[3]);
-        reinterpret_cast<uint4 *>(r0)[k] = val;
-        reinterpret_cast<uint4 *>(r1)[k] = val;
+        if (packed) {
+            uint32_t q0, q1, q2;
+            pack_chunk(val, q0, q1, q2);
+            uint32_t *d0 = reinterpret_cast<uint32_t *>(r0) + 3 * k;
+            uint32_t *d1 = reinterpret_cast<uint32_t *>(r1) + 3 * k;
+            d0[0] = q0; d0[1] = q1; d0[2] = q2;
+            d1[0] = q0; d1[1] = q1; d1[2] = q2;
+        } else {
+            reinterpret_cast<uint4 *>(r0)[k] = val;
+            reinterpret_cast<uint4 *>(r1)[k] = val;
+        }
     }
 }
 
@@ -268,6 +277,18 @@ __global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_HI
     step_body<LOG2P, F32, false, false, true>(a);
 }
 
+// Packed registers (six bits each, rows of 3p/4 bytes): the plain gather
+// on packed rows, dense iterations only.  Built for one block fewer per SM
+// than step_kernel: the unpacking of the arcs in flight needs the registers.
+#ifndef HB_PACKED_MIN_BLOCKS
+#define HB_PACKED_MIN_BLOCKS 4
+#endif
+template <int LOG2P, bool F32>
+__global__ void __launch_bounds__(kStepThreads, Cfg<LOG2P>::CPL >= 4 ? 3 : HB_PACKED_MIN_BLOCKS)
+    step_kernel_packed(StepArgs a) {
+    step_body<LOG2P, F32, false, false, false, true>(a);
+}
+
 // The same gather in two passes (a.pass = 1, then 2): dense iterations
 // first gather the arcs into the hot counters [0, a.hot), then the others.
 template <int LOG2P, bool F32>
@@ -338,15 +359,18 @@ __global__ void finalize_kernel(StepArgs a, const uint8_t *regs, const int32_t *
     }
 }
 
+// Rows in the caller's order, one byte per register (packed rows are
+// unpacked on the way).
 __global__ void gather_rows_kernel(const uint8_t *regs, const int32_t *inv, int64_t n, int CH,
-                                   uint8_t *out) {
+                                   uint8_t *out, int packed) {
     const int64_t total = n * CH;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t u = k / CH;
         const int c = (int)(k - u * CH);
         const int64_t v = inv ? (int64_t)inv[u] : u;
-        reinterpret_cast<uint4 *>(out)[k] = reinterpret_cast<const uint4 *>(regs)[v * CH + c];
+        reinterpret_cast<uint4 *>(out)[k] = packed ? ld_packed(regs + 12 * (v * CH + c), 0)
+                                                   : reinterpret_cast<const uint4 *>(regs)[v * CH + c];
     }
 }
 
@@ -394,6 +418,17 @@ const void *hint_kernel_ptr(int log2m) {
     }
 }
 
+template <bool F32>
+const void *packed_kernel_ptr(int log2m) {
+    switch (log2m) {
+#define HB_CASE(B) case B: return reinterpret_cast<const void *>(&step_kernel_packed<B, F32>);
+        HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+        HB_CASE(12)
+#undef HB_CASE
+        default: return nullptr;
+    }
+}
+
 // Resident blocks per SM of a kernel, looked up once per kernel.
 int blocks_per_sm_of(const void *k) {
     static std::mutex mu;
@@ -414,6 +449,20 @@ int blocks_per_sm_of(const void *k) {
 template <bool F32>
 cudaError_t launch_step_t(const StepArgs &a_in, int log2m, int grid, cudaStream_t s) {
     StepArgs a = a_in;
+    if (a.packed) {
+        // packed rows: the packed kernel's own occupancy over the same SMs
+        const int per = blocks_per_sm_of(step_kernel_ptr<F32>(log2m));
+        const int per_p = blocks_per_sm_of(packed_kernel_ptr<F32>(log2m));
+        const int g = (grid / per) * per_p;
+        switch (log2m) {
+#define HB_CASE(B) case B: step_kernel_packed<B, F32><<<g, kStepThreads, 0, s>>>(a); break;
+            HB_CASE(4) HB_CASE(5) HB_CASE(6) HB_CASE(7) HB_CASE(8) HB_CASE(9) HB_CASE(10) HB_CASE(11)
+            HB_CASE(12)
+#undef HB_CASE
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     if (a.hot > 0 && !a.two_pass) {
         // one pass with L2 priorities: the grid of the hint kernel's own
         // occupancy over the same SMs
@@ -515,7 +564,7 @@ cudaError_t launch_init(const StepArgs &a, const int32_t *perm, uint64_t seed, b
     }
     if (a.n > 0)
         init_rows_kernel<<<grid_for(a.n * CH, 256), 256, 0, s>>>(a.regs[0], a.regs[1], perm, a.n,
-                                                                a.b, seed);
+                                                                a.b, seed, a.packed);
     if (fp32) init_nodes_kernel<true><<<grid_for(a.n, 256), 256, 0, s>>>(a, perm, seed);
     else init_nodes_kernel<false><<<grid_for(a.n, 256), 256, 0, s>>>(a, perm, seed);
     return cudaGetLastError();
@@ -604,9 +653,9 @@ cudaError_t launch_finalize(const StepArgs &a, const uint8_t *regs, const int32_
 }
 
 cudaError_t launch_gather_rows(const uint8_t *regs, const int32_t *inv, int64_t n, int P,
-                               uint8_t *out, cudaStream_t s) {
+                               uint8_t *out, cudaStream_t s, bool packed) {
     const int CH = P >> 4;
-    if (n > 0) gather_rows_kernel<<<grid_for(n * CH, 256), 256, 0, s>>>(regs, inv, n, CH, out);
+    if (n > 0) gather_rows_kernel<<<grid_for(n * CH, 256), 256, 0, s>>>(regs, inv, n, CH, out, packed ? 1 : 0);
     return cudaGetLastError();
 }
 

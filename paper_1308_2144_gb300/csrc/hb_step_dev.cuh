@@ -134,8 +134,9 @@ __device__ __forceinline__ int32_t arc_target(const int32_t *p, int64_t n, unsig
 // run without bounds checks (targets were validated at creation; debug
 // builds check them here).  n and err serve the debug check only.  WIN:
 // only targets w with w - wlo < wspan (unsigned) are gathered, the others
-// are skipped (the two-phase gather below).
-template <int LOG2P, int UMAX, bool WIN = false, bool HINT = false>
+// are skipped (the two-phase gather below).  PK: counters packed six bits
+// per register, rows of 3p/4 bytes (chunk k of a row at byte 12 k).
+template <int LOG2P, int UMAX, bool WIN = false, bool HINT = false, bool PK = false>
 __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
                                             const uint8_t *__restrict__ cur, int64_t e,
                                             int64_t eend, int logS, int cl,
@@ -149,6 +150,13 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
     const int cnt = (int)((eend - e + (1LL << logS) - 1) >> logS);
     const int32_t *tp = tgt + e;
     const uint8_t *base = cur + cl * 16;
+    // chunk c of target w's counter (this lane's chunks)
+    auto chunk = [&](int32_t w, int c) -> uint4 {
+        if constexpr (PK)
+            return ld_packed(cur + (size_t)(uint32_t)w * (3 * C::P / 4), cl + c * C::L);
+        else
+            return ld_counter_h<HINT>(base + (size_t)(uint32_t)w * C::P + c * C::L * 16, (uint32_t)w, hint);
+    };
     int j = 0;
     for (; j + U <= cnt; j += U) {
         int32_t w[U];
@@ -161,11 +169,11 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
             for (int c = 0; c < C::CPL; ++c)
 #if HB_DEBUG
                 g[u][c] = (w[u] >= 0 && (!WIN || (uint32_t)w[u] - wlo < wspan))
-                              ? ld_counter_h<HINT>(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, (uint32_t)w[u], hint)
+                              ? chunk(w[u], c)
                               : make_uint4(0u, 0u, 0u, 0u);
 #else
                 g[u][c] = (!WIN || (uint32_t)w[u] - wlo < wspan)
-                              ? ld_counter_h<HINT>(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, (uint32_t)w[u], hint)
+                              ? chunk(w[u], c)
                               : make_uint4(0u, 0u, 0u, 0u);
 #endif
 #pragma unroll
@@ -184,7 +192,7 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
 #pragma unroll
             for (int c = 0; c < C::CPL; ++c)
                 g[u][c] = (w[u] >= 0 && (!WIN || (uint32_t)w[u] - wlo < wspan))
-                              ? ld_counter_h<HINT>(base + (size_t)(uint32_t)w[u] * C::P + c * C::L * 16, (uint32_t)w[u], hint)
+                              ? chunk(w[u], c)
                               : z;
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -306,8 +314,8 @@ __device__ __forceinline__ double discount_of(const StepArgs &a, int t) {
 // the same).  Folds in the node's own counter, writes it to the write
 // buffer, sets the changed flag, and for changed nodes evaluates size()
 // and updates the accumulators (Sec. 5), appending the node to the changed
-// list.
-template <int LOG2P, bool F32>
+// list.  PK: rows packed six bits per register.
+template <int LOG2P, bool F32, bool PK = false>
 __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *__restrict__ cur,
                                               uint8_t *__restrict__ nxt, int t, int64_t v,
                                               bool active, uint4 (&acc)[Cfg<LOG2P>::CPL], int cl,
@@ -322,7 +330,8 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
         const uint8_t *own = cur + v * C::P + cl * 16;
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) {
-            const uint4 o = ld_counter(own + c * C::L * 16);
+            const uint4 o = PK ? ld_packed(cur + v * (3 * C::P / 4), cl + c * C::L)
+                               : ld_counter(own + c * C::L * 16);
             const uint4 nv = vmax16(acc[c], o);
             diff |= ne16(nv, o);
             acc[c] = nv;
@@ -331,7 +340,10 @@ __device__ __forceinline__ void node_epilogue(const StepArgs &a, const uint8_t *
     const unsigned bal = __ballot_sync(FULL, diff);
     const unsigned tmask = logT == 5 ? FULL : (((1u << (1 << logT)) - 1u) << (team << logT));
     const bool ch = (bal & tmask) != 0u;
-    if (active && tl < C::L) {
+    if (PK && active && tl < C::L) {
+#pragma unroll
+        for (int c = 0; c < C::CPL; ++c) st_packed(nxt + v * (3 * C::P / 4), cl + c * C::L, acc[c]);
+    } else if (active && tl < C::L) {
         uint8_t *dst = nxt + v * C::P + cl * 16;
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) {
@@ -529,7 +541,7 @@ __device__ __forceinline__ void node_epilogue_wide(const StepArgs &a, const uint
 
 // The tail of one node: node_epilogue, or node_epilogue_wide for rows of
 // several runs.
-template <int LOG2P, bool F32, bool WIDE>
+template <int LOG2P, bool F32, bool WIDE, bool PK = false>
 __device__ __forceinline__ void node_tail(const StepArgs &a, const uint8_t *__restrict__ cur,
                                           uint8_t *__restrict__ nxt, int t, int64_t v, bool active,
                                           uint4 (&acc)[Cfg<LOG2P>::CPL], int cl, int tl, int team,
@@ -540,8 +552,8 @@ __device__ __forceinline__ void node_tail(const StepArgs &a, const uint8_t *__re
         node_epilogue_wide<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
                                        sparse, s_changed, rdist64, rdist32, pow2);
     else
-        node_epilogue<LOG2P, F32>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
-                                  sparse, s_changed, rdist64, rdist32, pow2);
+        node_epilogue<LOG2P, F32, PK>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
+                                      sparse, s_changed, rdist64, rdist32, pow2);
 }
 
 // The two-phase gather of a dense iteration (StepArgs::hot > 0): a first
@@ -578,7 +590,7 @@ __device__ __forceinline__ void fold_partial(const uint8_t *__restrict__ nxt, in
         acc[c] = vmax16(acc[c], __ldcs(reinterpret_cast<const uint4 *>(src + c * C::L * 16)));
 }
 
-template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false, bool HINT = false>
+template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false, bool HINT = false, bool PK = false>
 __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t pos0,
                                            int64_t pos_end, int logS, const int32_t *list,
@@ -627,17 +639,17 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
             gather_range_staged<LOG2P, 64, WIN>(tile, a.tgt, a.m, cur, A0, A1, e0 + slot, e1, logS, cl, acc,
                                                 a.n, &a.ctr->err, wlo, wspan);
     } else if (logS == C::LOGSMAX)
-        gather_arcs<LOG2P, 64, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
-                                    a.hint);
+        gather_arcs<LOG2P, 64, WIN, HINT, PK>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo,
+                                              wspan, a.hint);
     else if (a.aps <= 2)
-        gather_arcs<LOG2P, 2, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
-                                   a.hint);
+        gather_arcs<LOG2P, 2, WIN, HINT, PK>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo,
+                                             wspan, a.hint);
     else if (a.aps <= 4)
-        gather_arcs<LOG2P, 4, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
-                                   a.hint);
+        gather_arcs<LOG2P, 4, WIN, HINT, PK>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo,
+                                             wspan, a.hint);
     else
-        gather_arcs<LOG2P, 64, WIN, HINT>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo, wspan,
-                                    a.hint);
+        gather_arcs<LOG2P, 64, WIN, HINT, PK>(a.tgt, cur, e0 + slot, e1, logS, cl, acc, a.n, &a.ctr->err, wlo,
+                                              wspan, a.hint);
     for (int o = C::L; o < (1 << logT); o <<= 1)
 #pragma unroll
         for (int c = 0; c < C::CPL; ++c) acc[c] = vmax16(acc[c], shfl_xor16(acc[c], o));
@@ -646,14 +658,14 @@ __device__ __forceinline__ void light_item(const StepArgs &a, const uint8_t *__r
         return;
     }
     if (WIN && win.pass == 2 && active) fold_partial<LOG2P>(nxt, v, cl, acc);
-    node_tail<LOG2P, F32, WIDE>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
-                                sparse, s_changed, rdist64, rdist32, pow2);
+    node_tail<LOG2P, F32, WIDE, PK>(a, cur, nxt, t, v, active, acc, cl, tl, team, logT, clist, biglist,
+                                    sparse, s_changed, rdist64, rdist32, pow2);
 }
 
 // One chunk of a heavy node, by a whole warp.  Each chunk leaves its
 // partial union in scratch; the last chunk to arrive combines them and
-// finishes the node.
-template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false, bool HINT = false>
+// finishes the node.  The partial unions stay one byte per register.
+template <int LOG2P, bool F32, bool WIDE = false, bool WIN = false, bool HINT = false, bool PK = false>
 __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__restrict__ cur,
                                            uint8_t *__restrict__ nxt, int t, int64_t it,
                                            const int32_t *owner, const int64_t *cstart,
@@ -690,8 +702,8 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
         gather_range_staged<LOG2P, 64, WIN>(tile, a.tgt, a.m, cur, e0, e1, e0 + slot, e1, C::LOGSMAX, cl, acc,
                                             a.n, &a.ctr->err, win.lo, win.span);
     else
-        gather_arcs<LOG2P, 64, WIN, HINT>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err, win.lo,
-                                    win.span, a.hint);
+        gather_arcs<LOG2P, 64, WIN, HINT, PK>(a.tgt, cur, e0 + slot, e1, C::LOGSMAX, cl, acc, a.n, &a.ctr->err,
+                                              win.lo, win.span, a.hint);
 #pragma unroll
     for (int o = C::L; o < 32; o <<= 1)
 #pragma unroll
@@ -728,8 +740,8 @@ __device__ __forceinline__ void heavy_item(const StepArgs &a, const uint8_t *__r
         return;
     }
     if (WIN && win.pass == 2) fold_partial<LOG2P>(nxt, v, cl, acc);
-    node_tail<LOG2P, F32, WIDE>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
-                                s_changed, rdist64, rdist32, pow2);
+    node_tail<LOG2P, F32, WIDE, PK>(a, cur, nxt, t, v, true, acc, cl, lane, 0, 5, clist, biglist, sparse,
+                                    s_changed, rdist64, rdist32, pow2);
 }
 
 // Start of an iteration for one graph: shift this iteration's counters
@@ -936,8 +948,9 @@ __device__ __forceinline__ void union_tail_item(const StepArgs &a, int t, int64_
 
 // The gather kernel's body: every work item of the iteration's plan (heavy
 // chunks, then light items of each degree class), with the per-node tail
-// of one run per row or, WIDE, of several runs per row.
-template <int LOG2P, bool F32, bool WIDE, bool WIN = false, bool HINT = false>
+// of one run per row or, WIDE, of several runs per row.  PK: packed rows
+// (dense iterations only, no staging).
+template <int LOG2P, bool F32, bool WIDE, bool WIN = false, bool HINT = false, bool PK = false>
 __device__ __forceinline__ void step_body(const StepArgs &a) {
     using C = Cfg<LOG2P>;
     const Counters *ctr = a.ctr;
@@ -980,7 +993,7 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     __shared__ int4 s_tile[kWarpsPerBlock][kTile / 4];
     // targets staged in shared memory when a warp item's nodes are
     // consecutive ids (no node list) and the target array is 16-byte aligned
-    int32_t *tile = (HB_STAGE && list == nullptr && (reinterpret_cast<uintptr_t>(a.tgt) & 15) == 0)
+    int32_t *tile = (HB_STAGE && !PK && list == nullptr && (reinterpret_cast<uintptr_t>(a.tgt) & 15) == 0)
                         ? reinterpret_cast<int32_t *>(s_tile[threadIdx.x >> 5])
                         : nullptr;
     const double rdist64 = 1.0 / (double)(t + 1);
@@ -997,8 +1010,8 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t it = gw; it < items; it += nw) {
         if (it < hch) {
-            heavy_item<LOG2P, F32, WIDE, WIN, HINT>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist, sparse,
-                                              s_changed, rdist64, rdist32, s_pow2, win, tile);
+            heavy_item<LOG2P, F32, WIDE, WIN, HINT, PK>(a, cur, nxt, t, it, owner, cstart, list, clist, biglist,
+                                                        sparse, s_changed, rdist64, rdist32, s_pow2, win, tile);
         } else {
             const int64_t li = it - hch;
             int j = 0;
@@ -1007,9 +1020,9 @@ __device__ __forceinline__ void step_body(const StepArgs &a) {
             for (int q = 1; q < C::NLIGHT; ++q)
                 if (li >= ib[q]) { j = q; ibj = ib[q]; cntj = cnt[q]; seg0 = a.seg_begin[q + 1]; }
             const int64_t pos0 = seg0 + ((li - ibj) << j);
-            light_item<LOG2P, F32, WIDE, WIN, HINT>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
-                                              clist, biglist, sparse, s_changed, rdist64, rdist32, s_pow2,
-                                              prefetch && !WIDE, win, tile);
+            light_item<LOG2P, F32, WIDE, WIN, HINT, PK>(a, cur, nxt, t, pos0, seg0 + cntj, C::LOGSMAX - j, list,
+                                                        clist, biglist, sparse, s_changed, rdist64, rdist32,
+                                                        s_pow2, prefetch && !WIDE, win, tile);
         }
     }
     __syncthreads();

@@ -36,6 +36,7 @@ HB_NO_RELABEL = 0x8
 HB_PROFILE = 0x10
 HB_PULL_GATHER = 0x20
 HB_NEIGHBOURHOOD = 0x40
+HB_PACKED_REGISTERS = 0x80
 
 FRONTIER = {"auto": 0, "pull": 1, "push": 2, "off": 3}
 
@@ -82,7 +83,8 @@ class Info(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double), ("kernel_bytes", ctypes.c_double),
                 ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
                 ("push_bytes", ctypes.c_double), ("arcs_per_slot", ctypes.c_int32),
-                ("hot_nodes", ctypes.c_int32), ("hot_passes", ctypes.c_int32)]
+                ("hot_nodes", ctypes.c_int32), ("hot_passes", ctypes.c_int32),
+                ("packed", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -279,13 +281,13 @@ def _stream_ptr(stream):
 
 def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
                  max_steps=1 << 20, stream=None, profile=False, pull_gather=False,
-                 neighbourhood=False, arcs_per_slot=0, hot_nodes=0, hot_passes=1) -> Options:
+                 neighbourhood=False, arcs_per_slot=0, hot_nodes=0, hot_passes=1, packed=False) -> Options:
     o = Options()
     load().hb_default_options(ctypes.byref(o))
     o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
                | (HB_FP32_ESTIMATE if fp32 else 0) | (0 if relabel else HB_NO_RELABEL)
                | (HB_PROFILE if profile else 0) | (HB_PULL_GATHER if pull_gather else 0)
-               | (HB_NEIGHBOURHOOD if neighbourhood else 0))
+               | (HB_NEIGHBOURHOOD if neighbourhood else 0) | (HB_PACKED_REGISTERS if packed else 0))
     o.frontier = FRONTIER[frontier] if isinstance(frontier, str) else int(frontier)
     o.max_steps = int(max_steps)
     o.stream = _stream_ptr(stream)
