@@ -98,6 +98,9 @@ typedef struct {
                             Results never depend on it. */
     int32_t hot_passes;  /* how the hot range is used: 1 (or 0) one pass with L2
                             priorities, 2 the two-phase gather (as hb_set_hot_nodes) */
+    double frontier_switch; /* HB_FRONTIER_AUTO's switch from creation (as
+                               hb_set_frontier_switch); 0 = the default, 0.25.
+                               Results never depend on it. */
 } hb_options;
 
 typedef struct hb_graph hb_graph;   /* opaque handle */
@@ -126,6 +129,8 @@ typedef struct {
                                     hb_tune) */
     int32_t hot_passes;          /* 1: one pass with L2 priorities; 2: the two-phase gather */
     int32_t packed;              /* 1 if the counters are packed six bits per register */
+    double frontier_switch;      /* HB_FRONTIER_AUTO pushes when the arcs to push are at most
+                                    this fraction of m (hb_set_frontier_switch) */
 } hb_info;
 
 /* Algorithmic bytes of one gather-kernel launch, counted from the nodes it
@@ -228,6 +233,17 @@ hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
 /* Set the class sizing directly (a power of two from 1 to 128) and
  * re-initialise. */
 hb_status hb_set_class_sizing(hb_graph *g, int32_t arcs_per_slot);
+
+/* The switch of HB_FRONTIER_AUTO (Sec. 5 / 5.1 modification tracking: how
+ * the nodes to recompute are chosen, never what they compute).  After the
+ * first iteration, an iteration pushes the counters that changed in the
+ * one before along the reverse CSR when those counters' reverse arcs number
+ * at most push_frac * m, and otherwise recomputes every node from all its
+ * successors.  push_frac > 0 and finite (default 0.25; a value of 1 or more
+ * pushes whenever the push touches no more arcs than a full scan).  Takes
+ * effect from the next iteration; the counters are not re-initialised.
+ * HB_ERR_INVALID for a value out of range. */
+hb_status hb_set_frontier_switch(hb_graph *g, double push_frac);
 
 /* The hot range of dense iterations' gather: the nodes [0, hot_nodes) of
  * the handle's internal order (clipped to n).  After the degree relabelling

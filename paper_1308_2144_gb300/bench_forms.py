@@ -6,6 +6,7 @@ runs on the same GPU.
     python -m paper_1308_2144_gb300.bench_forms serve [--rate 200 --seconds 60 --warm 10]
     python -m paper_1308_2144_gb300.bench_forms runs [--runs 16]
     python -m paper_1308_2144_gb300.bench_forms packed [--graph enwiki --log2m 6]
+    python -m paper_1308_2144_gb300.bench_forms switch [--graph web]
 
 batch: independent R-MAT graphs (0.57, 0.19, 0.19, 0.05) with node counts
 log-uniform in [1e3, 2e6], edge factor uniform in 4..32, log2m uniform in
@@ -42,6 +43,16 @@ end with the same accumulators, else the line says so.  Prints one JSON
 line: per arm the time to the fixpoint, iterations, arc-updates/s, the
 gather kernel's mean duration and algorithmic GB/s (CUDA events,
 HB_PROFILE), and the bytes of the counters.
+
+switch: the frontier switch of HB_FRONTIER_AUTO (hb_set_frontier_switch:
+push when the arcs to push are at most that fraction of m, else recompute
+every node) on one graph with the gather options the autotuner picks for it
+(web-like: 16 arcs per slot, one pass with L2 priorities for the hot 64 MiB,
+128-byte L2 fetches; encyclopedia-like: 128 arcs per slot).  For each
+fraction, the best of --repeat runs from t = 0 to the fixpoint, then one run
+iteration by iteration (synchronised after each) for the per-iteration mode,
+arcs and time.  Every fraction must end with the same accumulators.  Prints
+one JSON line.
 """
 from __future__ import annotations
 
@@ -395,6 +406,66 @@ def packed_main(args):
     print(json.dumps(line), flush=True)
 
 
+def _bench_graph(name):
+    if name == "web":
+        return graphs.web_graph(device="cuda"), 4, True, 16, 64, \
+            "web-like (R-MAT scale 28, 268,435,456 nodes, edge factor 16), transpose, log2m 4, FP32"
+    if name == "web25":
+        return graphs.web_graph(scale=25, device="cuda", bucket_bits=3), 4, True, 16, 64, \
+            "web-like at profiling size (R-MAT scale 25, 33,554,432 nodes), transpose, log2m 4, FP32"
+    return graphs.enwiki_graph(device="cuda"), 6, False, 128, 0, \
+        "encyclopedia-like (R-MAT scale 23, 4,206,785 nodes), transpose, log2m 6, FP64"
+
+
+def switch_main(args):
+    g, b, fp32, aps, hot_mib, desc = _bench_graph(args.graph)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    prev = hbl.hb_set_l2_fetch_bytes(128)
+    h = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=42, n=g.n, fp32=fp32, arcs_per_slot=aps,
+                      hot_nodes=(hot_mib << 20) >> b, hot_passes=1)
+    line = {"form": "switch", "graph": desc, "n": g.n, "m": g.m, "arcs_per_slot": aps, "hot_mib": hot_mib}
+    ref_acc, identical, rows = None, True, []
+    for frac in args.fracs:
+        h.set_frontier_switch(frac)
+        h.reset(42)
+        h.run()                                   # warm-up
+        best = float("inf")
+        for _ in range(args.repeat):
+            h.reset(42)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.run()
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+        arcs = h.info()["total_arcs"]
+        acc = h.accumulators()
+        if ref_acc is None:
+            ref_acc = acc
+        else:
+            identical &= all(torch.equal(x, y) for x, y in zip(acc, ref_acc))
+        del acc
+        h.reset(42)
+        its = []
+        while True:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            k = h.step()
+            torch.cuda.synchronize()
+            inf = h.info()
+            its.append(["push" if inf["last_sparse"] else "dense", inf["last_arcs"],
+                        round(1e3 * (time.perf_counter() - t0), 3)])
+            if k == 0:
+                break
+        rows.append({"frac": frac, "ms": round(1e3 * best, 3), "iterations": len(its),
+                     "arc_updates_per_s": arcs / best, "per_iteration": its})
+    h.close()
+    hbl.hb_set_l2_fetch_bytes(prev)
+    line["identical_accumulators"] = bool(identical)
+    line["fracs"] = rows
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -426,10 +497,15 @@ def main():
     k.add_argument("--log2m", type=int, default=6)
     k.add_argument("--repeat", type=int, default=3)
     k.add_argument("--fp32", action="store_true")
+    w = sub.add_parser("switch")
+    w.add_argument("--graph", choices=["enwiki", "web", "web25"], default="web")
+    w.add_argument("--fracs", type=float, nargs="+", default=[0.0625, 0.125, 0.25, 0.5, 1.0, 2.0])
+    w.add_argument("--repeat", type=int, default=3)
     args = ap.parse_args()
     build.build()
     hbl.load()
-    {"batch": batch_main, "serve": serve_main, "runs": runs_main, "packed": packed_main}[args.cmd](args)
+    {"batch": batch_main, "serve": serve_main, "runs": runs_main, "packed": packed_main,
+     "switch": switch_main}[args.cmd](args)
 
 
 if __name__ == "__main__":

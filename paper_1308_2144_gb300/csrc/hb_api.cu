@@ -103,6 +103,7 @@ void default_opts(hb_options *o) {
     o->arcs_per_slot = 0;
     o->hot_nodes = 0;
     o->hot_passes = 1;
+    o->frontier_switch = 0.0;
 }
 
 // The class sizing an options block asks for (0: the default); false if it
@@ -271,7 +272,7 @@ hb_status setup_shared(hb_graph *g) {
     a.run_seeds = g->run_seeds;
     a.aps = g->y.aps;
     a.frontier = g->opt.frontier;
-    a.sparse_frac = 0.25;
+    a.sparse_frac = g->opt.frontier_switch > 0.0 ? g->opt.frontier_switch : kFrontierSwitch;
     a.hot = 0;   // the hot range is put in place after set-up (apply_hot)
     if (dense_list) {
         int64_t *sb_dev = M.alloc<int64_t>(kSegs);
@@ -510,6 +511,8 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     if (!sizing_of(o, &aps)) return fail(HB_ERR_INVALID, "arcs_per_slot must be 0 or a power of two from 1 to 128");
     if (o.hot_nodes < 0) return fail(HB_ERR_INVALID, "hot_nodes must be >= 0");
     if (o.hot_passes < 0 || o.hot_passes > 2) return fail(HB_ERR_INVALID, "hot_passes must be 0, 1 or 2");
+    if (!(o.frontier_switch >= 0.0) || !std::isfinite(o.frontier_switch))
+        return fail(HB_ERR_INVALID, "frontier_switch must be 0 (the default) or a finite positive fraction");
     if (o.flags & HB_PACKED_REGISTERS) {
         if (o.frontier != HB_FRONTIER_OFF)
             return fail(HB_ERR_INVALID, "HB_PACKED_REGISTERS needs the frontier policy HB_FRONTIER_OFF");
@@ -968,6 +971,7 @@ hb_status hb_get_info(hb_graph *g, hb_info *info) {
     info->kernel_ms = g->kernel_ms;
     info->kernel_bytes = g->kernel_bytes;
     info->packed = g->packed ? 1 : 0;
+    info->frontier_switch = g->a.sparse_frac;
     info->push_launches = g->push_launches;
     info->push_ms = g->push_ms;
     info->push_bytes = g->push_bytes;
@@ -1085,6 +1089,16 @@ hb_status hb_set_hot_nodes(hb_graph *g, int32_t hot_nodes, int32_t passes) {
     if (g->packed && hot_nodes > 0)
         return fail(HB_ERR_STATE, "handles with HB_PACKED_REGISTERS take no hot range");
     return apply_hot(g, hot_nodes, passes);
+}
+
+hb_status hb_set_frontier_switch(hb_graph *g, double push_frac) {
+    hb_status st = check(g);
+    if (st != HB_OK) return st;
+    if (!(push_frac > 0.0) || !std::isfinite(push_frac))
+        return fail(HB_ERR_INVALID, "push_frac must be a finite positive fraction");
+    g->opt.frontier_switch = push_frac;
+    g->a.sparse_frac = push_frac;
+    return HB_OK;
 }
 
 hb_status hb_reset(hb_graph *g, uint64_t seed) {

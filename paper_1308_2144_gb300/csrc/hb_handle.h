@@ -100,6 +100,9 @@ constexpr int kTuneIters = 8;
 // for the one-pass gather with L2 priorities, and for the two-phase gather.
 constexpr int64_t kTuneHintMiB[] = {32, 64, 96, 128};
 constexpr int64_t kTuneHotMiB[] = {64, 128, 192};
+// HB_FRONTIER_AUTO pushes when the arcs to push are at most this fraction
+// of m (hb_set_frontier_switch changes it per handle).
+constexpr double kFrontierSwitch = 0.25;
 
 }  // namespace hb
 
@@ -171,4 +174,5 @@ inline int64_t row_bytes(const hb_graph *g) {
     const int64_t P = (int64_t)1 << g->b;
     return g->packed ? 3 * P / 4 : P;
 }
+
 

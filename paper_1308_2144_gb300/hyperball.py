@@ -52,7 +52,7 @@ EXPORTS = ["hb_default_options", "hb_create", "hb_create32", "hb_step", "hb_run_
            "hb_version", "hb_step_noalloc", "hb_batch_create", "hb_batch_step", "hb_batch_run",
            "hb_batch_reset", "hb_batch_get_centralities", "hb_batch_get_registers",
            "hb_batch_get_accumulators", "hb_batch_get_info", "hb_batch_get_totals",
-           "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_set_hot_nodes", "hb_set_l2_fetch_bytes", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
+           "hb_batch_destroy", "hb_batch_create_runs", "hb_batch_get_run_stats", "hb_tune", "hb_set_class_sizing", "hb_set_hot_nodes", "hb_set_frontier_switch", "hb_set_l2_fetch_bytes", "hb_batch_tune", "hb_server_default_options", "hb_server_create",
            "hb_server_add_graph", "hb_server_submit", "hb_server_wait", "hb_server_cancel", "hb_server_take",
            "hb_server_stats", "hb_server_destroy"]
 
@@ -70,7 +70,8 @@ class HBNotConverged(HBError):
 class Options(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("frontier", ctypes.c_int32),
                 ("max_steps", ctypes.c_int32), ("stream", ctypes.c_void_p), ("arcs_per_slot", ctypes.c_int32),
-                ("hot_nodes", ctypes.c_int32), ("hot_passes", ctypes.c_int32)]
+                ("hot_nodes", ctypes.c_int32), ("hot_passes", ctypes.c_int32),
+                ("frontier_switch", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):
@@ -84,7 +85,7 @@ class Info(ctypes.Structure):
                 ("push_launches", ctypes.c_int64), ("push_ms", ctypes.c_double),
                 ("push_bytes", ctypes.c_double), ("arcs_per_slot", ctypes.c_int32),
                 ("hot_nodes", ctypes.c_int32), ("hot_passes", ctypes.c_int32),
-                ("packed", ctypes.c_int32)]
+                ("packed", ctypes.c_int32), ("frontier_switch", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -174,6 +175,8 @@ def load():
         L.hb_set_l2_fetch_bytes.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.hb_set_hot_nodes.restype = st
         L.hb_set_hot_nodes.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32]
+        L.hb_set_frontier_switch.restype = st
+        L.hb_set_frontier_switch.argtypes = [_vp, ctypes.c_double]
         L.hb_tune.restype = st
         L.hb_tune.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32)]
         L.hb_batch_tune.restype = st
@@ -281,7 +284,8 @@ def _stream_ptr(stream):
 
 def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, frontier="auto",
                  max_steps=1 << 20, stream=None, profile=False, pull_gather=False,
-                 neighbourhood=False, arcs_per_slot=0, hot_nodes=0, hot_passes=1, packed=False) -> Options:
+                 neighbourhood=False, arcs_per_slot=0, hot_nodes=0, hot_passes=1, packed=False,
+                 frontier_switch=0.0) -> Options:
     o = Options()
     load().hb_default_options(ctypes.byref(o))
     o.flags = ((HB_TRANSPOSE if transpose else 0) | (HB_BORROW_DEVICE_PTRS if borrow else 0)
@@ -294,6 +298,7 @@ def make_options(*, transpose=False, borrow=False, fp32=False, relabel=True, fro
     o.arcs_per_slot = int(arcs_per_slot)
     o.hot_nodes = int(hot_nodes)
     o.hot_passes = int(hot_passes)
+    o.frontier_switch = float(frontier_switch)
     return o
 
 
@@ -711,6 +716,11 @@ class HyperBall:
         (passes=1) or the two-phase gather (passes=2); results do not
         depend on it."""
         _check(load().hb_set_hot_nodes(self._h, int(hot_nodes), int(passes)))
+
+    def set_frontier_switch(self, push_frac: float):
+        """HB_FRONTIER_AUTO pushes when the arcs to push are at most
+        push_frac * m; results do not depend on it."""
+        _check(load().hb_set_frontier_switch(self._h, float(push_frac)))
 
     def set_weights(self, weights=None):
         """Node weights by replicas (Sec. 6); restarts the computation."""
