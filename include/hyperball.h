@@ -227,7 +227,8 @@ hb_status hb_reset(hb_graph *g, uint64_t seed);
  * pass gathers only part of every list).  Finally the counters are
  * re-initialised with the handle's seed.  Results never depend on any of
  * these choices.  *arcs_per_slot (may be NULL) receives the sizing;
- * hb_get_info reports all three. */
+ * hb_get_info reports all three.  The frontier switch
+ * (hb_set_frontier_switch) is left as it is. */
 hb_status hb_tune(hb_graph *g, int32_t *arcs_per_slot);
 
 /* Set the class sizing directly (a power of two from 1 to 128) and
