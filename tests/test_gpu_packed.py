@@ -245,3 +245,22 @@ def test_packed_encyclopedia_like_full_size():
     assert pk.info()["total_arcs"] == ref.info()["total_arcs"]
     ref.close()
     pk.close()
+
+
+def test_packed_profile_counts_packed_bytes():
+    """HB_PROFILE's algorithmic bytes count a packed counter read or write
+    as 3p/4 bytes: against byte registers, every dense launch (all of them
+    with HB_FRONTIER_OFF) differs by (m + 2 N) p/4, N the nodes recomputed."""
+    g = graphs.rmat_graph(scale=14, edge_factor=8, seed=12, device="cuda")
+    b = 6
+    infos = []
+    for packed in (False, True):
+        h = hbl.HyperBall(g.offsets, g.targets, log2m=b, seed=4, n=g.n, frontier="off", profile=True, packed=packed)
+        h.run()
+        infos.append(h.info())
+        h.close()
+    ib, ip = infos
+    assert ib["kernel_launches"] == ip["kernel_launches"] == ib["t"]
+    diff = ib["kernel_bytes"] - ip["kernel_bytes"]
+    want = ib["kernel_launches"] * (g.m + 2 * ib["last_nodes"]) * (1 << b) / 4
+    assert diff == pytest.approx(want, rel=1e-12)
