@@ -259,6 +259,20 @@ __device__ __forceinline__ uint4 ld_packed(const uint8_t *row, int k) {
     const uint32_t *q = reinterpret_cast<const uint32_t *>(row + 12 * k);
     return unpack_chunk(__ldg(q), __ldg(q + 1), __ldg(q + 2));
 }
+// Chunk g of a packed buffer (the buffer 8-byte aligned) with one 8-byte
+// and one 4-byte load instead of three 4-byte ones: 12 g is a multiple of 8
+// for even g, so there the first two words form an aligned 8-byte word, and
+// for odd g the last two do.  The words are selected, not branched on, so
+// lanes of either parity run the same instructions.  The gather uses it
+// where a counter is a single chunk (p = 16); for wider counters the
+// selects cost more than the load they save.
+__device__ __forceinline__ uint4 ld_packed_pair(const uint8_t *base, int64_t g) {
+    const uint32_t *q = reinterpret_cast<const uint32_t *>(base + 12 * g);
+    const bool odd = (g & 1) != 0;
+    const uint2 d = __ldg(reinterpret_cast<const uint2 *>(q + (odd ? 1 : 0)));
+    const uint32_t x = __ldg(q + (odd ? 0 : 2));
+    return unpack_chunk(odd ? x : d.x, odd ? d.x : d.y, odd ? d.y : x);
+}
 __device__ __forceinline__ void st_packed(uint8_t *row, int k, uint4 c) {
     uint32_t w0, w1, w2;
     pack_chunk(c, w0, w1, w2);

@@ -152,7 +152,9 @@ __device__ __forceinline__ void gather_arcs(const int32_t *__restrict__ tgt,
     const uint8_t *base = cur + cl * 16;
     // chunk c of target w's counter (this lane's chunks)
     auto chunk = [&](int32_t w, int c) -> uint4 {
-        if constexpr (PK)
+        if constexpr (PK && C::CH == 1)
+            return ld_packed_pair(cur, (int64_t)(uint32_t)w);
+        else if constexpr (PK)
             return ld_packed(cur + (size_t)(uint32_t)w * (3 * C::P / 4), cl + c * C::L);
         else
             return ld_counter_h<HINT>(base + (size_t)(uint32_t)w * C::P + c * C::L * 16, (uint32_t)w, hint);
