@@ -162,7 +162,14 @@ void hb_default_options(hb_options *opt);
  * the remaining bits (Sec. 4.1, Algorithm 1), capped at 64-log2m.
  * log2m must lie in [4, 12] (p >= 16 as Sec. 4.1 assumes; 4096 is the
  * largest p of Sec. 8).  The graph is validated on the device; a malformed
- * graph gives HB_ERR_INVALID and no handle.  opt may be NULL (defaults). */
+ * graph gives HB_ERR_INVALID and no handle.  opt may be NULL (defaults).
+ * With a frontier policy that pushes (AUTO, PUSH) and at least 2^20 arcs,
+ * the reverse lists of the pushed frontier are still being built on a
+ * second stream of the library's when this returns, under the first
+ * iterations, which gather; calls on the handle order themselves after that
+ * build where they need it (the first iteration that may push, the
+ * two-phase gather's reordering, hb_destroy).  Borrowed inputs are read by
+ * it too: they must stay unchanged until hb_destroy, as always. */
 hb_status hb_create(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m,
                     int log2m, uint64_t seed, const hb_options *opt, hb_graph **out);
 

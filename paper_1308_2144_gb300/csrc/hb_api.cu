@@ -141,6 +141,7 @@ hb_status apply_hot(hb_graph *g, int64_t hot_nodes, int passes) {
             if (!g->hcnt) return fail(HB_ERR_OOM, "out of device memory (hot counts)");
         }
         g->hcnt_hot = 0;
+        wait_reverse(g);   // the reverse lists' build reads the lists reordered here
         cudaError_t e = partition_hot(g->off, g->tgt, g->n, g->m, hot, g->hcnt, g->s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->s);
         if (e != cudaSuccess) {
@@ -226,9 +227,21 @@ hb_status setup_shared(hb_graph *g) {
         g->roff = M.alloc<int64_t>(n + 1);
         g->rtgt = M.alloc<int32_t>(m);
         if (M.err != cudaSuccess) return fail(HB_ERR_OOM, "out of device memory (reverse CSR)");
-        e = g->indeg ? transpose_csr_counted(g->off, g->tgt, n, m, g->indeg, g->perm, g->roff, g->rtgt, s)
-                     : transpose_csr(g->off, g->tgt, n, m, g->roff, g->rtgt, s);
+        // large graphs of single-graph handles: the targets' scatter on a
+        // second stream, under the first (gathered) iterations
+        bool defer = g->defer_reverse && m >= kDeferReverseArcs;
+        if (defer && !g->rev_s &&
+            (cudaStreamCreateWithFlags(&g->rev_s, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreateWithFlags(&g->rev_ev, cudaEventDisableTiming) != cudaSuccess)) {
+            cudaGetLastError();
+            defer = false;
+        }
+        cudaStream_t xs = defer ? g->rev_s : nullptr;
+        cudaEvent_t xe = defer ? g->rev_ev : nullptr;
+        e = g->indeg ? transpose_csr_counted(g->off, g->tgt, n, m, g->indeg, g->perm, g->roff, g->rtgt, s, xs, xe)
+                     : transpose_csr(g->off, g->tgt, n, m, g->roff, g->rtgt, s, xs, xe);
         if (e != cudaSuccess) return cuda_fail(e, "reverse CSR");
+        g->rev_pending = defer;
     }
     StepArgs &a = g->a;
     a = StepArgs{};
@@ -488,11 +501,14 @@ hb_status init_state(hb_graph *g, uint64_t seed) {
 }
 
 // lruns > 0: 2^lruns runs of one graph per row (hb_create_runs), run r
-// hashed with seeds[r] (host or device memory).
+// hashed with seeds[r] (host or device memory).  defer_reverse: the
+// handle's own iterations may start before its reverse lists are complete
+// (single-graph handles; templates of batches and servers are complete on
+// return).
 template <class OffT>
 hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
                       uint64_t seed, const hb_options *opt, hb_graph **out, int lruns = 0,
-                      const uint64_t *seeds = nullptr) {
+                      const uint64_t *seeds = nullptr, bool defer_reverse = false) {
     if (!out) return fail(HB_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (log2m < kMinLog2m || log2m > kMaxLog2m)
@@ -535,6 +551,7 @@ hb_status create_impl(const OffT *offsets, const int32_t *targets, int64_t n, in
     g->relabel = (o.flags & HB_NO_RELABEL) == 0;
     g->profile = (o.flags & HB_PROFILE) != 0;
     g->track_nf = (o.flags & HB_NEIGHBOURHOOD) != 0;
+    g->defer_reverse = defer_reverse;
     g->packed = (o.flags & HB_PACKED_REGISTERS) != 0;
     if (g->profile) {
         for (cudaEvent_t &x : g->ev)
@@ -714,6 +731,17 @@ hb_status check(hb_graph *g) {
 
 const uint8_t *current_regs(hb_graph *g) { return g->a.regs[g->t & 1]; }
 
+// Whether the next iteration may push (and so read the reverse lists): the
+// test that starts every iteration on the device, made here on the counters
+// of the iteration before, with a margin so that the answer errs towards
+// yes.  The first iteration of a computation always gathers.
+bool may_push(const hb_graph *g) {
+    if (g->t == 0) return false;
+    if (g->a.frontier == HB_FRONTIER_PUSH) return true;
+    if (g->a.frontier != HB_FRONTIER_AUTO) return false;
+    return (double)g->ctr_host->push_arcs <= g->a.sparse_frac * (double)g->m * (1.0 + 1e-9) + 1.0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -725,19 +753,20 @@ void hb_default_options(hb_options *opt) {
 hb_status hb_create(const int64_t *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
                     uint64_t seed, const hb_options *opt, hb_graph **out) {
     g_err.clear();
-    return create_impl<int64_t>(offsets, targets, n, m, log2m, seed, opt, out);
+    return create_impl<int64_t>(offsets, targets, n, m, log2m, seed, opt, out, 0, nullptr, true);
 }
 
 hb_status hb_create32(const int32_t *offsets, const int32_t *targets, int64_t n, int64_t m, int log2m,
                       uint64_t seed, const hb_options *opt, hb_graph **out) {
     g_err.clear();
-    return create_impl<int32_t>(offsets, targets, n, m, log2m, seed, opt, out);
+    return create_impl<int32_t>(offsets, targets, n, m, log2m, seed, opt, out, 0, nullptr, true);
 }
 
 hb_status hb_step(hb_graph *g, int64_t *n_changed) {
     hb_status st = check(g);
     if (st != HB_OK) return st;
     NvtxRange nv("hb_step");
+    if (g->rev_pending && may_push(g)) wait_reverse(g);
     cudaError_t e = launch_iteration(g->a, g->y, g->fp32, g->step_grid, g->s, g->profile ? g->ev : nullptr,
                                      &g->launches);
     if (e == cudaSuccess && g->track_nf) {
@@ -1233,7 +1262,7 @@ hb_status hb_create_runs(const int64_t *offsets, const int32_t *targets, int64_t
     if (log2m + lr > kMaxLog2m) return fail(HB_ERR_INVALID, "runs * 2^log2m must not exceed 4096 bytes");
     if (opt && (opt->flags & HB_NEIGHBOURHOOD))
         return fail(HB_ERR_INVALID, "HB_NEIGHBOURHOOD needs a handle of one run");
-    return create_impl<int64_t>(offsets, targets, n, m, log2m, seeds[0], opt, out, lr, seeds);
+    return create_impl<int64_t>(offsets, targets, n, m, log2m, seeds[0], opt, out, lr, seeds, true);
 }
 
 namespace {
@@ -1506,6 +1535,7 @@ hb_status hb_load(const char *path, const hb_options *opt, hb_graph **out) {
 
 void hb_destroy(hb_graph *g) {
     if (!g) return;
+    wait_reverse(g);
     if (g->s) cudaStreamSynchronize(g->s);
     else cudaDeviceSynchronize();
     delete g;

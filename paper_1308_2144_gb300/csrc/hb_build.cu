@@ -439,9 +439,11 @@ cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaSt
 
 // Source nodes of the first and last arc of every kArcTile tile of the
 // CSR (off, m arcs): 2 entries per tile, freed by the caller.
-static cudaError_t tile_ends(const int64_t *off, int64_t n, int64_t m, int64_t **ends, cudaStream_t s) {
+static cudaError_t tile_ends(const int64_t *off, int64_t n, int64_t m, int64_t **ends, cudaStream_t s,
+                             bool default_pool = false) {
     const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
-    cudaError_t e = tmp_alloc(ends, sizeof(int64_t) * 2 * ntiles, s);
+    cudaError_t e = default_pool ? cudaMallocAsync(reinterpret_cast<void **>(ends), sizeof(int64_t) * 2 * ntiles, s)
+                                 : tmp_alloc(ends, sizeof(int64_t) * 2 * ntiles, s);
     if (e != cudaSuccess) return e;
     tile_ends_kernel<<<grid_for(ntiles, 256), 256, 0, s>>>(off, n, m, ntiles, *ends);
     return cudaGetLastError();
@@ -449,9 +451,16 @@ static cudaError_t tile_ends(const int64_t *off, int64_t n, int64_t m, int64_t *
 
 cudaError_t transpose_csr_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                                   const unsigned long long *indeg, const int32_t *perm, int64_t *toff,
-                                  int32_t *ttgt, cudaStream_t s) {
+                                  int32_t *ttgt, cudaStream_t s, cudaStream_t scatter_s,
+                                  cudaEvent_t scatter_done) {
+    // With the scatter on its own stream, the buffers it uses (and frees on
+    // that stream) come from the device's default pool: a block freed there is
+    // never handed to a later allocation of the library's pool on s, which
+    // would make s wait for the scatter.
+    const bool apart = scatter_s != nullptr;
     unsigned long long *cnt = nullptr;
-    cudaError_t e = tmp_alloc(&cnt, sizeof(unsigned long long) * (n + 1), s);
+    cudaError_t e = apart ? cudaMallocAsync(reinterpret_cast<void **>(&cnt), sizeof(unsigned long long) * (n + 1), s)
+                          : tmp_alloc(&cnt, sizeof(unsigned long long) * (n + 1), s);
     if (e != cudaSuccess) return e;
     if (indeg) {
         permuted_counts<<<grid_for(n + 1, 256), 256, 0, s>>>(indeg, perm, n, cnt);
@@ -461,22 +470,33 @@ cudaError_t transpose_csr_counted(const int64_t *off, const int32_t *tgt, int64_
     }
     e = scan_exclusive_i64(reinterpret_cast<int64_t *>(cnt), toff, n + 1, s);
     int64_t *ends = nullptr;
-    if (e == cudaSuccess && m > 0) e = tile_ends(off, n, m, &ends, s);
+    if (e == cudaSuccess && m > 0) e = tile_ends(off, n, m, &ends, s, apart);
+    cudaStream_t xs = s;   // the scatter's stream
     if (e == cudaSuccess && m > 0) {
-        cudaMemcpyAsync(cnt, toff, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
-        const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
-        scatter_transpose<<<grid_for(ntiles * kArcThreads, kArcThreads), kArcThreads, 0, s>>>(off, tgt, n, m, ends,
-                                                                                          cnt, ttgt);
-        e = cudaGetLastError();
+        e = cudaMemcpyAsync(cnt, toff, sizeof(int64_t) * n, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && scatter_s) {
+            // the scatter on its own stream, ordered after everything above
+            e = cudaEventRecord(scatter_done, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(scatter_s, scatter_done, 0);
+            if (e == cudaSuccess) xs = scatter_s;
+        }
+        if (e == cudaSuccess) {
+            const int64_t ntiles = (m + kArcTile - 1) / kArcTile;
+            scatter_transpose<<<grid_for(ntiles * kArcThreads, kArcThreads), kArcThreads, 0, xs>>>(off, tgt, n, m,
+                                                                                               ends, cnt, ttgt);
+            e = cudaGetLastError();
+        }
     }
-    cudaFreeAsync(cnt, s);
-    if (ends) cudaFreeAsync(ends, s);
+    cudaFreeAsync(cnt, xs);
+    if (ends) cudaFreeAsync(ends, xs);
+    if (e == cudaSuccess && scatter_s) e = cudaEventRecord(scatter_done, xs);
     return e;
 }
 
 cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                          int64_t *toff, int32_t *ttgt, cudaStream_t s) {
-    return transpose_csr_counted(off, tgt, n, m, nullptr, nullptr, toff, ttgt, s);
+                          int64_t *toff, int32_t *ttgt, cudaStream_t s, cudaStream_t scatter_s,
+                          cudaEvent_t scatter_done) {
+    return transpose_csr_counted(off, tgt, n, m, nullptr, nullptr, toff, ttgt, s, scatter_s, scatter_done);
 }
 
 // Node order for the step kernel: out-degree buckets descending (so every

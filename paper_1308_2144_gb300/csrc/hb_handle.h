@@ -103,6 +103,11 @@ constexpr int64_t kTuneHotMiB[] = {64, 128, 192};
 // HB_FRONTIER_AUTO pushes when the arcs to push are at most this fraction
 // of m (hb_set_frontier_switch changes it per handle).
 constexpr double kFrontierSwitch = 0.25;
+// Handles made by hb_create, hb_create32 and hb_create_runs with at least
+// this many arcs build their reverse lists on a second stream while the
+// first iterations, which gather, run (hb_step makes the handle's stream
+// wait for them before the first iteration that may push).
+constexpr int64_t kDeferReverseArcs = (int64_t)1 << 20;
 
 }  // namespace hb
 
@@ -137,6 +142,10 @@ struct hb_graph {
     std::vector<int32_t> run_last; // per run: last iteration in which it changed (-1: none)
     bool track_nf = false;         // HB_NEIGHBOURHOOD: N(t) after every iteration
     bool packed = false;           // HB_PACKED_REGISTERS: rows of 3p/4 bytes, six bits per register
+    bool defer_reverse = false;    // reverse lists may be built on rev_s (public creates)
+    bool rev_pending = false;      // rev_s may still be writing rtgt; s has not waited for rev_ev
+    cudaStream_t rev_s = nullptr;
+    cudaEvent_t rev_ev = nullptr;  // recorded on rev_s once rtgt is complete
     double *nf_part = nullptr;     // block partials of the estimate sum
     std::vector<double> nf;        // N(0), N(1), ... of the current run
     Counters *ctr = nullptr;
@@ -161,6 +170,9 @@ struct hb_graph {
     bool own_ctr_host = true;
 
     ~hb_graph() {
+        if (rev_s) cudaStreamSynchronize(rev_s);   // nothing of it outlives the buffers
+        if (rev_s) cudaStreamDestroy(rev_s);
+        if (rev_ev) cudaEventDestroy(rev_ev);
         for (cudaEvent_t &x : ev)
             if (x) cudaEventDestroy(x);
         if (ctr_host && own_ctr_host) cudaFreeHost(ctr_host);
@@ -175,4 +187,10 @@ inline int64_t row_bytes(const hb_graph *g) {
     return g->packed ? 3 * P / 4 : P;
 }
 
-
+// Order the handle's stream after the reverse lists' build, if it may still
+// run: before anything that reads the reverse lists or rewrites the targets.
+inline void wait_reverse(hb_graph *g) {
+    if (!g->rev_pending) return;
+    cudaStreamWaitEvent(g->s, g->rev_ev, 0);
+    g->rev_pending = false;
+}

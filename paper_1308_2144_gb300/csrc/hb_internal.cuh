@@ -450,14 +450,19 @@ cudaError_t validate_offsets(const int64_t *off, int64_t n, int64_t m, unsigned 
 cudaError_t check_targets(const int32_t *tgt, int64_t len, int64_t n, unsigned long long *err_dev,
                           unsigned long long *indeg, cudaStream_t s);
 cudaError_t widen_offsets(const int32_t *in, int64_t *out, int64_t count, cudaStream_t s);
+// With scatter_s, the offsets are computed on s and the targets scattered
+// on scatter_s after them; scatter_done is then recorded on scatter_s when
+// the targets are in place.
 cudaError_t transpose_csr(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
-                          int64_t *toff, int32_t *ttgt, cudaStream_t s);
+                          int64_t *toff, int32_t *ttgt, cudaStream_t s, cudaStream_t scatter_s = nullptr,
+                          cudaEvent_t scatter_done = nullptr);
 // transpose_csr of a relabelled graph whose node v is the caller's perm[v]
 // (perm null: the identity) and has in-degree indeg[perm[v]]; indeg null
 // counts the in-arcs instead.
 cudaError_t transpose_csr_counted(const int64_t *off, const int32_t *tgt, int64_t n, int64_t m,
                                   const unsigned long long *indeg, const int32_t *perm, int64_t *toff,
-                                  int32_t *ttgt, cudaStream_t s);
+                                  int32_t *ttgt, cudaStream_t s, cudaStream_t scatter_s = nullptr,
+                                  cudaEvent_t scatter_done = nullptr);
 // Node order for the step kernel (perm: new -> caller's id, inv: its
 // inverse).  indeg (n entries) holds the in-degree of each of the caller's
 // nodes when counted is true, and receives it otherwise.

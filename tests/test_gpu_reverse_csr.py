@@ -6,7 +6,10 @@ caller's order (reverse lists counted by the library, not from the in-degree
 precount) and for a graph the library transposes itself.  A missing,
 duplicated or misplaced reverse arc changes the pushed union, so the
 counters must equal the oracle's bit for bit with every iteration that can
-push pushing."""
+push pushing.  Also the reverse lists built on a second stream under the
+first iterations: pushed and automatic frontiers, the two-phase gather's
+reordering of the target lists asked for before the first step, and
+handles destroyed while the build may still run."""
 import numpy as np
 import pytest
 import torch
@@ -64,6 +67,57 @@ def test_hub_reverse_csr_caller_order_and_transpose(orc):
     ref = orc.run(off, tgt, 4, 3)
     h = hbl.HyperBall(torch.from_numpy(toff).cuda(), torch.from_numpy(ttgt).cuda(), log2m=4, seed=3, n=n,
                       transpose=True, frontier="push")
+    assert h.run() == ref.steps
+    assert np.array_equal(h.registers().cpu().numpy(), ref.regs)
+    h.close()
+
+
+# Graphs of at least 2^20 arcs made through hb_create build their reverse
+# lists on a second stream while the first iterations gather; the handle's
+# stream waits for them before the first iteration that may push, before the
+# two-phase gather reorders the target lists, and at destroy.
+
+@pytest.mark.parametrize("frontier,hot_passes", [("push", 0), ("auto", 0), ("auto", 1), ("auto", 2)])
+def test_reverse_lists_built_under_the_first_iterations(orc, frontier, hot_passes):
+    off, tgt = graphs.rmat_graph(scale=18, edge_factor=16, seed=41).numpy()
+    n = off.size - 1
+    assert tgt.size >= 1 << 20
+    hot = dict(hot_nodes=n // 8, hot_passes=hot_passes) if hot_passes else {}
+    walk_parity(orc, off, tgt, 4, 9, frontier=frontier, **hot)
+
+
+def test_targets_reordered_right_after_create(orc):
+    # the two-phase gather's reordering of every target list, asked for
+    # before the first step, while the reverse lists may still be built
+    off, tgt = graphs.rmat_graph(scale=18, edge_factor=16, seed=43).numpy()
+    n = off.size - 1
+    d_off, d_tgt = torch.from_numpy(off).cuda(), torch.from_numpy(tgt).cuda()
+    h = hbl.HyperBall(d_off, d_tgt, log2m=5, seed=2, n=n, frontier="auto")
+    h.set_hot_nodes(n // 5, 2)
+    c = orc.init(n, 5, 2)
+    s, hm = np.zeros(n), np.zeros(n)
+    t = 0
+    pushed = 0
+    while True:
+        c, _, k = orc.step(off, tgt, 5, t, c, s, hm)
+        assert h.step() == k
+        pushed += h.info()["last_sparse"]
+        assert np.array_equal(h.registers().cpu().numpy(), c), t
+        t += 1
+        if k == 0:
+            break
+    assert pushed > 0
+    h.close()
+
+
+def test_destroy_while_reverse_lists_may_be_built(orc):
+    g = graphs.rmat_graph(scale=20, edge_factor=16, seed=45, device="cuda")
+    for seed in range(4):
+        h = hbl.HyperBall(g.offsets, g.targets, log2m=4, seed=seed, n=g.n, frontier="push")
+        h.close()
+    off, tgt = g.numpy()
+    ref = orc.run(off, tgt, 4, 6)
+    h = hbl.HyperBall(g.offsets, g.targets, log2m=4, seed=6, n=g.n, frontier="push")
     assert h.run() == ref.steps
     assert np.array_equal(h.registers().cpu().numpy(), ref.regs)
     h.close()
